@@ -1,0 +1,244 @@
+/*
+ * lilac.h -- C ABI of the GB300 sparse library: CSR sparse matrix-vector
+ * multiply on a device-resident matrix, and the two loops built on it that
+ * the paper accelerates, conjugate gradient and PageRank.
+ *
+ * Paper: P. Ginsbach, B. Collie, M. F. P. O'Boyle, "Automatically Harnessing
+ * Sparse Acceleration", CC 2020 (arXiv 2001.07938).
+ *
+ *  - The arguments of the SpMV entry points are those of the paper's
+ *    spmv_csr computation (Section 3.2, CSR paragraph: rows, row_ptr,
+ *    col_ind, val, x -> y); the paper's LiLAC-What program names them as
+ *    the harness interface (Section 3.1).
+ *  - The paper's persistent harness state and data marshaling (Section 3.3:
+ *    PersistentVariables / BeforeFirstExecution / AfterLastExecution,
+ *    Marshaling with CudaRead; Section 4.2: the construct / update /
+ *    destruct contract of ReadObject) become an explicit handle:
+ *    lilac_csr_create uploads the matrix once (construct + update),
+ *    lilac_csr_update_values re-uploads changed values (update), and
+ *    lilac_csr_destroy frees it (destruct).  The library keeps no pointer
+ *    to caller memory; it copies what it needs.
+ *  - The data-dependent invariant the paper caches (the column count
+ *    "cols" = Maximum(col_ind), Section 3.3) is computed once at create,
+ *    together with the row-length statistics and the tile schedule the
+ *    kernels use, and the dangling-vertex set PageRank needs (on first use).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns a lilac_status; no exception crosses the ABI.
+ *    lilac_last_error() gives a one-line message for the calling thread's
+ *    last failure.
+ *  - Indices are int32 and 0-based; nnz < 2^31.  Empty rows are allowed
+ *    (their y is 0), so are duplicate (i, j) entries (they add up) and
+ *    unsorted columns.
+ *  - `stream` is a cudaStream_t (NULL: the legacy default stream).  Device
+ *    vectors are caller-owned and must not alias each other.  Work is
+ *    stream-ordered and asynchronous unless a call says it synchronizes.
+ *  - A handle may be used from one stream at a time: two calls on the same
+ *    handle must not run concurrently on different streams (they share the
+ *    handle's scratch memory).
+ *  - A call that fails on the device (a bounded wait that timed out) marks
+ *    the handle; later calls return LILAC_ERR_TIMEOUT until
+ *    lilac_csr_reset_error().
+ */
+#ifndef LILAC_H
+#define LILAC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lilac_csr_s* lilac_csr; /* opaque; owned by the library */
+
+typedef enum {
+    LILAC_OK = 0,
+    LILAC_ERR_INVALID_ARG = 1,   /* NULL handle/pointer, negative size, bad option */
+    LILAC_ERR_INVALID_CSR = 2,   /* row_ptr not monotone / not 0..nnz, col_ind out of range */
+    LILAC_ERR_OOM = 3,           /* device allocation failed */
+    LILAC_ERR_BUDGET = 4,        /* request exceeds a configured device-memory budget */
+    LILAC_ERR_CUDA = 5,          /* a CUDA runtime call failed (see lilac_last_error) */
+    LILAC_ERR_BREAKDOWN = 6,     /* CG: p.Ap <= 0 or not finite (matrix not SPD) */
+    LILAC_ERR_NOT_CONVERGED = 7, /* CG: tolerance not reached within max_iter */
+    LILAC_ERR_TIMEOUT = 8,       /* a device-side bounded wait gave up */
+    LILAC_ERR_DTYPE = 9,         /* operation not defined for the handle's value type */
+    LILAC_ERR_UNSUPPORTED = 10   /* feature not available in this build or device */
+} lilac_status;
+
+typedef enum { LILAC_F64 = 0, LILAC_F32 = 1 } lilac_dtype;
+typedef enum { LILAC_MEM_HOST = 0, LILAC_MEM_DEVICE = 1 } lilac_mem;
+
+/* SpMV kernel variants (all compute the same y; they differ in how rows and
+ * nonzeros map to threads). */
+typedef enum {
+    LILAC_VARIANT_AUTO = 0,   /* chosen at create from row-length statistics */
+    LILAC_VARIANT_SCALAR = 1, /* one thread per row */
+    LILAC_VARIANT_VECTOR = 2, /* V lanes per row, V in {2,4,8,16,32}; V = 32 is warp-per-row */
+    LILAC_VARIANT_STAGED = 3, /* nnz-balanced row tiles staged in shared memory by bulk
+                                 asynchronous copies; rows longer than a tile are split */
+    LILAC_VARIANT_MERGE = 4   /* merge-path partition of (rows + nonzeros) */
+} lilac_variant;
+
+/* lilac_csr_create flags */
+#define LILAC_CREATE_TUNE_TIMED 0x1u /* time the candidate variants once at create and keep the fastest */
+
+/*
+ * Upload a CSR matrix once and return a handle (construct + update of the
+ * paper's marshaling contract, Section 4.2).
+ *   rows     number of rows, >= 0 (the length of row_ptr minus one, Section 3.2)
+ *   ncols    number of columns; < 0 means max(col_ind) + 1 (the Maximum
+ *            invariant of Section 3.3; 0 when nnz == 0)
+ *   nnz      number of stored entries, 0 <= nnz < 2^31; must equal row_ptr[rows]
+ *   row_ptr  rows + 1 int32 offsets, row_ptr[0] == 0, non-decreasing
+ *   col_ind  nnz int32 column indices in [0, ncols)
+ *   vals     nnz values of type `dtype` (double for LILAC_F64, float for LILAC_F32)
+ *   where    whether the three arrays are in host or device memory
+ *   flags    LILAC_CREATE_* bits
+ *   stream   stream for the upload; the call synchronizes it before returning
+ *   out      receives the handle (NULL on failure)
+ * The arrays are copied; the caller may free or change them afterwards.
+ * Errors: INVALID_ARG, INVALID_CSR (validated on the device), OOM, CUDA.
+ */
+lilac_status lilac_csr_create(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
+                              const int32_t* col_ind, const void* vals, lilac_dtype dtype,
+                              lilac_mem where, uint32_t flags, void* stream, lilac_csr* out);
+
+/*
+ * Replace the values (same structure): the paper's "update" step, run when
+ * the data of a marshaled array changed (Section 4.2).  nnz values of the
+ * handle's dtype.  Asynchronous on `stream`.  Cached FP32 copies derived
+ * from FP64 values are refreshed.
+ */
+lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem where, void* stream);
+
+/* Free everything the handle owns (the paper's "destruct").  NULL is a no-op.
+ * Synchronizes the device work the handle issued. */
+lilac_status lilac_csr_destroy(lilac_csr A);
+
+typedef struct {
+    int32_t rows;
+    int32_t ncols;
+    int64_t nnz;
+    int32_t dtype;          /* lilac_dtype */
+    int32_t variant;        /* lilac_variant in use */
+    int32_t vector_width;   /* lanes per row for VECTOR / STAGED */
+    int32_t max_row_len;
+    int32_t empty_rows;
+    int32_t num_tiles;      /* STAGED: row tiles incl. long-row chunks */
+    int32_t num_long_rows;  /* STAGED: rows split across tiles */
+    int32_t sm_count;
+    double mean_row_len;
+    double std_row_len;
+    int64_t device_bytes;   /* device memory held by the handle right now */
+    int64_t h2d_bytes;      /* bytes uploaded to the matrix so far (create + updates) */
+} lilac_csr_info_t;
+
+/* Describe the handle.  Synchronous only on host state. */
+lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
+
+/* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR
+ * and STAGED, lanes per row (power of two 1..32; 0 keeps the current one).
+ * Host-only; affects later calls. */
+lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
+
+/*
+ * y = A x (the paper's spmv_csr computation, Section 3.2):
+ *   y[i] = sum over row_ptr[i] <= j < row_ptr[i+1] of val[j] * x[col_ind[j]].
+ *   x  ncols elements, y  rows elements, both of the handle's dtype; FP64
+ *      matrices accumulate in FP64, FP32 matrices in FP32.
+ *   where  LILAC_MEM_DEVICE: x and y are device pointers; the call is
+ *          asynchronous.  LILAC_MEM_HOST: x and y are host pointers; the
+ *          library copies x in and y out through its own device buffers and
+ *          synchronizes `stream` before returning (pinned host memory makes
+ *          the copies asynchronous DMA).
+ * Errors: INVALID_ARG, CUDA, TIMEOUT.
+ */
+lilac_status lilac_spmv(lilac_csr A, const void* x, void* y, lilac_mem where, void* stream);
+
+typedef struct {
+    int32_t max_iter;       /* iteration cap (FP64 CG) or outer-refinement cap (mixed) */
+    double rtol;            /* stop when ||r|| <= rtol ||b||; <= 0: run exactly max_iter */
+    int32_t precision;      /* 0: FP64 CG.  1: FP32 inner CG + FP64 iterative refinement */
+    double inner_rtol;      /* mixed: inner stop ||r_in|| <= inner_rtol ||r_outer|| */
+    int32_t inner_max_iter; /* mixed: inner iteration cap per refinement */
+    int32_t use_x0;         /* 1: start from x as given; 0: start from x = 0 */
+    int32_t true_residual;  /* 1: recompute ||b - A x|| / ||b|| in FP64 at the end */
+    int32_t use_graph;      /* 1: replay the iterations as a captured CUDA graph */
+    int32_t check_every;    /* iterations between host convergence checks when rtol > 0 */
+    int32_t profile;        /* 1: time every SpMV launch of the solve with CUDA events
+                               (reported in lilac_cg_info; needs info) */
+} lilac_cg_opts;
+
+typedef struct {
+    int32_t iters;          /* CG iterations done (all inner iterations when mixed) */
+    int32_t refinements;    /* mixed: outer refinement steps */
+    int32_t status;         /* lilac_status of the solve */
+    int32_t pad;
+    double rel_res;         /* recursive (FP64 CG) or outer true (mixed) ||r|| / ||b|| */
+    double true_rel_res;    /* ||b - A x|| / ||b|| in FP64 if requested, else -1 */
+    double spmv_ms;         /* opts->profile: summed duration of the SpMV launches */
+    int32_t spmv_launches;  /* opts->profile: number of SpMV launches timed */
+    int32_t kernel_launches; /* kernels the solve launched (including no-op ones after convergence) */
+} lilac_cg_info;
+
+/* Fill *o with the defaults: max_iter 1000, rtol 1e-10, FP64, inner_rtol
+ * 1e-5, inner_max_iter 1000, use_x0 0, true_residual 1, use_graph 1,
+ * check_every 32, profile 0. */
+void lilac_cg_opts_default(lilac_cg_opts* o);
+
+/*
+ * Solve A x = b for symmetric positive definite A with unpreconditioned
+ * conjugate gradient (Hestenes-Stiefel; the NAS CG solver whose SpMV loop
+ * the paper's compiler replaces, Section 2 and Section 5).  Each iteration is
+ * q = A p with p.q fused into the SpMV; x += alpha p, r -= alpha q with r.r
+ * fused into one pass; p = r + beta p.  The scalars stay on the device.
+ *   b, x    rows FP64 elements; x holds x0 on entry if opts->use_x0, the
+ *           solution on exit.  `where` as in lilac_spmv.
+ *   opts    NULL: defaults.  precision 1 needs ncols == rows; the inner
+ *           solves use FP32 values (the handle's, or an FP32 copy derived
+ *           once from FP64 values) and the FP64 residual b - A x uses the
+ *           handle's own values.
+ *   info    nullable; if given, the call synchronizes `stream` at the end.
+ * Returns OK, NOT_CONVERGED (rtol > 0 not reached), BREAKDOWN, or an error.
+ * With rtol > 0 the call synchronizes `stream` every check_every iterations.
+ */
+lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_mem where,
+                      const lilac_cg_opts* opts, lilac_cg_info* info, void* stream);
+
+/*
+ * PageRank power iteration (the GAP PageRank kernel the paper accelerates,
+ * Section 5 and Section 6.1) on the TRANSPOSED link matrix: row i lists the
+ * sources j of the edges j -> i with value 1/outdeg(j); a vertex whose
+ * column is empty has no out-edge (dangling) and its rank is spread
+ * uniformly.  Per iteration, with N = rows and D = sum of x_j over dangling j:
+ *     y_i = d * (A x)_i + (d * D + 1 - d) / N,    l1_t = sum_i |y_i - x_i|,   x = y.
+ *   x             N elements of the handle's dtype: the start vector on entry
+ *                 (unless init_uniform, which starts from 1/N), the result on exit
+ *   iters         number of iterations (>= 0), no early stop
+ *   damping       d in [0, 1]
+ *   l1_per_iter   nullable host array of iters doubles; if given, the call
+ *                 synchronizes `stream` and copies the per-iteration L1 changes
+ * Row sums, y and x are in the handle's dtype; D and L1 are accumulated in
+ * FP64.  Needs rows == ncols.
+ */
+lilac_status lilac_pagerank(lilac_csr AT, void* x, int32_t init_uniform, int32_t iters,
+                            double damping, double* l1_per_iter, lilac_mem where, void* stream);
+
+/* Clear a sticky device error of the handle and re-zero its scratch memory. */
+lilac_status lilac_csr_reset_error(lilac_csr A);
+
+/* Static text for a status code. */
+const char* lilac_status_string(lilac_status s);
+
+/* Message of the calling thread's last failed call ("" if none). */
+const char* lilac_last_error(void);
+
+/* ABI version of this header: major * 10000 + minor * 100 + patch. */
+int32_t lilac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LILAC_H */

@@ -1,0 +1,163 @@
+// SpMV launch dispatch: the handle's variant and lanes-per-row select one
+// instantiation of the kernels in spmv_kernels.cuh.  Grids are persistent:
+// the SM count times the resident CTAs per SM, never more CTAs than there
+// is work.
+#pragma once
+
+#include "lilac_impl.h"
+
+namespace lilac {
+
+template <class Kernel>
+int occupancy_per_sm(Kernel k, int threads, size_t smem) {
+    int bps = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();
+        bps = 1;
+    }
+    return bps < 1 ? 1 : bps;
+}
+
+// Resident CTAs per SM of one kernel instantiation, per device (0: unknown).
+template <int V, class Op, bool STAGED>
+int& bps_slot(int device) {
+    static int cache[64] = {};
+    return cache[device & 63];
+}
+
+// The first use of an instantiation on a device queries its occupancy (and
+// raises its shared-memory limit); prepare_spmv() does that ahead of a
+// stream capture, where such calls must not happen.
+template <int V, class Op>
+lilac_status prepare_rows(lilac_csr_s* A) {
+    int& bps = bps_slot<V, Op, false>(A->device);
+    if (bps == 0) bps = occupancy_per_sm(spmv_rows_kernel<V, kRowsThreads, Op>, kRowsThreads, 0);
+    return LILAC_OK;
+}
+
+template <int V, class Op>
+lilac_status prepare_staged(lilac_csr_s* A) {
+    using L = StagedLayout<typename Op::ValT, kTileNnz, kTileRows>;
+    int& bps = bps_slot<V, Op, true>(A->device);
+    if (bps == 0) {
+        auto kern = spmv_staged_kernel<V, kStagedThreads, kTileNnz, kTileRows, Op>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)L::kSmemBytes));
+        bps = occupancy_per_sm(kern, kStagedThreads, L::kSmemBytes);
+    }
+    return LILAC_OK;
+}
+
+template <int V, class Op>
+lilac_status launch_rows(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                         const Op& op, cudaStream_t stream) {
+    LILAC_TRY(prepare_rows<V, Op>(A));
+    const int bps = bps_slot<V, Op, false>(A->device);
+    const int64_t need = ((int64_t)A->rows * V + kRowsThreads - 1) / kRowsThreads;
+    int64_t grid = (int64_t)A->sm_count * bps;
+    if (grid > need) grid = need;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) grid = 1;
+    CsrView<typename Op::ValT> view{A->row_ptr.as<int>(), A->col_ind.as<int>(), val, A->rows};
+    spmv_rows_kernel<V, kRowsThreads, Op>
+        <<<(unsigned)grid, kRowsThreads, 0, stream>>>(view, x, op, A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+template <int V, class Op>
+lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                           const Op& op, cudaStream_t stream) {
+    using L = StagedLayout<typename Op::ValT, kTileNnz, kTileRows>;
+    if (A->ntiles == 0 && Op::NR == 0) return LILAC_OK;  // no rows and nothing to sum
+    LILAC_TRY(prepare_staged<V, Op>(A));
+    const int bps = bps_slot<V, Op, true>(A->device);
+    int64_t grid = (int64_t)A->sm_count * bps;
+    if (grid > A->ntiles) grid = A->ntiles;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) grid = 1;
+    CsrView<typename Op::ValT> view{A->row_ptr.as<int>(), A->col_ind.as<int>(), val, A->rows};
+    spmv_staged_kernel<V, kStagedThreads, kTileNnz, kTileRows, Op>
+        <<<(unsigned)grid, kStagedThreads, L::kSmemBytes, stream>>>(
+            view, A->tiles.as<TileDesc>(), A->ntiles, A->longs.as<LongRow>(), A->nlong, x, op,
+            A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, ...)                        \
+    switch (A->variant) {                                                   \
+        case LILAC_VARIANT_SCALAR:                                          \
+            return FN_ROWS<1, Op>(__VA_ARGS__);                             \
+        case LILAC_VARIANT_VECTOR:                                          \
+            switch (A->vwidth) {                                            \
+                case 2: return FN_ROWS<2, Op>(__VA_ARGS__);                 \
+                case 4: return FN_ROWS<4, Op>(__VA_ARGS__);                 \
+                case 8: return FN_ROWS<8, Op>(__VA_ARGS__);                 \
+                case 16: return FN_ROWS<16, Op>(__VA_ARGS__);               \
+                default: return FN_ROWS<32, Op>(__VA_ARGS__);               \
+            }                                                               \
+        case LILAC_VARIANT_STAGED:                                          \
+        default:                                                            \
+            switch (A->vwidth) {                                            \
+                case 1: return FN_STAGED<1, Op>(__VA_ARGS__);               \
+                case 2: return FN_STAGED<2, Op>(__VA_ARGS__);               \
+                case 4: return FN_STAGED<4, Op>(__VA_ARGS__);               \
+                case 8: return FN_STAGED<8, Op>(__VA_ARGS__);               \
+                case 16: return FN_STAGED<16, Op>(__VA_ARGS__);             \
+                default: return FN_STAGED<32, Op>(__VA_ARGS__);             \
+            }                                                               \
+    }
+
+template <class Op>
+lilac_status prepare_spmv(lilac_csr_s* A) {
+    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, A)
+}
+
+template <class Op>
+lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                         const Op& op, cudaStream_t stream) {
+    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, A, val, x, op, stream)
+}
+
+// Replay `body` (which enqueues work on the stream it is given) as a CUDA
+// graph captured once per key and cached in the handle, or run it directly.
+// Everything `body` launches must have been prepared (prepare_spmv) first.
+template <class F>
+lilac_status run_maybe_graph(lilac_csr_s* A, const GraphKey& key, bool use_graph,
+                             cudaStream_t stream, F&& body) {
+    if (!use_graph) return body(stream);
+    auto it = A->graphs.find(key);
+    if (it == A->graphs.end()) {
+        if (A->graphs.size() >= 64) {
+            for (auto& kv : A->graphs) cudaGraphExecDestroy(kv.second);
+            A->graphs.clear();
+        }
+        if (!A->capture_stream)
+            LILAC_CUDA_TRY(cudaStreamCreateWithFlags(&A->capture_stream, cudaStreamNonBlocking));
+        LILAC_CUDA_TRY(cudaStreamBeginCapture(A->capture_stream, cudaStreamCaptureModeThreadLocal));
+        lilac_status st = body(A->capture_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(A->capture_stream, &g);
+        if (st != LILAC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) {
+            set_last_error(std::string("stream capture: ") + cudaGetErrorString(e));
+            return LILAC_ERR_CUDA;
+        }
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            set_last_error(std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+            return LILAC_ERR_CUDA;
+        }
+        it = A->graphs.emplace(key, ex).first;
+    }
+    LILAC_CUDA_TRY(cudaGraphLaunch(it->second, stream));
+    return LILAC_OK;
+}
+
+}  // namespace lilac

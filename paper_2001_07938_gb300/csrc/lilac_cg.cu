@@ -1,0 +1,363 @@
+// lilac_cg: unpreconditioned conjugate gradient on the resident matrix (the
+// NAS CG solver whose SpMV the paper's compiler offloads, Section 2 and
+// Section 5), with the dot products and axpys fused around the SpMV and every
+// scalar kept on the device, plus the mixed-precision form: FP32 inner CG
+// and FP64 iterative refinement.
+//
+// One iteration is three launches:
+//   K1  q = A p, p.q  (SpMV epilogue) -> alpha = rr / p.q
+//   K2  x += alpha p, r -= alpha q, r.r (one pass) -> beta, convergence
+//   K3  p = r + beta p
+// A solve with a fixed iteration count is replayed as one CUDA graph; with a
+// tolerance, graphs of `check_every` iterations are replayed until the
+// device flags convergence (kernels after convergence return at once).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "launch.cuh"
+
+namespace lilac {
+
+__global__ void cg_state_reset_kernel(CgState* st, int max_iter) {
+    st->rr = 0.0;
+    st->pq = 0.0;
+    st->alpha = 0.0;
+    st->beta = 0.0;
+    st->bb = 0.0;
+    st->tol2 = -1.0;
+    st->true_rr = -1.0;
+    st->iters = 0;
+    st->max_iter = max_iter;
+    st->done = 0;
+    st->status = LILAC_ERR_NOT_CONVERGED;
+}
+
+static lilac_status ensure_cg_work(lilac_csr A, CgWork& W, bool f32) {
+    const size_t vsz = f32 ? 4 : 8;
+    const size_t n = (size_t)std::max(1, A->rows);
+    if (W.r.p && W.n == A->rows) return LILAC_OK;
+    W.n = A->rows;
+    W.f32 = f32;
+    LILAC_TRY(A->ws_alloc(W.r, vsz * n));
+    LILAC_TRY(A->ws_alloc(W.p, vsz * n));
+    LILAC_TRY(A->ws_alloc(W.q, vsz * n));
+    LILAC_TRY(A->ws_alloc(W.state, sizeof(CgState)));
+    return LILAC_OK;
+}
+
+enum GraphKind { G_CG64_FIXED = 1, G_CG64_CHUNK = 2, G_CG32_CHUNK = 3 };
+
+// Profiling of the SpMV launches (opts->profile): event pairs recorded on the
+// launching stream around every SpMV, also inside captured graphs.
+struct Prof {
+    bool on = false;
+    double ms = 0.0;
+    int launches = 0;
+    int kernels = 0;  // all kernels launched by the solve
+};
+
+static lilac_status ensure_prof_events(lilac_csr A, int pairs) {
+    while ((int)A->prof_events.size() < 2 * pairs) {
+        cudaEvent_t e;
+        LILAC_CUDA_TRY(cudaEventCreate(&e));
+        A->prof_events.push_back(e);
+    }
+    return LILAC_OK;
+}
+
+// Add the durations of the first `pairs` event pairs (after a synchronize).
+static lilac_status collect_prof(lilac_csr A, int pairs, Prof& prof) {
+    for (int i = 0; i < pairs; ++i) {
+        float ms = 0.f;
+        LILAC_CUDA_TRY(cudaEventElapsedTime(&ms, A->prof_events[2 * i], A->prof_events[2 * i + 1]));
+        prof.ms += ms;
+        prof.launches += 1;
+    }
+    return LILAC_OK;
+}
+
+// Enqueue `nit` iterations of CG on the work set W (vectors of type T; the
+// matrix values `val` of type V).
+template <class V, class T>
+static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, int nit,
+                                  cudaStream_t s, bool profile) {
+    const int n = A->rows;
+    const int vg = vec_grid(A, n);
+    CgState* st = W.state.as<CgState>();
+    for (int it = 0; it < nit; ++it) {
+        if (profile)
+            LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it], s, cudaEventRecordExternal));
+        LILAC_TRY(launch_spmv(A, val, W.p.as<T>(), OpCgPq<V, T>{W.q.as<T>(), W.p.as<T>(), st}, s));
+        if (profile)
+            LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
+        cg_update_kernel<T><<<vg, kVecThreads, 0, s>>>(n, x, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(),
+                                                       FinCgUpdate<T>{st, nullptr}, A->scratch());
+        cg_direction_kernel<T><<<vg, kVecThreads, 0, s>>>(n, W.r.as<T>(), W.p.as<T>(), st);
+    }
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+// Run CG iterations until the device says done: either one graph of
+// max_iter iterations (no tolerance) or graphs of `chunk` iterations with a
+// host check in between.  `start` enqueues the start of the solve.
+template <class V, class T, class Start>
+static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int max_iter,
+                                bool has_tol, int chunk, bool use_graph, int kind_fixed,
+                                int kind_chunk, const void* key_b, Start&& start, cudaStream_t s,
+                                CgState* host_state, Prof& prof) {
+    LILAC_TRY(prepare_spmv<OpCgPq<V, T>>(A));
+    const uint64_t pflag = prof.on ? 1 : 0;
+    if (!has_tol) {
+        if (prof.on) LILAC_TRY(ensure_prof_events(A, max_iter));
+        GraphKey key{kind_fixed, key_b, x, max_iter, pflag, A->variant, A->vwidth, A->ws_gen};
+        LILAC_TRY(run_maybe_graph(A, key, use_graph, s, [&](cudaStream_t cs) -> lilac_status {
+            LILAC_TRY(start(cs));
+            return enqueue_iters<V, T>(A, val, x, W, max_iter, cs, prof.on);
+        }));
+        prof.kernels += 2 + 3 * max_iter;
+        if (prof.on) {
+            LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+            LILAC_TRY(collect_prof(A, max_iter, prof));
+        }
+        return LILAC_OK;
+    }
+    LILAC_TRY(start(s));
+    prof.kernels += 2;
+    if (prof.on) LILAC_TRY(ensure_prof_events(A, chunk));
+    int done_iters = 0;
+    while (done_iters < max_iter) {
+        const int nit = std::min(chunk, max_iter - done_iters);
+        GraphKey key{kind_chunk, key_b, x, nit, pflag, A->variant, A->vwidth, A->ws_gen};
+        LILAC_TRY(run_maybe_graph(A, key, use_graph, s, [&](cudaStream_t cs) {
+            return enqueue_iters<V, T>(A, val, x, W, nit, cs, prof.on);
+        }));
+        done_iters += nit;
+        prof.kernels += 3 * nit;
+        LILAC_CUDA_TRY(cudaMemcpyAsync(host_state, W.state.p, sizeof(CgState),
+                                       cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (prof.on) LILAC_TRY(collect_prof(A, nit, prof));
+        if (host_state->done) break;
+    }
+    return LILAC_OK;
+}
+
+template <class V>
+static lilac_status true_residual(lilac_csr A, const V* val, const double* b, const double* x,
+                                  CgState* st, cudaStream_t s) {
+    OpResidual<V, RES_TRUE> op{nullptr, nullptr, b, st, 0.0};
+    return launch_spmv(A, val, x, op, s);
+}
+
+// Plain FP64 CG.
+static lilac_status cg_f64(lilac_csr A, const double* b, double* x, const lilac_cg_opts& o,
+                           cudaStream_t s, CgState* hs, Prof& prof) {
+    if (A->dtype != LILAC_F64) {
+        set_last_error("FP64 CG needs an FP64 matrix (use precision 1 for FP32 values)");
+        return LILAC_ERR_DTYPE;
+    }
+    CgWork& W = A->cg64;
+    LILAC_TRY(ensure_cg_work(A, W, false));
+    const double* val = A->val.as<double>();
+    CgState* st = W.state.as<CgState>();
+    const int n = A->rows;
+    const bool has_tol = o.rtol > 0.0;
+    if (o.use_x0) LILAC_TRY(prepare_spmv<OpResidual<double, RES_INIT>>(A));
+    auto start = [&](cudaStream_t cs) -> lilac_status {
+        cg_state_reset_kernel<<<1, 1, 0, cs>>>(st, o.max_iter);
+        if (o.use_x0) {
+            OpResidual<double, RES_INIT> op{W.r.as<double>(), W.p.as<double>(), b, st, o.rtol};
+            LILAC_TRY(launch_spmv(A, val, x, op, cs));
+        } else {
+            cg_start_zero_kernel<double, double><<<vec_grid(A, n), kVecThreads, 0, cs>>>(
+                n, b, 1.0, x, W.r.as<double>(), W.p.as<double>(), FinCgStart<double>{st, o.rtol},
+                A->scratch());
+        }
+        LILAC_CUDA_TRY(cudaGetLastError());
+        return LILAC_OK;
+    };
+    LILAC_TRY(run_cg_loop<double, double>(A, val, x, W, o.max_iter, has_tol, o.check_every,
+                                          o.use_graph != 0, G_CG64_FIXED + (o.use_x0 ? 100 : 0),
+                                          G_CG64_CHUNK, b, start, s, hs, prof));
+    if (o.true_residual) {
+        LILAC_TRY(true_residual(A, val, b, x, st, s));
+        prof.kernels += 1;
+    }
+    return LILAC_OK;
+}
+
+// Mixed precision: FP64 residual r = b - A x (handle values), FP32 CG on
+// A d = r / ||r|| with FP32 values, x += ||r|| d in FP64; repeat until
+// ||r|| <= rtol ||b|| or max_iter refinements.
+static lilac_status cg_mixed(lilac_csr A, const double* b, double* x, const lilac_cg_opts& o,
+                             cudaStream_t s, CgState* hs, lilac_cg_info* info, Prof& prof) {
+    if (A->rows != A->ncols) {
+        set_last_error("CG needs a square matrix");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    LILAC_TRY(make_val32(A, s));
+    const float* val32 = A->dtype == LILAC_F32 ? A->val.as<float>() : A->val32.as<float>();
+    CgWork& W = A->cg32;
+    LILAC_TRY(ensure_cg_work(A, W, true));
+    const int n = A->rows;
+    if (!A->cg_outer_state.p) LILAC_TRY(A->ws_alloc(A->cg_outer_state, sizeof(CgState)));
+    if (!A->cg_outer_r.p || A->cg_outer_r.bytes < sizeof(double) * (size_t)std::max(1, n))
+        LILAC_TRY(A->ws_alloc(A->cg_outer_r, sizeof(double) * (size_t)std::max(1, n)));
+    if (!A->ir_x.p || A->ir_x.bytes < sizeof(float) * (size_t)std::max(1, n))
+        LILAC_TRY(A->ws_alloc(A->ir_x, sizeof(float) * (size_t)std::max(1, n)));
+    CgState* ost = A->cg_outer_state.as<CgState>();
+    double* r64 = A->cg_outer_r.as<double>();
+    float* d32 = A->ir_x.as<float>();
+    if (!o.use_x0) LILAC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+    cg_state_reset_kernel<<<1, 1, 0, s>>>(ost, o.max_iter);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    prof.kernels += 2;  // make_val32 conversion (first use) is not counted
+
+    int total_inner = 0, refinements = 0;
+    CgState outer{};
+    lilac_status result = LILAC_ERR_NOT_CONVERGED;
+    for (;;) {
+        if (A->dtype == LILAC_F64) {
+            OpResidual<double, RES_OUTER> op{r64, nullptr, b, ost, o.rtol};
+            LILAC_TRY(launch_spmv(A, A->val.as<double>(), x, op, s));
+        } else {
+            OpResidual<float, RES_OUTER> op{r64, nullptr, b, ost, o.rtol};
+            LILAC_TRY(launch_spmv(A, A->val.as<float>(), x, op, s));
+        }
+        prof.kernels += 1;
+        LILAC_CUDA_TRY(cudaMemcpyAsync(&outer, ost, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (outer.done) {
+            result = LILAC_OK;
+            break;
+        }
+        if (refinements >= o.max_iter) break;
+        // inner FP32 solve of A d = r * scale from d = 0
+        CgState* ist = W.state.as<CgState>();
+        const double scale = outer.scale;
+        auto start = [&](cudaStream_t cs) -> lilac_status {
+            cg_state_reset_kernel<<<1, 1, 0, cs>>>(ist, o.inner_max_iter);
+            cg_start_zero_kernel<float, double><<<vec_grid(A, n), kVecThreads, 0, cs>>>(
+                n, r64, scale, d32, W.r.as<float>(), W.p.as<float>(),
+                FinCgStart<float>{ist, o.inner_rtol}, A->scratch());
+            LILAC_CUDA_TRY(cudaGetLastError());
+            return LILAC_OK;
+        };
+        LILAC_TRY(run_cg_loop<float, float>(A, val32, d32, W, o.inner_max_iter, true,
+                                            o.check_every, o.use_graph != 0, G_CG32_CHUNK + 100,
+                                            G_CG32_CHUNK, r64, start, s, hs, prof));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(hs, ist, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+        total_inner += hs->iters;
+        if (hs->status == LILAC_ERR_BREAKDOWN && hs->iters == 0) {
+            result = LILAC_ERR_BREAKDOWN;
+            break;
+        }
+        ir_apply_kernel<<<vec_grid(A, n), kVecThreads, 0, s>>>(n, x, d32, ost);
+        LILAC_CUDA_TRY(cudaGetLastError());
+        prof.kernels += 1;
+        ++refinements;
+    }
+    info->iters = total_inner;
+    info->refinements = refinements;
+    info->status = result;
+    info->rel_res = outer.bb > 0.0 ? std::sqrt(outer.rr / outer.bb) : 0.0;
+    info->true_rel_res = info->rel_res;  // the outer residual is the true FP64 residual
+    return LILAC_OK;
+}
+
+}  // namespace lilac
+
+using namespace lilac;
+
+extern "C" void lilac_cg_opts_default(lilac_cg_opts* o) {
+    if (!o) return;
+    o->max_iter = 1000;
+    o->rtol = 1e-10;
+    o->precision = 0;
+    o->inner_rtol = 1e-5;
+    o->inner_max_iter = 1000;
+    o->use_x0 = 0;
+    o->true_residual = 1;
+    o->use_graph = 1;
+    o->check_every = 32;
+    o->profile = 0;
+}
+
+extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_mem where,
+                                 const lilac_cg_opts* opts, lilac_cg_info* info, void* stream) {
+    LILAC_TRY(check_handle(A));
+    lilac_cg_opts o;
+    lilac_cg_opts_default(&o);
+    if (opts) o = *opts;
+    if ((A->rows > 0 && (!b || !x)) || o.max_iter < 0 || (o.precision != 0 && o.precision != 1) ||
+        o.check_every < 1 || (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE) ||
+        (o.precision == 1 && (o.inner_max_iter < 1 || !(o.inner_rtol > 0.0)))) {
+        set_last_error("invalid argument to lilac_cg");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    if (A->rows != A->ncols) {
+        set_last_error("CG needs a square matrix");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    lilac_cg_info local{};
+    if (A->rows == 0) {
+        if (info) *info = lilac_cg_info{0, 0, LILAC_OK, 0, 0.0, 0.0, 0.0, 0, 0};
+        return LILAC_OK;
+    }
+    DeviceGuard g(A->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = A->rows;
+    const double* bd = b;
+    double* xd = x;
+    if (where == LILAC_MEM_HOST) {
+        if (!A->ir_b.p) LILAC_TRY(A->ws_alloc(A->ir_b, sizeof(double) * (size_t)n));
+        if (!A->stage_y.p || A->stage_y.bytes < sizeof(double) * (size_t)n)
+            LILAC_TRY(A->ws_alloc(A->stage_y, sizeof(double) * (size_t)n));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->ir_b.p, b, sizeof(double) * (size_t)n,
+                                       cudaMemcpyHostToDevice, s));
+        if (o.use_x0)
+            LILAC_CUDA_TRY(cudaMemcpyAsync(A->stage_y.p, x, sizeof(double) * (size_t)n,
+                                           cudaMemcpyHostToDevice, s));
+        bd = A->ir_b.as<double>();
+        xd = A->stage_y.as<double>();
+    }
+    CgState hs{};
+    lilac_status st;
+    Prof prof;
+    prof.on = o.profile != 0 && info != nullptr;
+    if (o.precision == 0) {
+        st = cg_f64(A, bd, xd, o, s, &hs, prof);
+        if (st == LILAC_OK && (info || o.rtol > 0.0 || where == LILAC_MEM_HOST)) {
+            LILAC_CUDA_TRY(cudaMemcpyAsync(&hs, A->cg64.state.p, sizeof(CgState),
+                                           cudaMemcpyDeviceToHost, s));
+            LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+            local.iters = hs.iters;
+            local.refinements = 0;
+            local.status = hs.status;
+            local.rel_res = hs.bb > 0.0 ? std::sqrt(hs.rr / hs.bb) : 0.0;
+            local.true_rel_res = (o.true_residual && hs.true_rr >= 0.0 && hs.bb > 0.0)
+                                     ? std::sqrt(hs.true_rr / hs.bb)
+                                     : (o.true_residual && hs.bb == 0.0 ? 0.0 : -1.0);
+        }
+    } else {
+        st = cg_mixed(A, bd, xd, o, s, &hs, &local, prof);
+    }
+    if (st != LILAC_OK) return st;
+    local.spmv_ms = prof.ms;
+    local.spmv_launches = prof.launches;
+    local.kernel_launches = prof.kernels;
+    if (where == LILAC_MEM_HOST) {
+        LILAC_CUDA_TRY(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    if (info || o.rtol > 0.0 || o.precision == 1) LILAC_TRY(check_device_status(A, s));
+    if (info) *info = local;
+    if (info || o.rtol > 0.0 || o.precision == 1) {
+        if (local.status == LILAC_ERR_BREAKDOWN || local.status == LILAC_ERR_NOT_CONVERGED)
+            return (lilac_status)local.status;
+    }
+    return LILAC_OK;
+}

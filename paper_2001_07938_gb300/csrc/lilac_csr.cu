@@ -1,0 +1,511 @@
+// Handle lifecycle: create (validate, upload once, cache the invariants and
+// the tile schedule), update_values, destroy, info, variant override, and
+// the status plumbing.  This is the explicit-handle form of the paper's
+// persistent harness state and marshaling (Section 3.3, Section 4.2).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.cuh"
+
+namespace lilac {
+
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+lilac_status DevBuf::alloc(size_t n) {
+    release();
+    if (n == 0) return LILAC_OK;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        (void)cudaGetLastError();
+        set_last_error(std::string("cudaMalloc(") + std::to_string(n) + "): " + cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? LILAC_ERR_OOM : LILAC_ERR_CUDA;
+    }
+    bytes = n;
+    return LILAC_OK;
+}
+
+void DevBuf::release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+}
+
+DeviceGuard::DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+}
+
+DeviceGuard::~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+}
+
+lilac_status check_handle(lilac_csr A) {
+    if (!A) {
+        set_last_error("NULL handle");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    if (A->sticky_error) {
+        set_last_error("handle has a device timeout recorded; call lilac_csr_reset_error");
+        return LILAC_ERR_TIMEOUT;
+    }
+    return LILAC_OK;
+}
+
+// Read the device error word (synchronizes `stream`).
+lilac_status check_device_status(lilac_csr A, cudaStream_t stream) {
+    int st = 0;
+    LILAC_CUDA_TRY(cudaMemcpyAsync(&st, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
+    if (st != DEV_OK) {
+        A->sticky_error = true;
+        set_last_error("a device-side bounded wait timed out");
+        return LILAC_ERR_TIMEOUT;
+    }
+    return LILAC_OK;
+}
+
+// Column range check and max(col_ind) (the ncols invariant).  out[0] = max
+// column, out[1] = 1 if some column is negative or >= ncols (ncols >= 0).
+__global__ void csr_columns_kernel(int64_t nnz, const int* __restrict__ col, int ncols, int* out) {
+    int mx = -1, bad = 0;
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const int c = col[k];
+        mx = c > mx ? c : mx;
+        if (c < 0 || (ncols >= 0 && c >= ncols)) bad = 1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(out, mx);
+        if (bad) atomicOr(out + 1, 1);
+    }
+}
+
+__global__ void f64_to_f32_kernel(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+lilac_status make_val32(lilac_csr A, cudaStream_t stream) {
+    if (A->dtype == LILAC_F32 || A->val32_valid) return LILAC_OK;
+    if (!A->val32.p) LILAC_TRY(A->ws_alloc(A->val32, sizeof(float) * (size_t)((A->nnz + 11) & ~3ll)));
+    if (A->nnz > 0) {
+        f64_to_f32_kernel<<<A->sm_count * 4, 256, 0, stream>>>(A->nnz, A->val.as<double>(),
+                                                               A->val32.as<float>());
+        LILAC_CUDA_TRY(cudaGetLastError());
+    }
+    A->val32_valid = true;
+    return LILAC_OK;
+}
+
+// Grid of the elementwise vector kernels: up to 8 CTAs of 256 threads per SM.
+int vec_grid(const lilac_csr_s* A, int64_t n) {
+    int64_t need = (n + 255) / 256;
+    int64_t g = (int64_t)A->sm_count * 8;
+    return (int)std::max<int64_t>(1, std::min(g, need));
+}
+
+// Greedy row tiles: consecutive rows while the tile holds at most kTileNnz
+// nonzeros and kTileRows rows; a row longer than kTileNnz becomes its own
+// chunks of kTileNnz nonzeros.
+static void build_tiles(const std::vector<int32_t>& rp, int rows, std::vector<TileDesc>& tiles,
+                        std::vector<LongRow>& longs, int& nchunks) {
+    tiles.clear();
+    longs.clear();
+    nchunks = 0;
+    int r = 0;
+    while (r < rows) {
+        const int len = rp[r + 1] - rp[r];
+        if (len > kTileNnz) {
+            const int lid = (int)longs.size();
+            const int nch = (len + kTileNnz - 1) / kTileNnz;
+            longs.push_back({r, nchunks, nch, 0});
+            for (int c = 0; c < nch; ++c) {
+                const int k0 = rp[r] + c * kTileNnz;
+                const int k1 = std::min(rp[r + 1], k0 + kTileNnz);
+                tiles.push_back({lid, -(nchunks + c) - 1, k0, k1});
+            }
+            nchunks += nch;
+            ++r;
+            continue;
+        }
+        const int r0 = r;
+        const int k0 = rp[r];
+        while (r < rows && (r - r0) < kTileRows && rp[r + 1] - k0 <= kTileNnz) ++r;
+        tiles.push_back({r0, r, k0, rp[r]});
+    }
+}
+
+// Lanes per row from the mean row length: the smallest power of two >= mean/2.
+static int pick_width(double mean) {
+    int v = 1;
+    while (v < 32 && v < mean / 2.0) v *= 2;
+    return v;
+}
+
+}  // namespace lilac
+
+using namespace lilac;
+
+lilac::Scratch lilac_csr_s::scratch() const {
+    Scratch s;
+    s.partials = partials.as<double>();
+    s.long_part = long_part.as<double>();
+    s.long_red = long_red.as<double>();
+    s.long_cnt = long_cnt.as<unsigned>();
+    s.ticket = ticket.as<unsigned>();
+    s.status = status.as<int>();
+    return s;
+}
+
+int64_t lilac_csr_s::device_bytes() const {
+    const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
+                                  &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
+                                  &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
+                                  &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
+                                  &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out};
+    int64_t t = 0;
+    for (auto* b : all) t += (int64_t)b->bytes;
+    return t;
+}
+
+static lilac_status zero_scratch(lilac_csr A, cudaStream_t stream) {
+    lilac::DevBuf* bufs[] = {&A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
+                             &A->status};
+    for (auto* b : bufs)
+        if (b->p) LILAC_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, stream));
+    return LILAC_OK;
+}
+
+static lilac_status tune_timed(lilac_csr A, cudaStream_t stream);
+
+static lilac_status create_impl(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
+                                const int32_t* col_ind, const void* vals, lilac_dtype dtype,
+                                lilac_mem where, uint32_t flags, cudaStream_t stream,
+                                lilac_csr A) {
+    const size_t vsz = dtype == LILAC_F64 ? 8 : 4;
+    // host copy of row_ptr: validation, statistics and the tile schedule
+    A->h_row_ptr.resize((size_t)rows + 1);
+    if (where == LILAC_MEM_HOST) {
+        std::memcpy(A->h_row_ptr.data(), row_ptr, sizeof(int32_t) * ((size_t)rows + 1));
+    } else {
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->h_row_ptr.data(), row_ptr,
+                                       sizeof(int32_t) * ((size_t)rows + 1), cudaMemcpyDeviceToHost,
+                                       stream));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
+    }
+    const auto& rp = A->h_row_ptr;
+    if (rp[0] != 0 || (int64_t)rp[rows] != nnz) {
+        set_last_error("row_ptr[0] must be 0 and row_ptr[rows] must equal nnz");
+        return LILAC_ERR_INVALID_CSR;
+    }
+    int32_t maxlen = 0, empty = 0;
+    double sum2 = 0.0;
+    for (int32_t i = 0; i < rows; ++i) {
+        const int32_t len = rp[i + 1] - rp[i];
+        if (len < 0) {
+            set_last_error("row_ptr decreases at row " + std::to_string(i));
+            return LILAC_ERR_INVALID_CSR;
+        }
+        maxlen = std::max(maxlen, len);
+        empty += len == 0;
+        sum2 += (double)len * (double)len;
+    }
+    A->max_row_len = maxlen;
+    A->empty_rows = empty;
+    A->mean_row_len = rows ? (double)nnz / rows : 0.0;
+    A->std_row_len =
+        rows ? std::sqrt(std::max(0.0, sum2 / rows - A->mean_row_len * A->mean_row_len)) : 0.0;
+
+    // device arrays, padded for 16-byte-rounded bulk copies
+    const size_t nnz_pad = (size_t)((nnz + 11) & ~3ll);
+    const size_t rp_pad = (size_t)(((int64_t)rows + 1 + 11) & ~3ll);
+    LILAC_TRY(A->row_ptr.alloc(sizeof(int32_t) * rp_pad));
+    LILAC_TRY(A->col_ind.alloc(sizeof(int32_t) * nnz_pad));
+    LILAC_TRY(A->val.alloc(vsz * nnz_pad));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->row_ptr.p, 0, A->row_ptr.bytes, stream));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->col_ind.p, 0, A->col_ind.bytes, stream));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->val.p, 0, A->val.bytes, stream));
+    const cudaMemcpyKind kind =
+        where == LILAC_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+    LILAC_CUDA_TRY(cudaMemcpyAsync(A->row_ptr.p, rp.data(), sizeof(int32_t) * ((size_t)rows + 1),
+                                   cudaMemcpyHostToDevice, stream));
+    if (nnz > 0) {
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->col_ind.p, col_ind, sizeof(int32_t) * (size_t)nnz, kind, stream));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->val.p, vals, vsz * (size_t)nnz, kind, stream));
+    }
+    A->h2d_bytes += (int64_t)(sizeof(int32_t) * ((size_t)rows + 1) + (sizeof(int32_t) + vsz) * (size_t)nnz);
+
+    // column validation and the ncols invariant, on the device
+    lilac::DevBuf colres;
+    LILAC_TRY(colres.alloc(2 * sizeof(int)));
+    int init[2] = {-1, 0};
+    LILAC_CUDA_TRY(cudaMemcpyAsync(colres.p, init, sizeof(init), cudaMemcpyHostToDevice, stream));
+    if (nnz > 0) {
+        csr_columns_kernel<<<A->sm_count * 4, 256, 0, stream>>>(nnz, A->col_ind.as<int>(), ncols,
+                                                               colres.as<int>());
+        LILAC_CUDA_TRY(cudaGetLastError());
+    }
+    int res[2];
+    LILAC_CUDA_TRY(cudaMemcpyAsync(res, colres.p, sizeof(res), cudaMemcpyDeviceToHost, stream));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
+    colres.release();
+    if (res[1]) {
+        set_last_error("col_ind holds an index outside [0, ncols)");
+        return LILAC_ERR_INVALID_CSR;
+    }
+    A->ncols = ncols >= 0 ? ncols : res[0] + 1;
+
+    // STAGED tile schedule
+    std::vector<TileDesc> tiles;
+    std::vector<LongRow> longs;
+    build_tiles(rp, rows, tiles, longs, A->nlong_chunks);
+    A->ntiles = (int)tiles.size();
+    A->nlong = (int)longs.size();
+    if (A->ntiles) {
+        LILAC_TRY(A->tiles.alloc(sizeof(TileDesc) * tiles.size()));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->tiles.p, tiles.data(), sizeof(TileDesc) * tiles.size(),
+                                       cudaMemcpyHostToDevice, stream));
+    }
+    if (A->nlong) {
+        LILAC_TRY(A->longs.alloc(sizeof(LongRow) * longs.size()));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->longs.p, longs.data(), sizeof(LongRow) * longs.size(),
+                                       cudaMemcpyHostToDevice, stream));
+    }
+    // scratch
+    LILAC_TRY(A->partials.alloc(sizeof(double) * kMaxCtas * kMaxRed));
+    LILAC_TRY(A->long_part.alloc(sizeof(double) * std::max(1, A->nlong_chunks)));
+    LILAC_TRY(A->long_red.alloc(sizeof(double) * kMaxRed * std::max(1, A->nlong)));
+    LILAC_TRY(A->long_cnt.alloc(sizeof(unsigned) * std::max(1, A->nlong)));
+    LILAC_TRY(A->ticket.alloc(sizeof(unsigned) * 4));
+    LILAC_TRY(A->status.alloc(sizeof(int) * 4));
+    LILAC_TRY(zero_scratch(A, stream));
+
+    // autotuner: heuristic from the row statistics
+    A->variant = LILAC_VARIANT_STAGED;
+    A->vwidth = pick_width(A->mean_row_len);
+    if (flags & LILAC_CREATE_TUNE_TIMED) LILAC_TRY(tune_timed(A, stream));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
+    return LILAC_OK;
+}
+
+// Time each candidate (variant, width) once on this matrix and keep the
+// fastest: the one-off tuning phase of an autotuning library (SparseX,
+// Section 5), paid at create like the paper's cached invariants.
+static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
+    if (A->rows == 0 || A->nnz == 0) return LILAC_OK;
+    const size_t vsz = A->dtype == LILAC_F64 ? 8 : 4;
+    lilac::DevBuf x, y;
+    LILAC_TRY(x.alloc(vsz * (size_t)std::max(1, A->ncols)));
+    LILAC_TRY(y.alloc(vsz * (size_t)A->rows));
+    LILAC_CUDA_TRY(cudaMemsetAsync(x.p, 0, x.bytes, stream));
+    struct Cand { int variant, width; };
+    std::vector<Cand> cands;
+    const int w0 = pick_width(A->mean_row_len);
+    for (int w : {w0 / 2, w0, w0 * 2})
+        if (w >= 1 && w <= 32) cands.push_back({LILAC_VARIANT_STAGED, w});
+    cands.push_back({LILAC_VARIANT_SCALAR, 1});
+    for (int w : {w0, w0 * 2})
+        if (w >= 2 && w <= 32) cands.push_back({LILAC_VARIANT_VECTOR, w});
+    cudaEvent_t e0, e1;
+    LILAC_CUDA_TRY(cudaEventCreate(&e0));
+    LILAC_CUDA_TRY(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Cand bestc{A->variant, A->vwidth};
+    for (const Cand& c : cands) {
+        A->variant = c.variant;
+        A->vwidth = c.width;
+        lilac_status st = LILAC_OK;
+        auto run = [&]() {
+            if (A->dtype == LILAC_F64)
+                st = launch_spmv(A, A->val.as<double>(), x.as<double>(), OpStore<double, double>{y.as<double>()}, stream);
+            else
+                st = launch_spmv(A, A->val.as<float>(), x.as<float>(), OpStore<float, float>{y.as<float>()}, stream);
+        };
+        run();  // warm-up
+        LILAC_CUDA_TRY(cudaEventRecord(e0, stream));
+        for (int it = 0; it < 5 && st == LILAC_OK; ++it) run();
+        LILAC_CUDA_TRY(cudaEventRecord(e1, stream));
+        LILAC_CUDA_TRY(cudaEventSynchronize(e1));
+        if (st != LILAC_OK) continue;
+        float ms = 0.f;
+        LILAC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    A->variant = bestc.variant;
+    A->vwidth = bestc.width;
+    return LILAC_OK;
+}
+
+static void free_handle(lilac_csr A) {
+    for (auto& kv : A->graphs) cudaGraphExecDestroy(kv.second);
+    A->graphs.clear();
+    for (cudaEvent_t e : A->prof_events) cudaEventDestroy(e);
+    A->prof_events.clear();
+    if (A->capture_stream) cudaStreamDestroy(A->capture_stream);
+    lilac::DevBuf* all[] = {&A->row_ptr, &A->col_ind, &A->val, &A->val32, &A->tiles, &A->longs,
+                            &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
+                            &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
+                            &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
+                            &A->cg32.state, &A->cg_outer_state, &A->cg_outer_r, &A->ir_x, &A->ir_b,
+                            &A->pr_y, &A->pr_state, &A->pr_l1, &A->pr_has_out};
+    for (auto* b : all) b->release();
+    delete A;
+}
+
+extern "C" {
+
+lilac_status lilac_csr_create(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
+                              const int32_t* col_ind, const void* vals, lilac_dtype dtype,
+                              lilac_mem where, uint32_t flags, void* stream, lilac_csr* out) {
+    if (!out) {
+        set_last_error("out is NULL");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (rows < 0 || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr ||
+        (nnz > 0 && (!col_ind || !vals)) || (dtype != LILAC_F64 && dtype != LILAC_F32) ||
+        (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE)) {
+        set_last_error("invalid argument to lilac_csr_create");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    int dev = 0;
+    LILAC_CUDA_TRY(cudaGetDevice(&dev));
+    lilac_csr A = new lilac_csr_s();
+    A->device = dev;
+    A->rows = rows;
+    A->nnz = nnz;
+    A->dtype = dtype;
+    if (cudaDeviceGetAttribute(&A->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        A->sm_count <= 0)
+        A->sm_count = 1;
+    lilac_status st = create_impl(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, where, flags,
+                                  static_cast<cudaStream_t>(stream), A);
+    if (st != LILAC_OK) {
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        free_handle(A);
+        return st;
+    }
+    *out = A;
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem where, void* stream) {
+    LILAC_TRY(check_handle(A));
+    if ((A->nnz > 0 && !vals) || (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE)) {
+        set_last_error("invalid argument to lilac_csr_update_values");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(A->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t vsz = A->dtype == LILAC_F64 ? 8 : 4;
+    if (A->nnz > 0)
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->val.p, vals, vsz * (size_t)A->nnz,
+                                       where == LILAC_MEM_HOST ? cudaMemcpyHostToDevice
+                                                               : cudaMemcpyDeviceToDevice,
+                                       s));
+    A->h2d_bytes += (int64_t)(vsz * (size_t)A->nnz);
+    A->val32_valid = false;  // derived FP32 copy is stale
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_destroy(lilac_csr A) {
+    if (!A) return LILAC_OK;
+    DeviceGuard g(A->device);
+    cudaDeviceSynchronize();
+    free_handle(A);
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) {
+    if (!A || !info) {
+        set_last_error("NULL argument to lilac_csr_info");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    info->rows = A->rows;
+    info->ncols = A->ncols;
+    info->nnz = A->nnz;
+    info->dtype = A->dtype;
+    info->variant = A->variant;
+    info->vector_width = A->vwidth;
+    info->max_row_len = A->max_row_len;
+    info->empty_rows = A->empty_rows;
+    info->num_tiles = A->ntiles;
+    info->num_long_rows = A->nlong;
+    info->sm_count = A->sm_count;
+    info->mean_row_len = A->mean_row_len;
+    info->std_row_len = A->std_row_len;
+    info->device_bytes = A->device_bytes();
+    info->h2d_bytes = A->h2d_bytes;
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width) {
+    if (!A) {
+        set_last_error("NULL handle");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_STAGED ||
+        (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
+                               (vector_width & (vector_width - 1)) != 0))) {
+        set_last_error("unsupported variant / width");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    A->variant = variant;
+    if (vector_width) A->vwidth = vector_width;
+    if (variant == LILAC_VARIANT_SCALAR) A->vwidth = 1;
+    if (variant == LILAC_VARIANT_VECTOR && A->vwidth < 2) A->vwidth = 2;
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_reset_error(lilac_csr A) {
+    if (!A) {
+        set_last_error("NULL handle");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(A->device);
+    LILAC_TRY(zero_scratch(A, nullptr));
+    LILAC_CUDA_TRY(cudaDeviceSynchronize());
+    A->sticky_error = false;
+    return LILAC_OK;
+}
+
+const char* lilac_status_string(lilac_status s) {
+    switch (s) {
+        case LILAC_OK: return "ok";
+        case LILAC_ERR_INVALID_ARG: return "invalid argument";
+        case LILAC_ERR_INVALID_CSR: return "invalid CSR structure";
+        case LILAC_ERR_OOM: return "out of device memory";
+        case LILAC_ERR_BUDGET: return "over the device-memory budget";
+        case LILAC_ERR_CUDA: return "CUDA error";
+        case LILAC_ERR_BREAKDOWN: return "CG breakdown (p.Ap <= 0 or not finite)";
+        case LILAC_ERR_NOT_CONVERGED: return "not converged";
+        case LILAC_ERR_TIMEOUT: return "device wait timed out";
+        case LILAC_ERR_DTYPE: return "wrong value type for this operation";
+        case LILAC_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char* lilac_last_error(void) { return g_last_error.c_str(); }
+
+int32_t lilac_version(void) { return 10000; }
+
+}  // extern "C"

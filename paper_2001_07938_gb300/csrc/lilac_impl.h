@@ -1,0 +1,139 @@
+// Internal host-side definitions: the handle, error plumbing, device
+// buffers, and the SpMV launch dispatcher shared by the entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/lilac.h"
+#include "ops.cuh"
+
+namespace lilac {
+
+// Tile shape of the STAGED kernel: at most kTileNnz nonzeros and kTileRows
+// rows per tile; 256 threads per CTA.
+constexpr int kStagedThreads = 256;
+constexpr int kTileNnz = 2048;
+constexpr int kTileRows = 1024;
+constexpr int kRowsThreads = 256;
+constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
+
+void set_last_error(const std::string& msg);
+
+#define LILAC_CUDA_TRY(...)                                                                   \
+    do {                                                                                      \
+        cudaError_t _e = (__VA_ARGS__);                                                       \
+        if (_e != cudaSuccess) {                                                              \
+            ::lilac::set_last_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(_e)); \
+            return _e == cudaErrorMemoryAllocation ? LILAC_ERR_OOM : LILAC_ERR_CUDA;          \
+        }                                                                                     \
+    } while (0)
+
+#define LILAC_TRY(...)                        \
+    do {                                      \
+        lilac_status _s = (__VA_ARGS__);      \
+        if (_s != LILAC_OK) return _s;        \
+    } while (0)
+
+// Device allocation owned by a handle.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    lilac_status alloc(size_t n);
+    void release();
+    template <class T>
+    T* as() const { return static_cast<T*>(p); }
+};
+
+struct CgWork {
+    int n = 0;
+    bool f32 = false;
+    DevBuf r, p, q, state;  // vectors of the handle's CG precision; state = CgState
+};
+
+struct GraphKey {
+    int kind;
+    const void* a;
+    const void* b;
+    int iters;
+    uint64_t extra;
+    int variant;
+    int vwidth;
+    uint64_t gen;  // workspace generation of the handle at capture time
+    bool operator<(const GraphKey& o) const {
+        return std::tie(kind, a, b, iters, extra, variant, vwidth, gen) <
+               std::tie(o.kind, o.a, o.b, o.iters, o.extra, o.variant, o.vwidth, o.gen);
+    }
+};
+
+}  // namespace lilac
+
+struct lilac_csr_s {
+    int device = 0;
+    int sm_count = 0;
+    int32_t rows = 0, ncols = 0;
+    int64_t nnz = 0;
+    lilac_dtype dtype = LILAC_F64;
+    // matrix (padded so that 16-byte-rounded bulk copies stay inside)
+    lilac::DevBuf row_ptr, col_ind, val;
+    lilac::DevBuf val32;  // FP32 copy of FP64 values, built on first mixed-precision use
+    bool val32_valid = false;
+    // row statistics (the invariants cached at create)
+    int32_t max_row_len = 0, empty_rows = 0;
+    double mean_row_len = 0.0, std_row_len = 0.0;
+    // kernel choice
+    int variant = LILAC_VARIANT_STAGED;
+    int vwidth = 32;
+    // STAGED schedule
+    lilac::DevBuf tiles, longs;
+    int ntiles = 0, nlong = 0, nlong_chunks = 0;
+    // scratch
+    lilac::DevBuf partials, long_part, long_red, long_cnt, ticket, status;
+    // host-pointer staging (marshaling of x / y for LILAC_MEM_HOST calls)
+    lilac::DevBuf stage_x, stage_y;
+    // solvers
+    lilac::CgWork cg64, cg32;
+    lilac::DevBuf cg_outer_state, cg_outer_r, ir_x, ir_b;  // mixed precision outer loop
+    lilac::DevBuf pr_y, pr_state, pr_l1, pr_has_out;
+    bool pr_has_out_valid = false;
+    cudaStream_t capture_stream = nullptr;
+    std::map<lilac::GraphKey, cudaGraphExec_t> graphs;
+    std::vector<cudaEvent_t> prof_events;  // pairs around timed SpMV launches
+    // host copies
+    std::vector<int32_t> h_row_ptr;
+    int64_t h2d_bytes = 0;
+    bool sticky_error = false;
+    uint64_t ws_gen = 0;  // bumped whenever a buffer a captured graph may use is reallocated
+
+    // (Re)allocate a workspace buffer; cached graphs that used the old one
+    // stop matching.
+    lilac_status ws_alloc(lilac::DevBuf& b, size_t bytes) {
+        ++ws_gen;
+        return b.alloc(bytes);
+    }
+
+    lilac::Scratch scratch() const;
+    int64_t device_bytes() const;
+};
+
+namespace lilac {
+
+// Switch to the handle's device for the duration of a call.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev);
+    ~DeviceGuard();
+};
+
+lilac_status check_handle(lilac_csr A);
+lilac_status make_val32(lilac_csr A, cudaStream_t stream);
+lilac_status check_device_status(lilac_csr A, cudaStream_t stream);
+int vec_grid(const lilac_csr_s* A, int64_t n);
+
+}  // namespace lilac

@@ -1,0 +1,308 @@
+// Epilogues fused into the SpMV kernels, and the vector kernels of the CG
+// and PageRank loops.  Device scalars live in small state structs so that a
+// whole solve runs without the host reading anything between iterations.
+#pragma once
+
+#include <cmath>
+
+#include "../../include/lilac.h"
+#include "spmv_kernels.cuh"
+
+namespace lilac {
+
+// ---------------------------------------------------------------------------
+// Plain y = A x.
+template <class V, class T>
+struct OpStore {
+    using ValT = V;
+    using VecT = T;
+    using AccT = T;
+    static constexpr int NR = 0;
+    T* __restrict__ y;
+    __device__ bool skip() const { return false; }
+    __device__ void row(int r, AccT s, double*) const { y[r] = s; }
+    __device__ void finish(const double*) const {}
+};
+
+// ---------------------------------------------------------------------------
+// Conjugate gradient (Hestenes-Stiefel).  State of one solve on the device.
+struct CgState {
+    double rr;       // r.r of the current residual
+    double pq;       // p.Ap of the last iteration
+    double alpha;
+    double beta;
+    double bb;       // b.b (right-hand side of this solve)
+    double tol2;     // stop when rr <= tol2 (negative: never)
+    double true_rr;  // ||b - A x||^2 recomputed at the end (if asked)
+    double scale;    // mixed precision: 1 / ||r_outer|| used to scale the inner rhs
+    int iters;       // iterations completed
+    int max_iter;
+    int done;        // 1: later iteration kernels are no-ops
+    int status;      // lilac_status of the solve so far
+};
+
+__device__ __forceinline__ bool cg_done(const CgState* st) {
+    return *reinterpret_cast<const volatile int*>(&st->done) != 0;
+}
+
+// q = A p with p.q fused: after the grid sum, alpha = rr / p.q.
+template <class V, class T>
+struct OpCgPq {
+    using ValT = V;
+    using VecT = T;
+    using AccT = T;
+    static constexpr int NR = 1;
+    T* __restrict__ q;
+    const T* __restrict__ p;
+    CgState* st;
+    __device__ bool skip() const { return cg_done(st); }
+    __device__ void row(int r, AccT s, double* red) const {
+        q[r] = s;
+        red[0] += double(p[r]) * double(s);
+    }
+    __device__ void finish(const double* tot) const {
+        const double pq = tot[0];
+        st->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            st->status = LILAC_ERR_BREAKDOWN;
+            st->done = 1;
+        } else {
+            st->alpha = st->rr / pq;
+        }
+    }
+};
+
+// Residual r = b - A x in FP64 (values of any type promoted), with r.r and
+// b.b.  Mode INIT starts a CG solve from x0 (also p = r); mode TRUE only
+// records ||b - A x||^2; mode OUTER starts a refinement step (r kept in
+// FP64, scale = 1/||r||, convergence test against rtol ||b||).
+enum ResidualMode { RES_INIT = 0, RES_TRUE = 1, RES_OUTER = 2 };
+
+template <class V, int MODE>
+struct OpResidual {
+    using ValT = V;
+    using VecT = double;
+    using AccT = double;
+    static constexpr int NR = 2;
+    double* __restrict__ r;
+    double* __restrict__ p;  // INIT only
+    const double* __restrict__ b;
+    CgState* st;
+    double rtol;
+    __device__ bool skip() const { return false; }
+    __device__ void row(int i, AccT s, double* red) const {
+        const double bi = b[i];
+        const double ri = bi - s;
+        if (MODE != RES_TRUE) r[i] = ri;
+        if (MODE == RES_INIT) p[i] = ri;
+        red[0] += ri * ri;
+        red[1] += bi * bi;
+    }
+    __device__ void finish(const double* tot) const {
+        if (MODE == RES_TRUE) {
+            st->true_rr = tot[0];
+            st->bb = tot[1];
+            return;
+        }
+        st->rr = tot[0];
+        st->bb = tot[1];
+        st->tol2 = rtol > 0.0 ? rtol * rtol * tot[1] : -1.0;
+        st->iters = 0;
+        if (MODE == RES_OUTER) {
+            st->scale = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
+            const bool conv = tot[0] == 0.0 || tot[0] <= st->tol2;
+            st->done = conv ? 1 : 0;
+            st->status = conv ? LILAC_OK : LILAC_ERR_NOT_CONVERGED;
+        } else {
+            const bool conv = tot[0] == 0.0 || (st->tol2 >= 0.0 && tot[0] <= st->tol2);
+            st->done = conv ? 1 : 0;
+            st->status = conv ? LILAC_OK : LILAC_ERR_NOT_CONVERGED;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Vector kernels of CG.  Persistent grid-stride loops; grid sums through the
+// ticket.  THREADS is fixed at 256.
+constexpr int kVecThreads = 256;
+
+struct FinNone {
+    __device__ void finish(const double*) const {}
+};
+
+// x = 0, r = b, p = b (cast to T), rr = b.b: start of a solve from x0 = 0.
+template <class T>
+struct FinCgStart {
+    CgState* st;
+    double rtol;
+    __device__ void finish(const double* tot) const {
+        st->rr = tot[0];
+        st->bb = tot[0];
+        st->tol2 = rtol > 0.0 ? rtol * rtol * tot[0] : -1.0;
+        st->iters = 0;
+        const bool conv = tot[0] == 0.0;
+        st->done = conv ? 1 : 0;
+        st->status = conv ? LILAC_OK : LILAC_ERR_NOT_CONVERGED;
+    }
+};
+
+template <class T, class TB>
+static __global__ void __launch_bounds__(kVecThreads)
+    cg_start_zero_kernel(int n, const TB* __restrict__ b, double bscale, T* __restrict__ x,
+                         T* __restrict__ r, T* __restrict__ p, FinCgStart<T> fin, Scratch s) {
+    double red[1] = {0.0};
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+        const T bi = T(double(b[i]) * bscale);
+        x[i] = T(0);
+        r[i] = bi;
+        p[i] = bi;
+        red[0] += double(bi) * double(bi);
+    }
+    grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
+}
+
+// x += alpha p;  r -= alpha q;  rr_new = r.r  ->  beta, convergence test.
+template <class T>
+struct FinCgUpdate {
+    CgState* st;
+    double* rr_hist;  // nullable, max_iter + 1 entries
+    __device__ void finish(const double* tot) const {
+        const double rr_new = tot[0];
+        const int it = st->iters + 1;
+        st->iters = it;
+        if (rr_hist) rr_hist[it] = rr_new;
+        st->beta = rr_new / st->rr;
+        st->rr = rr_new;
+        if (rr_new == 0.0 || (st->tol2 >= 0.0 && rr_new <= st->tol2)) {
+            st->done = 1;
+            st->status = LILAC_OK;
+        } else if (it >= st->max_iter) {
+            st->done = 1;
+            st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+        }
+    }
+};
+
+template <class T>
+static __global__ void __launch_bounds__(kVecThreads)
+    cg_update_kernel(int n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
+                     const T* __restrict__ q, FinCgUpdate<T> fin, Scratch s) {
+    if (cg_done(fin.st)) return;
+    const T alpha = T(fin.st->alpha);
+    double red[1] = {0.0};
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+        x[i] += alpha * p[i];
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        red[0] += double(ri) * double(ri);
+    }
+    grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
+}
+
+// p = r + beta p.
+template <class T>
+static __global__ void __launch_bounds__(kVecThreads)
+    cg_direction_kernel(int n, const T* __restrict__ r, T* __restrict__ p, const CgState* st) {
+    if (cg_done(st)) return;
+    const T beta = T(st->beta);
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
+        p[i] = r[i] + beta * p[i];
+}
+
+// Mixed precision: x += d / scale (FP64), after an inner FP32 solve of
+// A d = scale * r.
+static __global__ void __launch_bounds__(kVecThreads)
+    ir_apply_kernel(int n, double* __restrict__ x, const float* __restrict__ d, const CgState* outer) {
+    const double inv = 1.0 / outer->scale;
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
+        x[i] += double(d[i]) * inv;
+}
+
+// ---------------------------------------------------------------------------
+// PageRank.
+struct PrState {
+    double teleport;  // (d * D + 1 - d) / N for the next iteration
+    double dangling;  // D of the vector the next iteration reads
+    int iter;         // iterations completed
+    int pad;
+};
+
+// has_out bit j set <=> column j holds an entry <=> vertex j has an out-edge.
+static __global__ void __launch_bounds__(kVecThreads)
+    mark_columns_kernel(int64_t nnz, const int* __restrict__ col_ind, unsigned* __restrict__ has_out) {
+    for (int64_t k = blockIdx.x * (int64_t)kVecThreads + threadIdx.x; k < nnz;
+         k += (int64_t)gridDim.x * kVecThreads) {
+        const int c = col_ind[k];
+        const unsigned bit = 1u << (c & 31);
+        if ((__ldg(has_out + (c >> 5)) & bit) == 0u) atomicOr(has_out + (c >> 5), bit);
+    }
+}
+
+__device__ __forceinline__ bool is_dangling(const unsigned* has_out, int j) {
+    return ((__ldg(has_out + (j >> 5)) >> (j & 31)) & 1u) == 0u;
+}
+
+struct FinPrStart {
+    PrState* st;
+    double damping;
+    int n;
+    __device__ void finish(const double* tot) const {
+        st->dangling = tot[0];
+        st->teleport = (damping * tot[0] + (1.0 - damping)) / double(n);
+        st->iter = 0;
+    }
+};
+
+// Optionally x = 1/N; D = sum of x over dangling vertices.
+template <class T>
+static __global__ void __launch_bounds__(kVecThreads)
+    pr_start_kernel(int n, T* __restrict__ x, int init_uniform, const unsigned* __restrict__ has_out,
+                    FinPrStart fin, Scratch s) {
+    double red[1] = {0.0};
+    const T u = T(1.0 / double(n));
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+        T xi;
+        if (init_uniform) {
+            xi = u;
+            x[i] = u;
+        } else {
+            xi = x[i];
+        }
+        if (is_dangling(has_out, i)) red[0] += double(xi);
+    }
+    grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
+}
+
+// y = d (A x) + teleport; L1 += |y - x|; D' += y over dangling rows.
+template <class V, class T>
+struct OpPageRank {
+    using ValT = V;
+    using VecT = T;
+    using AccT = T;
+    static constexpr int NR = 2;
+    T* __restrict__ y;
+    const T* __restrict__ x;
+    const unsigned* __restrict__ has_out;
+    PrState* st;
+    double* l1;  // device, one entry per iteration
+    T damping;
+    int n;
+    __device__ bool skip() const { return false; }
+    __device__ void row(int r, AccT s, double* red) const {
+        // written by the previous launch; this launch's finish() runs after every row()
+        const T tele = T(__ldcg(&st->teleport));
+        const T yi = damping * s + tele;
+        y[r] = yi;
+        red[0] += fabs(double(yi) - double(x[r]));
+        if (is_dangling(has_out, r)) red[1] += double(yi);
+    }
+    __device__ void finish(const double* tot) const {
+        const int t = st->iter;
+        l1[t] = tot[0];
+        st->dangling = tot[1];
+        st->teleport = (double(damping) * tot[1] + (1.0 - double(damping))) / double(n);
+        st->iter = t + 1;
+    }
+};
+
+}  // namespace lilac

@@ -1,0 +1,248 @@
+// CSR SpMV kernels, y = A x (the paper's spmv_csr, Section 3.2):
+//   y[i] = sum_{row_ptr[i] <= j < row_ptr[i+1]} val[j] * x[col_ind[j]].
+//
+// Every kernel hands each finished row sum to an epilogue `Op`, which stores
+// y (or a fused CG / PageRank / residual update) and may add up to kMaxRed
+// FP64 values per row into grid-wide sums.  Grid sums end in the last-CTA
+// ticket of lilac_device.cuh, so a launch with reductions needs no second
+// kernel, and every sum is taken in an order fixed by the launch shape.
+//
+// Op concept:
+//   using ValT (matrix value type), VecT (x / y type), AccT (row accumulator)
+//   static constexpr int NR                 number of FP64 reductions (0..kMaxRed)
+//   __device__ bool skip() const            true: the whole launch is a no-op
+//   __device__ void row(int r, AccT s, double* red) const
+//   __device__ void finish(const double* tot) const   (last CTA, thread 0; NR > 0)
+#pragma once
+
+#include "lilac_device.cuh"
+
+namespace lilac {
+
+template <class ValT>
+struct CsrView {
+    const int* __restrict__ row_ptr;
+    const int* __restrict__ col_ind;
+    const ValT* __restrict__ val;
+    int rows;
+};
+
+// One tile of the STAGED kernel.  Row tile: rows [r0, r1) whose nonzeros
+// [k0, k1) are contiguous.  Split-row chunk (r1 < 0): nonzeros [k0, k1) of
+// split row number r0, written to chunk slot -r1 - 1.
+struct TileDesc {
+    int r0, r1, k0, k1;
+};
+
+struct LongRow {
+    int row, first_slot, nchunks, pad;
+};
+
+// ---------------------------------------------------------------------------
+// SCALAR (V = 1) and VECTOR (V lanes per row) kernels: rows in a grid-stride
+// loop straight from global memory; V = 32 is warp-per-row.
+
+template <int V, int THREADS, class Op>
+__global__ void __launch_bounds__(THREADS)
+    spmv_rows_kernel(CsrView<typename Op::ValT> A, const typename Op::VecT* __restrict__ x,
+                     Op op, Scratch s) {
+    if (op.skip()) return;
+    using AccT = typename Op::AccT;
+    constexpr int NR = Op::NR;
+    double red[NR > 0 ? NR : 1] = {};
+    const int lane = threadIdx.x & (V - 1);
+    const int group = (int)((blockIdx.x * THREADS + threadIdx.x) / V);
+    const int ngroups = (int)(gridDim.x * THREADS / V);
+    const unsigned mask = group_mask<V>(threadIdx.x);
+    for (int r = group; r < A.rows; r += ngroups) {
+        const int kb = A.row_ptr[r], ke = A.row_ptr[r + 1];
+        AccT sum = AccT(0);
+        int k = kb + lane;
+        // two independent accumulations in flight
+        AccT sum2 = AccT(0);
+        for (; k + V < ke; k += 2 * V) {
+            sum += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
+            sum2 += AccT(ld_stream(A.val + k + V)) * AccT(__ldg(x + ld_stream(A.col_ind + k + V)));
+        }
+        if (k < ke) sum += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
+        sum += sum2;
+        if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+        if (lane == 0) op.row(r, sum, red);
+    }
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// STAGED kernel.  Persistent CTAs take tiles blockIdx.x, blockIdx.x + grid,
+// ... (static, so the per-CTA sums are reproducible).  Thread 0 streams the
+// next tile's val / col_ind / row_ptr segments into the other half of a
+// double buffer with cp.async.bulk while the block computes the current one
+// from shared memory; groups of V lanes reduce one row each.  Split rows
+// (longer than a tile) are summed chunk by chunk; the CTA that adds the last
+// chunk (arrival counter) adds the chunk sums in chunk order and runs the
+// epilogue for the row.
+//
+// Shared layout per stage: val[TN + 8] | col[TN + 8] | row_ptr[TR + 8].
+// Copies start at indices rounded down to a multiple of 4 (16 bytes for
+// 4- and 8-byte elements) and end rounded up; the device arrays are padded
+// by the host so the rounded-up end stays inside the allocation.
+
+template <class ValT, int TN, int TR>
+struct StagedLayout {
+    static constexpr int kValElems = TN + 8;
+    static constexpr int kRpElems = TR + 8;
+    static constexpr size_t kValBytes = sizeof(ValT) * kValElems;
+    static constexpr size_t kColBytes = sizeof(int) * kValElems;
+    static constexpr size_t kRpBytes = sizeof(int) * kRpElems;
+    static constexpr size_t kStageBytes = kValBytes + kColBytes + kRpBytes;
+    static constexpr size_t kSmemBytes = 2 * kStageBytes;
+};
+
+template <int V, int THREADS, int TN, int TR, class Op>
+__global__ void __launch_bounds__(THREADS)
+    spmv_staged_kernel(CsrView<typename Op::ValT> A, const TileDesc* __restrict__ tiles,
+                       int ntiles, const LongRow* __restrict__ longs, int nlong,
+                       const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
+    if (op.skip()) return;
+    using ValT = typename Op::ValT;
+    using AccT = typename Op::AccT;
+    using L = StagedLayout<ValT, TN, TR>;
+    constexpr int NR = Op::NR;
+    constexpr int NGROUPS = THREADS / V;
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ TileDesc sdesc[2];
+    __shared__ AccT sh_sum[32];
+    __shared__ int sh_ok;
+
+    double red[NR > 0 ? NR : 1] = {};
+    const int tid = threadIdx.x;
+    const int lane = tid & (V - 1);
+    const int group = tid / V;
+    const unsigned mask = group_mask<V>(tid);
+    const int cnt = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+
+    uint64_t policy = 0;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        policy = l2_policy_evict_first();
+    }
+    __syncthreads();
+
+    auto stage_ptr = [&](int st) { return smem + st * L::kStageBytes; };
+
+    // Thread 0: start the copies of the CTA's i-th tile into stage st.
+    auto issue = [&](int i, int st) {
+        const TileDesc t = tiles[blockIdx.x + (size_t)i * gridDim.x];
+        sdesc[st] = t;
+        unsigned char* base = stage_ptr(st);
+        const int ka = t.k0 & ~3;
+        const int kz = (t.k1 + 3) & ~3;
+        const uint32_t nk = (uint32_t)(kz - ka);
+        uint32_t bytes = nk * (uint32_t)(sizeof(ValT) + sizeof(int));
+        int ra = 0;
+        uint32_t nr = 0;
+        if (t.r1 >= 0) {
+            ra = t.r0 & ~3;
+            const int rz = (t.r1 + 1 + 3) & ~3;
+            nr = (uint32_t)(rz - ra);
+            bytes += nr * (uint32_t)sizeof(int);
+        }
+        mbar_arrive_expect_tx(&bar[st], bytes);
+        if (nk > 0) {
+            bulk_g2s(base, A.val + ka, nk * (uint32_t)sizeof(ValT), &bar[st], policy);
+            bulk_g2s(base + L::kValBytes, A.col_ind + ka, nk * (uint32_t)sizeof(int), &bar[st],
+                     policy);
+        }
+        if (nr > 0)
+            bulk_g2s(base + L::kValBytes + L::kColBytes, A.row_ptr + ra, nr * (uint32_t)sizeof(int),
+                     &bar[st], policy);
+    };
+
+    if (cnt > 0 && tid == 0) issue(0, 0);
+    bool failed = false;
+    for (int i = 0; i < cnt; ++i) {
+        const int st = i & 1;
+        if (i + 1 < cnt && tid == 0) {
+            fence_proxy_async_smem();
+            issue(i + 1, st ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((i >> 1) & 1));
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            failed = true;
+            // let the other stage's copy (if any) land before leaving
+            if (tid == 0 && i + 1 < cnt) (void)mbar_wait_bounded(&bar[st ^ 1], (uint32_t)(((i + 1) >> 1) & 1));
+            break;
+        }
+        const TileDesc t = sdesc[st];
+        const unsigned char* base = stage_ptr(st);
+        const ValT* vs = reinterpret_cast<const ValT*>(base);
+        const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
+        const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
+        const int ka = t.k0 & ~3;
+        if (t.r1 >= 0) {
+            const int ra = t.r0 & ~3;
+            const int nrows = t.r1 - t.r0;
+            for (int rr = group; rr < nrows; rr += NGROUPS) {
+                const int kb = rps[t.r0 - ra + rr] - ka;
+                const int ke = rps[t.r0 - ra + rr + 1] - ka;
+                AccT sum = AccT(0), sum2 = AccT(0);
+                int k = kb + lane;
+                for (; k + V < ke; k += 2 * V) {
+                    sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
+                    sum2 += AccT(vs[k + V]) * AccT(__ldg(x + cs[k + V]));
+                }
+                if (k < ke) sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
+                sum += sum2;
+                if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+                if (lane == 0) op.row(t.r0 + rr, sum, red);
+            }
+        } else {
+            // chunk of a split row: the whole block sums it
+            AccT sum = AccT(0);
+            for (int k = t.k0 - ka + tid; k < t.k1 - ka; k += THREADS)
+                sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
+            sum = block_sum_all<THREADS, AccT>(sum, sh_sum);
+            if (tid == 0) {
+                const int lid = t.r0;
+                const int slot = -t.r1 - 1;
+                s.long_part[slot] = (double)sum;
+                __threadfence();
+                const LongRow lr = longs[lid];
+                const unsigned c = atomicAdd(&s.long_cnt[lid], 1u);
+                if (c == (unsigned)lr.nchunks - 1u) {
+                    __threadfence();
+                    AccT rs = AccT(0);
+                    for (int j = 0; j < lr.nchunks; ++j) rs += AccT(__ldcg(&s.long_part[lr.first_slot + j]));
+                    double lred[NR > 0 ? NR : 1] = {};
+                    op.row(lr.row, rs, lred);
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = lred[q];
+                    s.long_cnt[lid] = 0u;
+                }
+            }
+        }
+        __syncthreads();  // stage st is free for the copy issued in iteration i + 1
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(s.status, DEV_TIMEOUT);
+        return;
+    }
+    (void)sh_ok;
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, nlong);
+    }
+}
+
+}  // namespace lilac

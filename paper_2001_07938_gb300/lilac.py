@@ -1,0 +1,330 @@
+"""Thin ctypes binding of liblilac.so (include/lilac.h).
+
+The functions keep the C names and arguments; they only marshal arguments
+(pointers of numpy arrays or torch tensors, the current CUDA stream) and
+turn a non-OK status into ``LilacError``.  All computation happens in the
+CUDA library.  There is no CPU fallback: if the library is missing, loading
+fails with an error that says how to build it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+LILAC_OK = 0
+LILAC_ERR_INVALID_ARG = 1
+LILAC_ERR_INVALID_CSR = 2
+LILAC_ERR_OOM = 3
+LILAC_ERR_BUDGET = 4
+LILAC_ERR_CUDA = 5
+LILAC_ERR_BREAKDOWN = 6
+LILAC_ERR_NOT_CONVERGED = 7
+LILAC_ERR_TIMEOUT = 8
+LILAC_ERR_DTYPE = 9
+LILAC_ERR_UNSUPPORTED = 10
+
+LILAC_F64, LILAC_F32 = 0, 1
+LILAC_MEM_HOST, LILAC_MEM_DEVICE = 0, 1
+LILAC_VARIANT_AUTO, LILAC_VARIANT_SCALAR, LILAC_VARIANT_VECTOR, LILAC_VARIANT_STAGED, \
+    LILAC_VARIANT_MERGE = 0, 1, 2, 3, 4
+LILAC_CREATE_TUNE_TIMED = 0x1
+
+VARIANT_NAMES = {1: "scalar", 2: "vector", 3: "staged", 4: "merge"}
+
+# every symbol include/lilac.h declares (checked by the tests)
+EXPORTS = (
+    "lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy", "lilac_csr_info",
+    "lilac_csr_set_variant", "lilac_spmv", "lilac_cg_opts_default", "lilac_cg",
+    "lilac_pagerank", "lilac_csr_reset_error", "lilac_status_string", "lilac_last_error",
+    "lilac_version",
+)
+
+
+class lilac_csr_info_t(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("ncols", ctypes.c_int32), ("nnz", ctypes.c_int64),
+                ("dtype", ctypes.c_int32), ("variant", ctypes.c_int32),
+                ("vector_width", ctypes.c_int32), ("max_row_len", ctypes.c_int32),
+                ("empty_rows", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
+                ("num_long_rows", ctypes.c_int32), ("sm_count", ctypes.c_int32),
+                ("mean_row_len", ctypes.c_double), ("std_row_len", ctypes.c_double),
+                ("device_bytes", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64)]
+
+
+class lilac_cg_opts(ctypes.Structure):
+    _fields_ = [("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
+                ("inner_max_iter", ctypes.c_int32), ("use_x0", ctypes.c_int32),
+                ("true_residual", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32)]
+
+
+class lilac_cg_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("refinements", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
+                ("spmv_ms", ctypes.c_double), ("spmv_launches", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int32)]
+
+
+class LilacError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().lilac_status_string(status).decode()
+        detail = _lib().lilac_last_error().decode()
+        super().__init__(f"{where}: {msg} ({status})" + (f": {detail}" if detail else ""))
+
+
+_LIB = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_2001_07938_gb300.build` "
+                "(the library is CUDA-only; there is no CPU path)")
+        lib = ctypes.CDLL(path)
+        c = ctypes
+        vp, i32, i64, u32, dbl = c.c_void_p, c.c_int32, c.c_int64, c.c_uint32, c.c_double
+        st = c.c_int
+        lib.lilac_csr_create.argtypes = [i32, i32, i64, vp, vp, vp, c.c_int, c.c_int, u32, vp,
+                                         c.POINTER(vp)]
+        lib.lilac_csr_update_values.argtypes = [vp, vp, c.c_int, vp]
+        lib.lilac_csr_destroy.argtypes = [vp]
+        lib.lilac_csr_info.argtypes = [vp, c.POINTER(lilac_csr_info_t)]
+        lib.lilac_csr_set_variant.argtypes = [vp, i32, i32]
+        lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
+        lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
+        lib.lilac_cg_opts_default.restype = None
+        lib.lilac_cg.argtypes = [vp, vp, vp, c.c_int, c.POINTER(lilac_cg_opts),
+                                 c.POINTER(lilac_cg_info), vp]
+        lib.lilac_pagerank.argtypes = [vp, vp, i32, i32, dbl, vp, c.c_int, vp]
+        lib.lilac_csr_reset_error.argtypes = [vp]
+        lib.lilac_status_string.argtypes = [c.c_int]
+        lib.lilac_status_string.restype = c.c_char_p
+        lib.lilac_last_error.argtypes = []
+        lib.lilac_last_error.restype = c.c_char_p
+        lib.lilac_version.argtypes = []
+        lib.lilac_version.restype = i32
+        for name in ("lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy",
+                     "lilac_csr_info", "lilac_csr_set_variant", "lilac_spmv", "lilac_cg",
+                     "lilac_pagerank", "lilac_csr_reset_error"):
+            getattr(lib, name).restype = st
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load the library (raises if it was not built)."""
+    return _lib()
+
+
+def _check(status: int, where: str, ok=(LILAC_OK,)):
+    if status not in ok:
+        raise LilacError(status, where)
+    return status
+
+
+# --- argument marshalling ----------------------------------------------------
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _ptr_where(a):
+    """(pointer, LILAC_MEM_*) of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None, LILAC_MEM_DEVICE
+    if _is_torch(a):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr(), (LILAC_MEM_DEVICE if a.is_cuda else LILAC_MEM_HOST)
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data, LILAC_MEM_HOST
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def current_stream():
+    """cudaStream_t of torch's current stream (0 without torch/CUDA)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return 0
+
+
+def _dtype_code(dt) -> int:
+    name = str(dt)
+    if name.endswith("float64") or name == "double":
+        return LILAC_F64
+    if name.endswith("float32") or name == "float":
+        return LILAC_F32
+    raise ValueError(f"values must be float64 or float32, got {dt}")
+
+
+# --- the C entry points, same names -----------------------------------------
+
+def lilac_csr_create(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, where, flags=0, stream=None):
+    h = ctypes.c_void_p()
+    _check(_lib().lilac_csr_create(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, where, flags,
+                                   stream if stream is not None else current_stream(),
+                                   ctypes.byref(h)), "lilac_csr_create")
+    return h
+
+
+def lilac_csr_update_values(A, vals, where, stream=None):
+    _check(_lib().lilac_csr_update_values(A, vals, where,
+                                          stream if stream is not None else current_stream()),
+           "lilac_csr_update_values")
+
+
+def lilac_csr_destroy(A):
+    _check(_lib().lilac_csr_destroy(A), "lilac_csr_destroy")
+
+
+def lilac_csr_info(A) -> dict:
+    info = lilac_csr_info_t()
+    _check(_lib().lilac_csr_info(A, ctypes.byref(info)), "lilac_csr_info")
+    return {f: getattr(info, f) for f, _ in lilac_csr_info_t._fields_}
+
+
+def lilac_csr_set_variant(A, variant, vector_width=0):
+    _check(_lib().lilac_csr_set_variant(A, variant, vector_width), "lilac_csr_set_variant")
+
+
+def lilac_spmv(A, x, y, where, stream=None):
+    _check(_lib().lilac_spmv(A, x, y, where, stream if stream is not None else current_stream()),
+           "lilac_spmv")
+
+
+def lilac_cg_opts_default() -> lilac_cg_opts:
+    o = lilac_cg_opts()
+    _lib().lilac_cg_opts_default(ctypes.byref(o))
+    return o
+
+
+def lilac_cg(A, b, x, where, opts=None, want_info=True, stream=None, raise_on=None):
+    info = lilac_cg_info()
+    st = _lib().lilac_cg(A, b, x, where, ctypes.byref(opts) if opts is not None else None,
+                         ctypes.byref(info) if want_info else None,
+                         stream if stream is not None else current_stream())
+    ok = (LILAC_OK, LILAC_ERR_NOT_CONVERGED, LILAC_ERR_BREAKDOWN) if raise_on is None else raise_on
+    _check(st, "lilac_cg", ok)
+    return st, info
+
+
+def lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where, stream=None):
+    _check(_lib().lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where,
+                                 stream if stream is not None else current_stream()),
+           "lilac_pagerank")
+
+
+def lilac_csr_reset_error(A):
+    _check(_lib().lilac_csr_reset_error(A), "lilac_csr_reset_error")
+
+
+def lilac_status_string(s: int) -> str:
+    return _lib().lilac_status_string(s).decode()
+
+
+def lilac_last_error() -> str:
+    return _lib().lilac_last_error().decode()
+
+
+def lilac_version() -> int:
+    return int(_lib().lilac_version())
+
+
+# --- a small object wrapper ----------------------------------------------------
+
+class CsrMatrix:
+    """Owns one lilac_csr handle.  Arrays may be numpy (host) or torch (host/device)."""
+
+    def __init__(self, row_ptr, col_ind, vals, ncols: int = -1, flags: int = 0, stream=None):
+        rp, where = _ptr_where(row_ptr)
+        ci, w2 = _ptr_where(col_ind)
+        va, w3 = _ptr_where(vals)
+        if len(col_ind) and len({where, w2, w3}) != 1:
+            raise ValueError("row_ptr, col_ind and vals must all be on the host or all on the device")
+        rows = len(row_ptr) - 1
+        nnz = len(col_ind)
+        self.dtype = _dtype_code(vals.dtype)
+        self.handle = lilac_csr_create(rows, ncols, nnz, rp, ci if nnz else None,
+                                       va if nnz else None, self.dtype, where, flags, stream)
+        self.rows = rows
+
+    @classmethod
+    def from_csr(cls, A, flags: int = 0, dtype=None):
+        """From a host CSR record with row_ptr / col_ind / vals / ncols fields."""
+        vals = A.vals if dtype is None else np.ascontiguousarray(A.vals.astype(dtype))
+        return cls(np.ascontiguousarray(A.row_ptr, np.int32),
+                   np.ascontiguousarray(A.col_ind, np.int32), vals, A.ncols, flags)
+
+    def info(self) -> dict:
+        return lilac_csr_info(self.handle)
+
+    def set_variant(self, variant: int, width: int = 0):
+        lilac_csr_set_variant(self.handle, variant, width)
+
+    def spmv(self, x, y, stream=None):
+        px, wx = _ptr_where(x)
+        py, wy = _ptr_where(y)
+        if wx != wy:
+            raise ValueError("x and y must both be host or both device")
+        lilac_spmv(self.handle, px, py, wx, stream)
+        return y
+
+    def cg(self, b, x, *, max_iter=1000, rtol=1e-10, precision=0, inner_rtol=1e-5,
+           inner_max_iter=1000, use_x0=False, true_residual=True, use_graph=True,
+           check_every=32, want_info=True, profile=False, stream=None):
+        o = lilac_cg_opts_default()
+        o.profile = int(profile)
+        o.max_iter, o.rtol, o.precision = max_iter, rtol, precision
+        o.inner_rtol, o.inner_max_iter = inner_rtol, inner_max_iter
+        o.use_x0, o.true_residual, o.use_graph = int(use_x0), int(true_residual), int(use_graph)
+        o.check_every = check_every
+        pb, wb = _ptr_where(b)
+        px, wx = _ptr_where(x)
+        if wb != wx:
+            raise ValueError("b and x must both be host or both device")
+        st, info = lilac_cg(self.handle, pb, px, wb, o, want_info, stream)
+        return st, info
+
+    def pagerank(self, x, iters=20, damping=0.85, init_uniform=True, want_l1=True, stream=None):
+        px, wx = _ptr_where(x)
+        l1 = np.zeros(max(iters, 1), np.float64) if want_l1 else None
+        lilac_pagerank(self.handle, px, int(init_uniform), iters, damping,
+                       l1.ctypes.data if l1 is not None else None, wx, stream)
+        return l1[:iters] if l1 is not None else None
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lilac_csr_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

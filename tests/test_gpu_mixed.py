@@ -1,0 +1,59 @@
+"""Mixed-precision CG (FP32 inner CG, FP64 iterative refinement) on the GPU.
+
+Accepted when the FP64 true residual ||b - A x|| / ||b||, computed by the
+oracle's SpMV with the handle's own values, is <= 1e-10.  The 3D Laplacian's
+values (6, -1) are exact in FP32, so the FP32 matrix is A itself; for a
+matrix whose values are not FP32-exact the refinement still converges to the
+FP64 system because the residual uses the FP64 values.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_07938_gb300 import inputs
+from paper_2001_07938_gb300 import lilac as L
+from lilac_testutil import dev, host, torch_cuda, true_rel_residual
+
+pytestmark = pytest.mark.gpu
+
+
+def _mixed(A, b, **kw):
+    torch = torch_cuda()
+    M = L.CsrMatrix.from_csr(A)
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    st, info = M.cg(dev(b), xd, precision=1, **kw)
+    torch.cuda.synchronize()
+    M.close()
+    return st, info, host(xd)
+
+
+def test_poisson3d_fp32_values_reach_1e10():
+    A, b = inputs.workload_poisson3d_ir(24)
+    st, info, x = _mixed(A, b, rtol=1e-10, max_iter=20)
+    assert st == L.LILAC_OK and info.status == L.LILAC_OK
+    assert info.refinements >= 2  # one FP32 solve alone cannot reach 1e-10
+    A64 = A.astype(np.float64)
+    assert true_rel_residual(A64, b, x) <= 1e-10
+    # one FP32 solve alone, asked for 1e-12, stalls far above 1e-10
+    st1, info1, x1 = _mixed(A, b, rtol=1e-10, max_iter=1, inner_rtol=1e-12, inner_max_iter=3000)
+    assert st1 == L.LILAC_ERR_NOT_CONVERGED and info1.refinements == 1
+    assert true_rel_residual(A64, b, x1) > 1e-9
+
+
+def test_fp64_values_not_fp32_exact():
+    A = inputs.banded_spd(5000, 12, 1.0, seed=3, fp32_exact=False)
+    b = inputs.uniform(4, A.n)
+    st, info, x = _mixed(A, b, rtol=1e-10, max_iter=30)
+    assert st == L.LILAC_OK
+    assert true_rel_residual(A, b, x) <= 1e-10
+    xr, _, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=5000, rtol=1e-12)
+    assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+
+
+@pytest.mark.slow
+def test_full_poisson3d_192():
+    """3D Poisson 192^3 (n = 7,077,888), FP32 values, b uniform in [-1, 1] seed 1."""
+    A, b = inputs.workload_poisson3d_ir()
+    st, info, x = _mixed(A, b, rtol=1e-10, max_iter=20, inner_max_iter=4000)
+    assert st == L.LILAC_OK
+    assert true_rel_residual(A.astype(np.float64), b, x) <= 1e-10

@@ -1,0 +1,197 @@
+"""GPU SpMV (lilac_spmv through the C ABI) against the FP64 oracle.
+
+Every kernel variant and lanes-per-row, FP64 and FP32, on matrices that span
+many tiles with a ragged tail, empty rows, unsorted and duplicate columns,
+rows longer than a tile (split rows), degenerate shapes, and the full-size
+workloads (2D Laplacian 64x64; random SPD n=75,000; R-MAT scale 22; 3D
+Laplacian 192^3) in the launch configuration the benchmark uses.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_07938_gb300 import inputs
+from paper_2001_07938_gb300 import lilac as L
+from lilac_testutil import ALL_VARIANTS, assert_spmv_close, dev, host, torch_cuda
+from conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(M, x_np, dtype):
+    torch = torch_cuda()
+    xd = dev(x_np.astype(dtype))
+    yd = torch.full((M.rows,), float("nan"), dtype=xd.dtype, device="cuda")
+    M.spmv(xd, yd)
+    torch.cuda.synchronize()
+    return host(yd)
+
+
+def _check_all_variants(A, dtype, seed=0, variants=ALL_VARIANTS):
+    fp32 = dtype == np.float32
+    Ad = A.astype(dtype)
+    x = inputs.uniform(seed + 17, max(A.ncols, 1), dtype=dtype)[: A.ncols]
+    M = L.CsrMatrix.from_csr(Ad)
+    results = {}
+    for var, w in variants:
+        M.set_variant(var, w)
+        y = _run(M, x, dtype)
+        assert_spmv_close(Ad, x.astype(np.float64), y, fp32, f"variant {var} width {w}")
+        results[(var, w)] = y
+    M.close()
+    return results
+
+
+def test_paper_example_bit_exact():
+    g = load_golden("csr_example_5x5.txt")
+    A = inputs.CSR(5, 5, np.array(g["row_ptr"], np.int32), np.array(g["col_ind"], np.int32),
+                   np.array(g["val"], np.float64))
+    x = np.array(g["x"], np.float64)
+    M = L.CsrMatrix.from_csr(A)
+    assert M.info()["ncols"] == 5  # max(col_ind) + 1, the cached invariant
+    for var, w in ALL_VARIANTS:
+        M.set_variant(var, w)
+        assert list(_run(M, x, np.float64)) == [float(t) for t in g["y"]]
+    M.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("shape", [(3000, 2500, 40), (777, 5000, 9), (5000, 300, 3)])
+def test_random_with_empty_rows_duplicates_unsorted(dtype, shape):
+    n, ncols, max_len = shape
+    A = inputs.random_csr(n, ncols, max_len, 0.2, seed=n)
+    _check_all_variants(A, dtype)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_laplacian2d_full_and_ragged(dtype):
+    for m in (64, 97):
+        _check_all_variants(inputs.laplacian2d(m), dtype, seed=m)
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_split_rows_longer_than_a_tile(dtype):
+    A = inputs.powerlaw_csr(6000, 9000, 60000, power=8, seed=3)
+    assert np.diff(A.row_ptr).max() > 2048 * 3
+    res = _check_all_variants(A, dtype)
+    M = L.CsrMatrix.from_csr(A.astype(dtype))
+    assert M.info()["num_long_rows"] > 0
+    M.close()
+    assert res
+
+
+def test_one_huge_row_and_tiny_shapes():
+    n1 = 100_003
+    A = inputs.CSR(1, n1, np.array([0, n1], np.int32), np.arange(n1, dtype=np.int32),
+                   inputs.uniform(9, n1))
+    _check_all_variants(A, np.float64)
+    one = inputs.CSR(1, 1, np.array([0, 1], np.int32), np.array([0], np.int32), np.array([2.5]))
+    _check_all_variants(one, np.float64)
+
+
+def test_all_empty_rows_and_zero_rows():
+    torch = torch_cuda()
+    A = inputs.CSR(1000, 10, np.zeros(1001, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    M = L.CsrMatrix(A.row_ptr, A.col_ind, A.vals, ncols=10)
+    for var, w in ALL_VARIANTS:
+        M.set_variant(var, w)
+        y = _run(M, np.ones(10), np.float64)
+        assert np.all(y == 0.0)
+    M.close()
+    Z = L.CsrMatrix(np.zeros(1, np.int32), np.zeros(0, np.int32), np.zeros(0), ncols=0)
+    assert Z.info()["rows"] == 0
+    Z.spmv(torch.zeros(0, dtype=torch.float64, device="cuda"),
+           torch.zeros(0, dtype=torch.float64, device="cuda"))
+    Z.close()
+
+
+def test_invalid_csr_is_rejected():
+    bad_col = inputs.CSR(2, 2, np.array([0, 1, 2], np.int32), np.array([0, 5], np.int32),
+                         np.ones(2))
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix(bad_col.row_ptr, bad_col.col_ind, bad_col.vals, ncols=2)
+    assert e.value.status == L.LILAC_ERR_INVALID_CSR
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix(np.array([0, 2, 1], np.int32), np.array([0, 1], np.int32), np.ones(2))
+    assert e.value.status == L.LILAC_ERR_INVALID_CSR
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix(np.array([0, 1, 3], np.int32), np.array([0, 1], np.int32), np.ones(2))
+    assert e.value.status == L.LILAC_ERR_INVALID_CSR
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix(np.array([0, 1], np.int32), np.array([-1], np.int32), np.ones(1))
+    assert e.value.status == L.LILAC_ERR_INVALID_CSR
+
+
+def test_device_input_host_vectors_update_values_and_determinism():
+    torch = torch_cuda()
+    A = inputs.random_csr(4000, 3000, 30, 0.1, seed=5)
+    # create from device arrays
+    M = L.CsrMatrix(dev(A.row_ptr), dev(A.col_ind), dev(A.vals))
+    info = M.info()
+    assert info["ncols"] == oracle.csr_ncols(A.col_ind)
+    x = inputs.uniform(1, info["ncols"])
+    y1 = _run(M, x, np.float64)
+    y2 = _run(M, x, np.float64)
+    np.testing.assert_array_equal(y1, y2)  # static schedule: bitwise reproducible
+    # host vectors through the library's own staging buffers
+    yh = np.empty(A.n)
+    M.spmv(x, yh)
+    np.testing.assert_array_equal(yh, y1)
+    # update_values: the paper's "update" step
+    v2 = inputs.uniform(2, A.nnz)
+    before = M.info()["h2d_bytes"]
+    L.lilac_csr_update_values(M.handle, v2.ctypes.data, L.LILAC_MEM_HOST)
+    torch.cuda.synchronize()
+    assert M.info()["h2d_bytes"] == before + 8 * A.nnz
+    A2 = inputs.CSR(A.n, info["ncols"], A.row_ptr, A.col_ind, v2)
+    assert_spmv_close(A2, x, _run(M, x, np.float64), False, "after update")
+    M.close()
+
+
+def test_timed_autotuner_picks_a_valid_variant():
+    A = inputs.spd_random(20000, 30, 20.0, 1)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_TUNE_TIMED)
+    info = M.info()
+    assert info["variant"] in (1, 2, 3)
+    x = inputs.uniform(3, A.n)
+    assert_spmv_close(A, x, _run(M, x, np.float64), False, "tuned")
+    M.close()
+
+
+# --- full-size workloads ---------------------------------------------------------
+
+def test_full_laplacian2d_64_fp64():
+    A, x = inputs.workload_laplacian2d_spmv(64)
+    assert A.n == 4096 and A.nnz == 20224
+    M = L.CsrMatrix.from_csr(A)
+    assert_spmv_close(A, x, _run(M, x, np.float64), False, "laplacian2d 64")
+    M.close()
+
+
+@pytest.mark.slow
+def test_full_spd_75k_fp64():
+    A, _ = inputs.workload_spd_cg()
+    x = inputs.uniform(7, A.n)
+    M = L.CsrMatrix.from_csr(A)
+    assert_spmv_close(A, x, _run(M, x, np.float64), False, "spd 75k")
+    M.close()
+
+
+@pytest.mark.slow
+def test_full_rmat22_fp32():
+    A = inputs.workload_rmat_pagerank()
+    x = inputs.uniform(8, A.n, 0.0, 1.0, dtype=np.float32)
+    M = L.CsrMatrix.from_csr(A)
+    assert M.info()["num_long_rows"] > 0
+    assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "rmat 22")
+    M.close()
+
+
+@pytest.mark.slow
+def test_full_laplacian3d_192_fp32():
+    A, _ = inputs.workload_poisson3d_ir()
+    assert A.nnz == 7 * 192 ** 3 - 6 * 192 ** 2
+    x = inputs.uniform(9, A.n, dtype=np.float32)
+    M = L.CsrMatrix.from_csr(A)
+    assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "laplacian3d 192")
+    M.close()
