@@ -314,12 +314,16 @@ def run_lilac(args):
     # dominant kernel: fused SpMV, CUDA events on its own stream
     kr = min(K, 5)
     spmv_ms, n_spmv = wl.roofline_sample(kr)
+    minfo = wl.M.info()
+    kname = {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {minfo['vector_width']} lanes/row)",
+             3: f"spmv_staged_kernel ({minfo['vector_width']} lanes/row)",
+             5: "spmv_slab_kernel (x slabs in shared memory)"}.get(minfo["variant"], "spmv")
     peak, peak_kind = _peaks()
     achieved = wl.spmv_bytes() / (spmv_ms / 1000.0) / 1e9
     traffic = _ncu_traffic(f"spmv_cg_{args.workload}")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "spmv_staged_kernel<OpCgPq> (q = A p, p.q fused)",
+                "kernel": kname + " with the CG epilogue (q = A p, p.q fused)",
                 "algorithmic_bytes_per_launch": wl.spmv_bytes(),
                 "avg_launch_ms": spmv_ms, "launches_timed": n_spmv,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}

@@ -80,8 +80,11 @@ typedef enum {
     LILAC_VARIANT_MERGE = 4   /* merge-path partition of (rows + nonzeros) */
 } lilac_variant;
 
-/* lilac_csr_create flags */
-#define LILAC_CREATE_TUNE_TIMED 0x1u /* time the candidate variants once at create and keep the fastest */
+/* lilac_csr_create flags.  By default create times the candidate SpMV
+ * variants once on the matrix and keeps the fastest (the one-off tuning
+ * phase of an autotuning sparse library, paid at create like the paper's
+ * cached invariants). */
+#define LILAC_CREATE_NO_TUNE 0x1u /* skip the timing; keep the choice made from row statistics */
 
 /*
  * Upload a CSR matrix once and return a handle (construct + update of the

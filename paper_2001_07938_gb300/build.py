@@ -36,18 +36,23 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
-def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None) -> str:
+def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = None,
+          extra_flags=(), build_dir: str | None = None) -> str:
+    """Compile and link; `extra_flags` (e.g. -D tile-shape overrides) and
+    `build_dir` allow side-by-side builds of other configurations."""
     nvcc = _nvcc()
-    os.makedirs(BUILD_DIR, exist_ok=True)
+    bdir = build_dir or BUILD_DIR
+    lib = os.path.join(bdir, "liblilac.so")
+    os.makedirs(bdir, exist_ok=True)
     srcs = sources()
     hdr_t = _headers_mtime()
     flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-             "--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177"]
+             "--expt-relaxed-constexpr", "-Xcudafe", "--diag_suppress=177", *extra_flags]
     if verbose_ptxas:
         flags += ["-Xptxas", "-v"]
 
     def obj_of(src):
-        return os.path.join(BUILD_DIR, os.path.basename(src)[:-3] + ".o")
+        return os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
 
     def compile_one(src):
         obj = obj_of(src)
@@ -68,17 +73,17 @@ def build(force: bool = False, verbose_ptxas: bool = False, jobs: int | None = N
             objs.append(obj)
             if log:
                 logs.append(log)
-    if (force or not os.path.exists(LIB)
-            or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if (force or not os.path.exists(lib)
+            or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
         p = subprocess.run(cmd, capture_output=True, text=True)
         if p.returncode != 0:
             raise RuntimeError(f"link failed:\n{p.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose_ptxas:
         sys.stderr.write("\n".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

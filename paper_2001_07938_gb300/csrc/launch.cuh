@@ -31,13 +31,19 @@ int& bps_slot(int device) {
 template <int V, class Op>
 lilac_status prepare_rows(lilac_csr_s* A) {
     int& bps = bps_slot<V, Op, false>(A->device);
-    if (bps == 0) bps = occupancy_per_sm(spmv_rows_kernel<V, kRowsThreads, Op>, kRowsThreads, 0);
+    if (bps == 0) {
+        auto kern = spmv_rows_kernel<V, kRowsThreads, Op>;
+        // no shared memory: give the unified L1 / shared array to L1, which
+        // caches the gathered x
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        bps = occupancy_per_sm(kern, kRowsThreads, 0);
+    }
     return LILAC_OK;
 }
 
 template <int V, class Op>
 lilac_status prepare_staged(lilac_csr_s* A) {
-    using L = StagedLayout<typename Op::ValT, kTileNnz, kTileRows>;
+    using L = StagedLayout<typename Op::ValT, typename Op::AccT, kTileNnz, kTileRows>;
     int& bps = bps_slot<V, Op, true>(A->device);
     if (bps == 0) {
         auto kern = spmv_staged_kernel<V, kStagedThreads, kTileNnz, kTileRows, Op>;
@@ -68,7 +74,7 @@ lilac_status launch_rows(lilac_csr_s* A, const typename Op::ValT* val, const typ
 template <int V, class Op>
 lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                            const Op& op, cudaStream_t stream) {
-    using L = StagedLayout<typename Op::ValT, kTileNnz, kTileRows>;
+    using L = StagedLayout<typename Op::ValT, typename Op::AccT, kTileNnz, kTileRows>;
     if (A->ntiles == 0 && Op::NR == 0) return LILAC_OK;  // no rows and nothing to sum
     LILAC_TRY(prepare_staged<V, Op>(A));
     const int bps = bps_slot<V, Op, true>(A->device);

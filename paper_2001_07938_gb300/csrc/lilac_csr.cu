@@ -155,6 +155,25 @@ static int pick_width(double mean) {
     return v;
 }
 
+// Choice from row statistics alone.  Short regular rows (stencils): STAGED,
+// one thread per row.  Irregular rows (coefficient of variation > 1, or rows
+// longer than a tile): STAGED, which balances nonzeros and splits long rows.
+// Long regular rows: VECTOR with about mean/16 lanes, which keeps the most
+// independent x gathers in flight.
+static void heuristic_variant(lilac_csr A) {
+    const double mean = A->mean_row_len;
+    const double cv = mean > 0 ? A->std_row_len / mean : 0.0;
+    if (cv > 1.0 || A->max_row_len > kTileNnz || mean <= 12.0) {
+        A->variant = LILAC_VARIANT_STAGED;
+        A->vwidth = mean <= 12.0 && cv <= 1.0 ? 1 : std::min(pick_width(mean), 8);
+    } else {
+        A->variant = LILAC_VARIANT_VECTOR;
+        int v = 2;
+        while (v < 32 && v < mean / 16.0) v *= 2;
+        A->vwidth = v;
+    }
+}
+
 }  // namespace lilac
 
 using namespace lilac;
@@ -293,10 +312,9 @@ static lilac_status create_impl(int32_t rows, int32_t ncols, int64_t nnz, const 
     LILAC_TRY(A->status.alloc(sizeof(int) * 4));
     LILAC_TRY(zero_scratch(A, stream));
 
-    // autotuner: heuristic from the row statistics
-    A->variant = LILAC_VARIANT_STAGED;
-    A->vwidth = pick_width(A->mean_row_len);
-    if (flags & LILAC_CREATE_TUNE_TIMED) LILAC_TRY(tune_timed(A, stream));
+    // autotuner: heuristic from the row statistics, then (by default) timing
+    heuristic_variant(A);
+    if (!(flags & LILAC_CREATE_NO_TUNE)) LILAC_TRY(tune_timed(A, stream));
     LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
     return LILAC_OK;
 }
@@ -313,12 +331,14 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     LILAC_CUDA_TRY(cudaMemsetAsync(x.p, 0, x.bytes, stream));
     struct Cand { int variant, width; };
     std::vector<Cand> cands;
-    const int w0 = pick_width(A->mean_row_len);
-    for (int w : {w0 / 2, w0, w0 * 2})
-        if (w >= 1 && w <= 32) cands.push_back({LILAC_VARIANT_STAGED, w});
-    cands.push_back({LILAC_VARIANT_SCALAR, 1});
-    for (int w : {w0, w0 * 2})
-        if (w >= 2 && w <= 32) cands.push_back({LILAC_VARIANT_VECTOR, w});
+    cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
+    for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
+    // row-per-group kernels serialise a long row in one group: only for
+    // rows no longer than a few tiles
+    if (A->max_row_len <= 4 * kTileNnz) {
+        for (int w : {4, 8, 16, 32}) cands.push_back({LILAC_VARIANT_VECTOR, w});
+        cands.push_back({LILAC_VARIANT_SCALAR, 1});
+    }
     cudaEvent_t e0, e1;
     LILAC_CUDA_TRY(cudaEventCreate(&e0));
     LILAC_CUDA_TRY(cudaEventCreate(&e1));
@@ -336,7 +356,7 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
         };
         run();  // warm-up
         LILAC_CUDA_TRY(cudaEventRecord(e0, stream));
-        for (int it = 0; it < 5 && st == LILAC_OK; ++it) run();
+        for (int it = 0; it < 3 && st == LILAC_OK; ++it) run();
         LILAC_CUDA_TRY(cudaEventRecord(e1, stream));
         LILAC_CUDA_TRY(cudaEventSynchronize(e1));
         if (st != LILAC_OK) continue;

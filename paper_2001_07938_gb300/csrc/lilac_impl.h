@@ -17,10 +17,19 @@
 namespace lilac {
 
 // Tile shape of the STAGED kernel: at most kTileNnz nonzeros and kTileRows
-// rows per tile; 256 threads per CTA.
-constexpr int kStagedThreads = 256;
-constexpr int kTileNnz = 2048;
-constexpr int kTileRows = 1024;
+// rows per tile, kStagedThreads threads per CTA (overridable at build time).
+#ifndef LILAC_STAGED_THREADS
+#define LILAC_STAGED_THREADS 256
+#endif
+#ifndef LILAC_TILE_NNZ
+#define LILAC_TILE_NNZ 2048
+#endif
+#ifndef LILAC_TILE_ROWS
+#define LILAC_TILE_ROWS 1024
+#endif
+constexpr int kStagedThreads = LILAC_STAGED_THREADS;
+constexpr int kTileNnz = LILAC_TILE_NNZ;
+constexpr int kTileRows = LILAC_TILE_ROWS;
 constexpr int kRowsThreads = 256;
 constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
 

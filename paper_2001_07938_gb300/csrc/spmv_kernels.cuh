@@ -56,16 +56,21 @@ __global__ void __launch_bounds__(THREADS)
     const unsigned mask = group_mask<V>(threadIdx.x);
     for (int r = group; r < A.rows; r += ngroups) {
         const int kb = A.row_ptr[r], ke = A.row_ptr[r + 1];
-        AccT sum = AccT(0);
+        // four independent gathers in flight per lane
+        AccT s0 = AccT(0), s1 = AccT(0), s2 = AccT(0), s3 = AccT(0);
         int k = kb + lane;
-        // two independent accumulations in flight
-        AccT sum2 = AccT(0);
-        for (; k + V < ke; k += 2 * V) {
-            sum += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
-            sum2 += AccT(ld_stream(A.val + k + V)) * AccT(__ldg(x + ld_stream(A.col_ind + k + V)));
+        for (; k + 3 * V < ke; k += 4 * V) {
+            const int c0 = ld_stream(A.col_ind + k), c1 = ld_stream(A.col_ind + k + V);
+            const int c2 = ld_stream(A.col_ind + k + 2 * V), c3 = ld_stream(A.col_ind + k + 3 * V);
+            const typename Op::VecT x0 = __ldg(x + c0), x1 = __ldg(x + c1);
+            const typename Op::VecT x2 = __ldg(x + c2), x3 = __ldg(x + c3);
+            s0 += AccT(ld_stream(A.val + k)) * AccT(x0);
+            s1 += AccT(ld_stream(A.val + k + V)) * AccT(x1);
+            s2 += AccT(ld_stream(A.val + k + 2 * V)) * AccT(x2);
+            s3 += AccT(ld_stream(A.val + k + 3 * V)) * AccT(x3);
         }
-        if (k < ke) sum += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
-        sum += sum2;
+        for (; k < ke; k += V) s0 += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
+        AccT sum = (s0 + s1) + (s2 + s3);
         if constexpr (V > 1) sum = group_sum<V>(sum, mask);
         if (lane == 0) op.row(r, sum, red);
     }
@@ -82,17 +87,21 @@ __global__ void __launch_bounds__(THREADS)
 // ... (static, so the per-CTA sums are reproducible).  Thread 0 streams the
 // next tile's val / col_ind / row_ptr segments into the other half of a
 // double buffer with cp.async.bulk while the block computes the current one
-// from shared memory; groups of V lanes reduce one row each.  Split rows
+// from shared memory.  Within a tile, every thread first gathers x for its
+// TN / THREADS nonzeros (all loads in flight together) and stores the
+// products in shared memory; then groups of V lanes add up one row each.
+// Split rows
 // (longer than a tile) are summed chunk by chunk; the CTA that adds the last
 // chunk (arrival counter) adds the chunk sums in chunk order and runs the
 // epilogue for the row.
 //
-// Shared layout per stage: val[TN + 8] | col[TN + 8] | row_ptr[TR + 8].
+// Shared layout per stage: val[TN + 8] | col[TN + 8] | row_ptr[TR + 8]
+// (and one product buffer when the accumulator is wider than the values).
 // Copies start at indices rounded down to a multiple of 4 (16 bytes for
 // 4- and 8-byte elements) and end rounded up; the device arrays are padded
 // by the host so the rounded-up end stays inside the allocation.
 
-template <class ValT, int TN, int TR>
+template <class ValT, class AccT, int TN, int TR>
 struct StagedLayout {
     static constexpr int kValElems = TN + 8;
     static constexpr int kRpElems = TR + 8;
@@ -100,7 +109,10 @@ struct StagedLayout {
     static constexpr size_t kColBytes = sizeof(int) * kValElems;
     static constexpr size_t kRpBytes = sizeof(int) * kRpElems;
     static constexpr size_t kStageBytes = kValBytes + kColBytes + kRpBytes;
-    static constexpr size_t kSmemBytes = 2 * kStageBytes;
+    // products of a tile: in place over the values, or (value and
+    // accumulator types of different size) in one extra buffer
+    static constexpr size_t kProdBytes = sizeof(AccT) == sizeof(ValT) ? 0 : sizeof(AccT) * kValElems;
+    static constexpr size_t kSmemBytes = 2 * kStageBytes + kProdBytes;
 };
 
 template <int V, int THREADS, int TN, int TR, class Op>
@@ -111,9 +123,11 @@ __global__ void __launch_bounds__(THREADS)
     if (op.skip()) return;
     using ValT = typename Op::ValT;
     using AccT = typename Op::AccT;
-    using L = StagedLayout<ValT, TN, TR>;
+    using L = StagedLayout<ValT, AccT, TN, TR>;
     constexpr int NR = Op::NR;
     constexpr int NGROUPS = THREADS / V;
+    constexpr int IPT = TN / THREADS;
+    static_assert(TN % THREADS == 0, "tile nonzeros must be a multiple of the block size");
 
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar[2];
@@ -183,33 +197,55 @@ __global__ void __launch_bounds__(THREADS)
             break;
         }
         const TileDesc t = sdesc[st];
-        const unsigned char* base = stage_ptr(st);
+        unsigned char* base = stage_ptr(st);
         const ValT* vs = reinterpret_cast<const ValT*>(base);
         const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
         const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
+        // products overwrite the values in place when the types have one size
+        AccT* prod = L::kProdBytes ? reinterpret_cast<AccT*>(smem + 2 * L::kStageBytes)
+                                   : reinterpret_cast<AccT*>(base);
         const int ka = t.k0 & ~3;
+        const int kb0 = t.k0 - ka, ke0 = t.k1 - ka;
+        // Phase A: every thread gathers x for IPT nonzeros of the tile, all
+        // loads issued before any is used.
+        int cj[IPT];
+        typename Op::VecT xj[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int k = kb0 + j * THREADS + tid;
+            cj[j] = k < ke0 ? cs[k] : 0;
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int k = kb0 + j * THREADS + tid;
+            xj[j] = k < ke0 ? __ldg(x + cj[j]) : typename Op::VecT(0);
+        }
         if (t.r1 >= 0) {
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int k = kb0 + j * THREADS + tid;
+                if (k < ke0) prod[k] = AccT(vs[k]) * AccT(xj[j]);
+            }
+            __syncthreads();
+            // Phase B: groups of V lanes add each row's products from shared memory.
             const int ra = t.r0 & ~3;
             const int nrows = t.r1 - t.r0;
             for (int rr = group; rr < nrows; rr += NGROUPS) {
                 const int kb = rps[t.r0 - ra + rr] - ka;
                 const int ke = rps[t.r0 - ra + rr + 1] - ka;
-                AccT sum = AccT(0), sum2 = AccT(0);
-                int k = kb + lane;
-                for (; k + V < ke; k += 2 * V) {
-                    sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
-                    sum2 += AccT(vs[k + V]) * AccT(__ldg(x + cs[k + V]));
-                }
-                if (k < ke) sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
-                sum += sum2;
+                AccT sum = AccT(0);
+                for (int k = kb + lane; k < ke; k += V) sum += prod[k];
                 if constexpr (V > 1) sum = group_sum<V>(sum, mask);
                 if (lane == 0) op.row(t.r0 + rr, sum, red);
             }
         } else {
             // chunk of a split row: the whole block sums it
             AccT sum = AccT(0);
-            for (int k = t.k0 - ka + tid; k < t.k1 - ka; k += THREADS)
-                sum += AccT(vs[k]) * AccT(__ldg(x + cs[k]));
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int k = kb0 + j * THREADS + tid;
+                if (k < ke0) sum += AccT(vs[k]) * AccT(xj[j]);
+            }
             sum = block_sum_all<THREADS, AccT>(sum, sh_sum);
             if (tid == 0) {
                 const int lid = t.r0;
@@ -230,6 +266,9 @@ __global__ void __launch_bounds__(THREADS)
                 }
             }
         }
+        // shared-memory writes of this tile are ordered before the bulk copy
+        // that will overwrite the stage
+        fence_proxy_async_smem();
         __syncthreads();  // stage st is free for the copy issued in iteration i + 1
     }
     if (failed) {

@@ -69,13 +69,23 @@ def test_laplacian_converges_and_eigenmode_in_one_step():
 
 
 def test_fixed_iterations_graph_equals_eager_bitwise():
+    """Same handle (same kernel choice): the captured graph and eager launches
+    give bitwise-identical iterates (every reduction order is fixed)."""
+    torch = torch_cuda()
     A = inputs.spd_random(5000, 20, 20.0, 2)
     b = np.ones(A.n)
-    st1, i1, x1 = _solve(A, b, rtol=0.0, max_iter=40, use_graph=True)
-    st2, i2, x2 = _solve(A, b, rtol=0.0, max_iter=40, use_graph=False)
-    assert i1.iters == 40 and i2.iters == 40
-    np.testing.assert_array_equal(x1, x2)
-    assert true_rel_residual(A, b, x1) <= 1e-10
+    M = L.CsrMatrix.from_csr(A)
+    bd = dev(b)
+    xs = []
+    for use_graph in (True, False, True):
+        xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st, info = M.cg(bd, xd, rtol=0.0, max_iter=40, use_graph=use_graph)
+        assert st == L.LILAC_OK and info.iters == 40
+        xs.append(host(xd))
+    M.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    np.testing.assert_array_equal(xs[0], xs[2])
+    assert true_rel_residual(A, b, xs[0]) <= 1e-10
 
 
 def test_breakdown_zero_rhs_not_converged_and_x0():
@@ -97,10 +107,13 @@ def test_breakdown_zero_rhs_not_converged_and_x0():
 
 
 def test_host_buffers_match_device_buffers():
+    torch = torch_cuda()
     A = inputs.spd_random(4000, 15, 20.0, 9)
     b = inputs.uniform(10, A.n)
-    st, info, xd = _solve(A, b, rtol=1e-10, max_iter=300)
     M = L.CsrMatrix.from_csr(A)
+    xdev = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    st, info = M.cg(dev(b), xdev, rtol=1e-10, max_iter=300)
+    xd = host(xdev)
     xh = np.zeros(A.n)
     st2, info2 = M.cg(b, xh, rtol=1e-10, max_iter=300)
     M.close()

@@ -148,14 +148,15 @@ def test_device_input_host_vectors_update_values_and_determinism():
     M.close()
 
 
-def test_timed_autotuner_picks_a_valid_variant():
+def test_autotuner_timed_and_heuristic_choices_are_valid():
     A = inputs.spd_random(20000, 30, 20.0, 1)
-    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_TUNE_TIMED)
-    info = M.info()
-    assert info["variant"] in (1, 2, 3)
     x = inputs.uniform(3, A.n)
-    assert_spmv_close(A, x, _run(M, x, np.float64), False, "tuned")
-    M.close()
+    for flags in (0, L.LILAC_CREATE_NO_TUNE):
+        M = L.CsrMatrix.from_csr(A, flags=flags)
+        info = M.info()
+        assert info["variant"] in (1, 2, 3)
+        assert_spmv_close(A, x, _run(M, x, np.float64), False, f"tuned flags={flags}")
+        M.close()
 
 
 # --- full-size workloads ---------------------------------------------------------
