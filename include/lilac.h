@@ -77,7 +77,10 @@ typedef enum {
     LILAC_VARIANT_VECTOR = 2, /* V lanes per row, V in {2,4,8,16,32}; V = 32 is warp-per-row */
     LILAC_VARIANT_STAGED = 3, /* nnz-balanced row tiles staged in shared memory by bulk
                                  asynchronous copies; rows longer than a tile are split */
-    LILAC_VARIANT_MERGE = 4   /* merge-path partition of (rows + nonzeros) */
+    LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) */
+    LILAC_VARIANT_SLAB = 5    /* row blocks x column slabs, built once per matrix: x is read
+                                 from shared memory, one slab of columns at a time; x must be
+                                 16-byte aligned (else STAGED runs) */
 } lilac_variant;
 
 /* lilac_csr_create flags.  By default create times the candidate SpMV
@@ -140,9 +143,10 @@ typedef struct {
 /* Describe the handle.  Synchronous only on host state. */
 lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
 
-/* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR
- * and STAGED, lanes per row (power of two 1..32; 0 keeps the current one).
- * Host-only; affects later calls. */
+/* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR,
+ * STAGED and SLAB, lanes per row (power of two 1..32; 0 keeps the current
+ * one).  Affects later calls.  Choosing SLAB builds its regrouped copy of the
+ * matrix on first use (synchronous; errors OOM, CUDA). */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
 
 /*

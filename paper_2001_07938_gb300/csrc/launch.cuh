@@ -91,8 +91,56 @@ lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const t
     return LILAC_OK;
 }
 
-#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, ...)                        \
+template <int V, class Op>
+lilac_status prepare_slab(lilac_csr_s* A) {
+    using L = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
+                         kSlabTileRows, kSlabWidth, kSlabBlockRows>;
+    int& bps = bps_slot<V + 64, Op, true>(A->device);
+    if (bps == 0) {
+        auto kern = spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth,
+                                     kSlabBlockRows, Op>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)L::kSmemBytes));
+        bps = occupancy_per_sm(kern, kSlabThreads, L::kSmemBytes);
+    }
+    return LILAC_OK;
+}
+
+template <int V, class Op>
+lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                         const Op& op, cudaStream_t stream) {
+    using L = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
+                         kSlabTileRows, kSlabWidth, kSlabBlockRows>;
+    // the regrouped copy holds the handle's own values; another value array
+    // (e.g. an FP32 copy) or an x that bulk copies cannot read go to STAGED
+    const bool own_vals = (const void*)val == A->val.p;
+    if (!A->slab_built || !own_vals || (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
+        return launch_staged<V, Op>(A, val, x, op, stream);
+    LILAC_TRY(prepare_slab<V, Op>(A));
+    const int bps = bps_slot<V + 64, Op, true>(A->device);
+    int64_t grid = (int64_t)A->sm_count * bps;
+    if (grid > A->slab_nblocks) grid = A->slab_nblocks;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) grid = 1;
+    spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth, kSlabBlockRows, Op>
+        <<<(unsigned)grid, kSlabThreads, L::kSmemBytes, stream>>>(
+            A->slab_val.as<typename Op::ValT>(), A->slab_col.as<int>(), A->slab_lrp.as<int>(),
+            A->slab_tiles.as<SlabTile>(), A->slab_blocks.as<SlabBlock>(), A->slab_nblocks,
+            A->ncols, x, op, A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, ...)               \
     switch (A->variant) {                                                   \
+        case LILAC_VARIANT_SLAB:                                            \
+            switch (A->vwidth) {                                            \
+                case 1:                                                     \
+                case 2:                                                     \
+                case 4: return FN_SLAB<4, Op>(__VA_ARGS__);                 \
+                case 8: return FN_SLAB<8, Op>(__VA_ARGS__);                 \
+                default: return FN_SLAB<16, Op>(__VA_ARGS__);               \
+            }                                                               \
         case LILAC_VARIANT_SCALAR:                                          \
             return FN_ROWS<1, Op>(__VA_ARGS__);                             \
         case LILAC_VARIANT_VECTOR:                                          \
@@ -115,15 +163,22 @@ lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const t
             }                                                               \
     }
 
+// SLAB launches fall back to STAGED in some cases, so prepare both.
+template <int V, class Op>
+lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
+    LILAC_TRY(prepare_slab<V, Op>(A));
+    return prepare_staged<V, Op>(A);
+}
+
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
-    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, A)
+    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, A)
 }
 
 template <class Op>
 lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, A, val, x, op, stream)
+    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, A, val, x, op, stream)
 }
 
 // Replay `body` (which enqueues work on the stream it is given) as a CUDA

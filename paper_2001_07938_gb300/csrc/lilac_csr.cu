@@ -191,6 +191,8 @@ lilac::Scratch lilac_csr_s::scratch() const {
 
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
+                                  &slab_val, &slab_col, &slab_lrp, &slab_tiles, &slab_blocks,
+                                  &slab_perm,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
@@ -333,6 +335,8 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     std::vector<Cand> cands;
     cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
     for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
+    if (slab_worthwhile(A) && ensure_slab(A, stream) == LILAC_OK)
+        for (int w : {4, 8, 16}) cands.push_back({LILAC_VARIANT_SLAB, w});
     // row-per-group kernels serialise a long row in one group: only for
     // rows no longer than a few tiles
     if (A->max_row_len <= 4 * kTileNnz) {
@@ -381,6 +385,8 @@ static void free_handle(lilac_csr A) {
     A->prof_events.clear();
     if (A->capture_stream) cudaStreamDestroy(A->capture_stream);
     lilac::DevBuf* all[] = {&A->row_ptr, &A->col_ind, &A->val, &A->val32, &A->tiles, &A->longs,
+                            &A->slab_val, &A->slab_col, &A->slab_lrp, &A->slab_tiles,
+                            &A->slab_blocks, &A->slab_perm,
                             &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
                             &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
                             &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
@@ -443,6 +449,7 @@ lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem wh
                                        s));
     A->h2d_bytes += (int64_t)(vsz * (size_t)A->nnz);
     A->val32_valid = false;  // derived FP32 copy is stale
+    LILAC_TRY(slab_refresh_values(A, s));
     return LILAC_OK;
 }
 
@@ -482,11 +489,16 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
     }
-    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_STAGED ||
+    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_SLAB ||
+        variant == LILAC_VARIANT_MERGE ||
         (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
                                (vector_width & (vector_width - 1)) != 0))) {
         set_last_error("unsupported variant / width");
         return LILAC_ERR_INVALID_ARG;
+    }
+    if (variant == LILAC_VARIANT_SLAB) {
+        DeviceGuard g(A->device);
+        LILAC_TRY(ensure_slab(A, nullptr));
     }
     A->variant = variant;
     if (vector_width) A->vwidth = vector_width;

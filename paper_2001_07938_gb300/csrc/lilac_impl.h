@@ -31,6 +31,13 @@ constexpr int kStagedThreads = LILAC_STAGED_THREADS;
 constexpr int kTileNnz = LILAC_TILE_NNZ;
 constexpr int kTileRows = LILAC_TILE_ROWS;
 constexpr int kRowsThreads = 256;
+// SLAB kernel shape: 512 threads, tiles of 2048 nonzeros touching at most
+// 512 rows, column slabs of 8192, row blocks of at most 2048 rows.
+constexpr int kSlabThreads = 512;
+constexpr int kSlabTileNnz = 2048;
+constexpr int kSlabTileRows = 512;
+constexpr int kSlabWidth = 8192;
+constexpr int kSlabBlockRows = 2048;
 constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
 
 void set_last_error(const std::string& msg);
@@ -102,6 +109,10 @@ struct lilac_csr_s {
     // STAGED schedule
     lilac::DevBuf tiles, longs;
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
+    // SLAB regrouped copy (built on first use)
+    lilac::DevBuf slab_val, slab_col, slab_lrp, slab_tiles, slab_blocks, slab_perm;
+    int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0;
+    bool slab_built = false;
     // scratch
     lilac::DevBuf partials, long_part, long_red, long_cnt, ticket, status;
     // host-pointer staging (marshaling of x / y for LILAC_MEM_HOST calls)
@@ -142,6 +153,9 @@ struct DeviceGuard {
 
 lilac_status check_handle(lilac_csr A);
 lilac_status make_val32(lilac_csr A, cudaStream_t stream);
+lilac_status ensure_slab(lilac_csr A, cudaStream_t stream);
+lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
+bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status check_device_status(lilac_csr A, cudaStream_t stream);
 int vec_grid(const lilac_csr_s* A, int64_t n);
 

@@ -285,3 +285,216 @@ __global__ void __launch_bounds__(THREADS)
 }
 
 }  // namespace lilac
+
+namespace lilac {
+
+// ---------------------------------------------------------------------------
+// SLAB kernel: x read from shared memory instead of L2.
+//
+// The matrix is regrouped once (lilac_slab.cu) into row blocks x column
+// slabs: within a row block, all nonzeros whose column lies in slab s
+// (columns [s*W, (s+1)*W)) are stored together, row by row, with local
+// column indices col - s*W and a per-(block, slab) row-pointer array.  A CTA
+// takes a row block, keeps slab s of x in shared memory (two slab buffers,
+// the next one loaded by a bulk copy while the current one is used), streams
+// the block's nonzeros slab by slab in tiles (double-buffered bulk copies as
+// in the STAGED kernel), gathers x from shared memory, and adds each row's
+// partial sums into a per-row accumulator in shared memory.  When the block
+// is done, the epilogue runs once per row.  Gathers never leave the SM, so
+// the kernel streams the matrix at HBM speed when rows have many nonzeros
+// per column slab.
+struct SlabTile {
+    int k0, k1;      // nonzeros [k0, k1) of the regrouped arrays
+    int lrp_idx;     // index in the row-pointer array of the tile's first row
+    int rl0;         // block-local index of that row
+    int nrows;       // rows [rl0, rl0 + nrows) overlap the tile
+    int slab;        // column slab
+    int next_slab;   // if this is the first tile of its slab: the slab after it (-1: none)
+    int first;       // 1: first tile of its slab within the block
+};
+
+struct SlabBlock {
+    int r0, nrows, tile_begin, tile_end;
+};
+
+template <class ValT, class VecT, class AccT, int TN, int TRS, int W, int RB>
+struct SlabLayout {
+    static constexpr size_t kXBytes = sizeof(VecT) * W;
+    static constexpr size_t kYBytes = sizeof(AccT) * RB;
+    static constexpr int kValElems = TN + 8;
+    static constexpr int kRpElems = TRS + 8;
+    static constexpr size_t kValBytes = sizeof(ValT) * kValElems;
+    static constexpr size_t kColBytes = sizeof(int) * kValElems;
+    static constexpr size_t kRpBytes = sizeof(int) * kRpElems;
+    static constexpr size_t kStageBytes = kValBytes + kColBytes + kRpBytes;
+    static constexpr size_t kProdBytes = sizeof(AccT) == sizeof(ValT) ? 0 : sizeof(AccT) * kValElems;
+    static constexpr size_t kStageOff = 2 * kXBytes + kYBytes;
+    static constexpr size_t kSmemBytes = kStageOff + 2 * kStageBytes + kProdBytes;
+};
+
+template <int V, int THREADS, int TN, int TRS, int W, int RB, class Op>
+__global__ void __launch_bounds__(THREADS, 1)
+    spmv_slab_kernel(const typename Op::ValT* __restrict__ sval, const int* __restrict__ scol,
+                     const int* __restrict__ lrp, const SlabTile* __restrict__ tiles,
+                     const SlabBlock* __restrict__ blocks, int nblocks, int ncols,
+                     const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
+    if (op.skip()) return;
+    using ValT = typename Op::ValT;
+    using VecT = typename Op::VecT;
+    using AccT = typename Op::AccT;
+    using L = SlabLayout<ValT, VecT, AccT, TN, TRS, W, RB>;
+    constexpr int NR = Op::NR;
+    constexpr int NGROUPS = THREADS / V;
+    constexpr int IPT = TN / THREADS;
+    static_assert(TN % THREADS == 0, "tile nonzeros must be a multiple of the block size");
+
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar[2];   // matrix stages
+    __shared__ __align__(8) uint64_t xbar[2];  // x slab buffers
+    __shared__ SlabTile sdesc[2];
+
+    VecT* xs[2] = {reinterpret_cast<VecT*>(smem), reinterpret_cast<VecT*>(smem + L::kXBytes)};
+    AccT* yacc = reinterpret_cast<AccT*>(smem + 2 * L::kXBytes);
+    auto stage_ptr = [&](int st) { return smem + L::kStageOff + st * L::kStageBytes; };
+    AccT* prod_extra = reinterpret_cast<AccT*>(smem + L::kStageOff + 2 * L::kStageBytes);
+
+    double red[NR > 0 ? NR : 1] = {};
+    const int tid = threadIdx.x;
+    const int lane = tid & (V - 1);
+    const int group = tid / V;
+    const unsigned mask = group_mask<V>(tid);
+
+    uint64_t policy = 0;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_init(&xbar[0], 1);
+        mbar_init(&xbar[1], 1);
+        fence_mbar_init();
+        policy = l2_policy_evict_first();
+    }
+    __syncthreads();
+
+    // per-buffer completed-load counts (the same in every thread)
+    uint32_t xloads[2] = {0u, 0u};
+    uint32_t sloads[2] = {0u, 0u};
+    int xslab[2] = {-1, -1};
+    bool failed = false;
+
+    // Thread 0: load x slab `sl` into buffer b (16-byte-aligned bulk part by
+    // the copy engine, the last < 16 bytes by plain loads).
+    auto issue_x = [&](int sl, int b) {
+        const int c0 = sl * W;
+        const int ne = min(W, ncols - c0);
+        const uint32_t bytes = (uint32_t)ne * (uint32_t)sizeof(VecT);
+        const uint32_t bulk = bytes & ~15u;
+        for (uint32_t e = bulk / sizeof(VecT); e < (uint32_t)ne; ++e) xs[b][e] = x[c0 + e];
+        mbar_arrive_expect_tx(&xbar[b], bulk);
+        if (bulk) bulk_g2s(xs[b], x + c0, bulk, &xbar[b], l2_policy_evict_normal());
+    };
+
+    auto issue_tile = [&](int ti, int st) {
+        const SlabTile t = tiles[ti];
+        sdesc[st] = t;
+        unsigned char* base = stage_ptr(st);
+        const int ka = t.k0 & ~3;
+        const int kz = (t.k1 + 3) & ~3;
+        const uint32_t nk = (uint32_t)(kz - ka);
+        const int ra = t.lrp_idx & ~3;
+        const int rz = (t.lrp_idx + t.nrows + 1 + 3) & ~3;
+        const uint32_t nr = (uint32_t)(rz - ra);
+        mbar_arrive_expect_tx(&bar[st], nk * (uint32_t)(sizeof(ValT) + sizeof(int)) + nr * 4u);
+        if (nk) {
+            bulk_g2s(base, sval + ka, nk * (uint32_t)sizeof(ValT), &bar[st], policy);
+            bulk_g2s(base + L::kValBytes, scol + ka, nk * 4u, &bar[st], policy);
+        }
+        bulk_g2s(base + L::kValBytes + L::kColBytes, lrp + ra, nr * 4u, &bar[st], policy);
+    };
+
+    for (int blk = blockIdx.x; blk < nblocks && !failed; blk += gridDim.x) {
+        const SlabBlock B = blocks[blk];
+        for (int r = tid; r < B.nrows; r += THREADS) yacc[r] = AccT(0);
+        const int tb = B.tile_begin, te = B.tile_end;
+        if (tb < te) {
+            const SlabTile t0 = tiles[tb];
+            xslab[0] = t0.slab;
+            xslab[1] = t0.next_slab;
+            if (tid == 0) {
+                fence_proxy_async_smem();
+                issue_x(t0.slab, 0);
+                if (t0.next_slab >= 0) issue_x(t0.next_slab, 1);
+                issue_tile(tb, 0);
+            }
+            ++xloads[0];
+            if (t0.next_slab >= 0) ++xloads[1];
+        }
+        for (int i = tb; i < te; ++i) {
+            const int st = (i - tb) & 1;
+            if (i + 1 < te && tid == 0) {
+                fence_proxy_async_smem();
+                issue_tile(i + 1, st ^ 1);
+            }
+            ++sloads[st];
+            bool ok = mbar_wait_bounded(&bar[st], (sloads[st] - 1u) & 1u);
+            const SlabTile t = sdesc[st];
+            // x buffer of this tile; on the first tile of a slab (not the
+            // block's first), the other buffer held the previous slab, whose
+            // tiles are all done: load the slab after this one into it
+            const int xb = xslab[0] == t.slab ? 0 : 1;
+            if (t.first && i > tb && t.next_slab >= 0) {
+                if (tid == 0) issue_x(t.next_slab, xb ^ 1);
+                xslab[xb ^ 1] = t.next_slab;
+                ++xloads[xb ^ 1];
+            }
+            ok = ok && mbar_wait_bounded(&xbar[xb], (xloads[xb] - 1u) & 1u);
+            if (!__syncthreads_and(ok ? 1 : 0)) {
+                failed = true;
+                break;
+            }
+            unsigned char* base = stage_ptr(st);
+            const ValT* vs = reinterpret_cast<const ValT*>(base);
+            const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
+            const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
+            AccT* prod = L::kProdBytes ? prod_extra : reinterpret_cast<AccT*>(base);
+            const VecT* xv = xs[xb];
+            const int ka = t.k0 & ~3;
+            const int kb0 = t.k0 - ka, ke0 = t.k1 - ka;
+            // Phase A: products, x from shared memory
+#pragma unroll
+            for (int j = 0; j < IPT; ++j) {
+                const int k = kb0 + j * THREADS + tid;
+                if (k < ke0) prod[k] = AccT(vs[k]) * AccT(xv[cs[k]]);
+            }
+            __syncthreads();
+            // Phase B: each row's part of the tile, added to its accumulator
+            const int ra = t.lrp_idx & ~3;
+            for (int rr = group; rr < t.nrows; rr += NGROUPS) {
+                const int a = max(rps[t.lrp_idx - ra + rr], t.k0) - ka;
+                const int b = min(rps[t.lrp_idx - ra + rr + 1], t.k1) - ka;
+                AccT sum = AccT(0);
+                for (int k = a + lane; k < b; k += V) sum += prod[k];
+                if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+                if (lane == 0 && b > a) yacc[t.rl0 + rr] += sum;
+            }
+            fence_proxy_async_smem();
+            __syncthreads();
+        }
+        if (failed) break;
+        // epilogue: one call per row of the block
+        __syncthreads();
+        for (int r = tid; r < B.nrows; r += THREADS) op.row(B.r0 + r, yacc[r], red);
+        __syncthreads();
+    }
+    if (failed) {
+        if (tid == 0) atomicExch(s.status, DEV_TIMEOUT);
+        return;
+    }
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+    }
+}
+
+}  // namespace lilac

@@ -58,4 +58,5 @@ def true_rel_residual(A, b, x):
     return float(np.linalg.norm(r) / np.linalg.norm(b))
 
 
-ALL_VARIANTS = [(1, 1)] + [(2, w) for w in (2, 4, 8, 16, 32)] + [(3, w) for w in (1, 2, 4, 8, 16, 32)]
+ALL_VARIANTS = ([(1, 1)] + [(2, w) for w in (2, 4, 8, 16, 32)] + [(3, w) for w in (1, 2, 4, 8, 16, 32)]
+                + [(5, w) for w in (4, 8, 16)])
