@@ -317,6 +317,7 @@ def run_lilac(args):
     minfo = wl.M.info()
     kname = {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {minfo['vector_width']} lanes/row)",
              3: f"spmv_staged_kernel ({minfo['vector_width']} lanes/row)",
+             4: f"spmv_merge_kernel ({minfo['vector_width']} lanes/row)",
              5: "spmv_slab_kernel (x slabs in shared memory)"}.get(minfo["variant"], "spmv")
     peak, peak_kind = _peaks()
     achieved = wl.spmv_bytes() / (spmv_ms / 1000.0) / 1e9

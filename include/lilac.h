@@ -77,7 +77,8 @@ typedef enum {
     LILAC_VARIANT_VECTOR = 2, /* V lanes per row, V in {2,4,8,16,32}; V = 32 is warp-per-row */
     LILAC_VARIANT_STAGED = 3, /* nnz-balanced row tiles staged in shared memory by bulk
                                  asynchronous copies; rows longer than a tile are split */
-    LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) */
+    LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) over CTAs, rows that
+                                 cross CTAs finished from carries; lanes per row 1, 4 or 16 */
     LILAC_VARIANT_SLAB = 5    /* row blocks x column slabs, built once per matrix: x is read
                                  from shared memory, one slab of columns at a time; x must be
                                  16-byte aligned (else STAGED runs) */

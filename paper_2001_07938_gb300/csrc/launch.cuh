@@ -92,6 +92,23 @@ lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const t
 }
 
 template <int V, class Op>
+lilac_status prepare_merge(lilac_csr_s* A) {
+    (void)A;
+    return LILAC_OK;
+}
+
+template <int V, class Op>
+lilac_status launch_merge(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                          const Op& op, cudaStream_t stream) {
+    CsrView<typename Op::ValT> view{A->row_ptr.as<int>(), A->col_ind.as<int>(), val, A->rows};
+    spmv_merge_kernel<V, kMergeThreads, kMergeItems, Op><<<(unsigned)A->merge_grid, kMergeThreads, 0, stream>>>(
+        view, A->nnz, A->merge_coords.as<int2>(), A->merge_per_cta, x, op, A->partials.as<double>(),
+        A->merge_carries.as<MergeCarry>(), A->ticket.as<unsigned>());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
     using L = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
                          kSlabTileRows, kSlabWidth, kSlabBlockRows>;
@@ -131,8 +148,15 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
     return LILAC_OK;
 }
 
-#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, ...)               \
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, ...)     \
     switch (A->variant) {                                                   \
+        case LILAC_VARIANT_MERGE:                                           \
+            switch (A->vwidth) {                                            \
+                case 1: return FN_MERGE<1, Op>(__VA_ARGS__);                \
+                case 2:                                                     \
+                case 4: return FN_MERGE<4, Op>(__VA_ARGS__);                \
+                default: return FN_MERGE<16, Op>(__VA_ARGS__);              \
+            }                                                               \
         case LILAC_VARIANT_SLAB:                                            \
             switch (A->vwidth) {                                            \
                 case 1:                                                     \
@@ -172,13 +196,14 @@ lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
 
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
-    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, A)
+    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge, A)
 }
 
 template <class Op>
 lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, A, val, x, op, stream)
+    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, A, val, x, op,
+                        stream)
 }
 
 // Replay `body` (which enqueues work on the stream it is given) as a CUDA

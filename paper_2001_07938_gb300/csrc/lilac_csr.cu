@@ -148,6 +148,30 @@ static void build_tiles(const std::vector<int32_t>& rp, int rows, std::vector<Ti
     }
 }
 
+// Merge-path partition of (rows + nnz) path items over about four CTAs per
+// SM, each range at least one sub-tile long; the start point of every range
+// is found on the host once (the same search the kernel would do).
+static void build_merge_partition(const std::vector<int32_t>& rp, int rows, int64_t nnz,
+                                  int sm_count, std::vector<int2>& coords, int64_t& per_cta) {
+    const int64_t total = (int64_t)rows + nnz;
+    const int64_t target = std::max<int64_t>(1, (int64_t)sm_count * 4);
+    per_cta = std::max<int64_t>(kMergeItems, (total + target - 1) / target);
+    const int64_t G = std::max<int64_t>(1, (total + per_cta - 1) / per_cta);
+    coords.resize((size_t)G);
+    for (int64_t c = 0; c < G; ++c) {
+        const int64_t d = c * per_cta;
+        int64_t lo = std::max<int64_t>(0, d - nnz), hi = std::min<int64_t>(d, rows);
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)rp[(size_t)mid + 1] <= d - mid - 1)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        coords[(size_t)c] = make_int2((int)lo, (int)(d - lo));
+    }
+}
+
 // Lanes per row from the mean row length: the smallest power of two >= mean/2.
 static int pick_width(double mean) {
     int v = 1;
@@ -192,7 +216,7 @@ lilac::Scratch lilac_csr_s::scratch() const {
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
                                   &slab_val, &slab_col, &slab_lrp, &slab_tiles, &slab_blocks,
-                                  &slab_perm,
+                                  &slab_perm, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
@@ -305,6 +329,16 @@ static lilac_status create_impl(int32_t rows, int32_t ncols, int64_t nnz, const 
         LILAC_CUDA_TRY(cudaMemcpyAsync(A->longs.p, longs.data(), sizeof(LongRow) * longs.size(),
                                        cudaMemcpyHostToDevice, stream));
     }
+    // MERGE partition
+    {
+        std::vector<int2> coords;
+        build_merge_partition(rp, rows, nnz, A->sm_count, coords, A->merge_per_cta);
+        A->merge_grid = (int)coords.size();
+        LILAC_TRY(A->merge_coords.alloc(sizeof(int2) * coords.size()));
+        LILAC_TRY(A->merge_carries.alloc(sizeof(MergeCarry) * coords.size()));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(A->merge_coords.p, coords.data(), sizeof(int2) * coords.size(),
+                                       cudaMemcpyHostToDevice, stream));
+    }
     // scratch
     LILAC_TRY(A->partials.alloc(sizeof(double) * kMaxCtas * kMaxRed));
     LILAC_TRY(A->long_part.alloc(sizeof(double) * std::max(1, A->nlong_chunks)));
@@ -335,8 +369,9 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     std::vector<Cand> cands;
     cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
     for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
-    if (slab_worthwhile(A) && ensure_slab(A, stream) == LILAC_OK)
-        for (int w : {4, 8, 16}) cands.push_back({LILAC_VARIANT_SLAB, w});
+    for (int w : {1, 4, 16}) cands.push_back({LILAC_VARIANT_MERGE, w});
+    // SLAB is not a candidate yet: every CTA still loads all of x slab by
+    // slab, and on the matrices it targets it measured slower than VECTOR.
     // row-per-group kernels serialise a long row in one group: only for
     // rows no longer than a few tiles
     if (A->max_row_len <= 4 * kTileNnz) {
@@ -386,7 +421,7 @@ static void free_handle(lilac_csr A) {
     if (A->capture_stream) cudaStreamDestroy(A->capture_stream);
     lilac::DevBuf* all[] = {&A->row_ptr, &A->col_ind, &A->val, &A->val32, &A->tiles, &A->longs,
                             &A->slab_val, &A->slab_col, &A->slab_lrp, &A->slab_tiles,
-                            &A->slab_blocks, &A->slab_perm,
+                            &A->slab_blocks, &A->slab_perm, &A->merge_coords, &A->merge_carries,
                             &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
                             &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
                             &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
@@ -490,7 +525,6 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         return LILAC_ERR_INVALID_ARG;
     }
     if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_SLAB ||
-        variant == LILAC_VARIANT_MERGE ||
         (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
                                (vector_width & (vector_width - 1)) != 0))) {
         set_last_error("unsupported variant / width");

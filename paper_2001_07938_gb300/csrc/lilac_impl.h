@@ -38,6 +38,10 @@ constexpr int kSlabTileNnz = 2048;
 constexpr int kSlabTileRows = 512;
 constexpr int kSlabWidth = 8192;
 constexpr int kSlabBlockRows = 2048;
+// MERGE kernel shape: 256 threads, sub-tiles of 2048 path items, about four
+// CTAs per SM.
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 2048;
 constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
 
 void set_last_error(const std::string& msg);
@@ -113,6 +117,10 @@ struct lilac_csr_s {
     lilac::DevBuf slab_val, slab_col, slab_lrp, slab_tiles, slab_blocks, slab_perm;
     int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0;
     bool slab_built = false;
+    // MERGE partition (computed at create): start of each CTA's path range
+    lilac::DevBuf merge_coords, merge_carries;
+    int merge_grid = 0;
+    int64_t merge_per_cta = 0;
     // scratch
     lilac::DevBuf partials, long_part, long_red, long_cnt, ticket, status;
     // host-pointer staging (marshaling of x / y for LILAC_MEM_HOST calls)

@@ -498,3 +498,219 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 }  // namespace lilac
+
+namespace lilac {
+
+// ---------------------------------------------------------------------------
+// MERGE kernel: merge-path partition (Merrill & Garland, "Merge-based
+// parallel sparse matrix-vector multiplication", SC 2016).  The merge of the
+// row-end list (row_ptr[1..rows]) with the nonzero indices (0..nnz-1) has
+// rows + nnz items; CTA c takes items [c*P, (c+1)*P), so every CTA gets the
+// same mix of row ends and nonzeros whatever the row lengths.  A CTA walks
+// its items in sub-tiles of ITEMS: products of the sub-tile's nonzeros go to
+// shared memory, the sub-tile's end point on the path is found by a search
+// in shared memory, and groups of V lanes sum each row's piece.  A row that
+// is still open at the end of a sub-tile carries its sum to the next one.
+// Across CTAs, each CTA records a head piece (its first row, which is open
+// at the CTA's start, if it ends in this CTA) and a tail piece (the row
+// open at its end); the last CTA to finish adds, for each row that crosses
+// CTAs, the tail pieces and the closing head piece in CTA order, and runs
+// the epilogue for it.
+struct MergeCarry {
+    int head_row;  // -1: none
+    int tail_row;  // -1: none
+    double head_v;
+    double tail_v;
+};
+
+// Path point d: (i, j) with i + j = d, i = row ends consumed, j = nonzeros
+// consumed; a nonzero j is consumed before the end of row i when j < row_ptr[i+1].
+__device__ __forceinline__ int2 merge_path_search(int64_t d, const int* __restrict__ row_ptr,
+                                                  int rows, int64_t nnz) {
+    int64_t lo = d - nnz > 0 ? d - nnz : 0;
+    int64_t hi = d < rows ? d : rows;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if ((int64_t)__ldg(row_ptr + mid + 1) <= d - mid - 1)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return make_int2((int)lo, (int)(d - lo));
+}
+
+template <int V, int THREADS, int ITEMS, class Op>
+__global__ void __launch_bounds__(THREADS)
+    spmv_merge_kernel(CsrView<typename Op::ValT> A, int64_t nnz, const int2* __restrict__ coords,
+                      int64_t per_cta, const typename Op::VecT* __restrict__ x, Op op,
+                      double* __restrict__ partials, MergeCarry* __restrict__ carries,
+                      unsigned* __restrict__ ticket) {
+    using AccT = typename Op::AccT;
+    constexpr int NR = Op::NR;
+    constexpr int NGROUPS = THREADS / V;
+    constexpr int IPT = ITEMS / THREADS;
+    static_assert(ITEMS % THREADS == 0, "items per sub-tile must be a multiple of the block size");
+    if (op.skip()) return;
+
+    __shared__ int rp_s[ITEMS + 2];
+    __shared__ AccT prod_s[ITEMS];
+    __shared__ int s_i, s_j, s_ie, s_je, s_head_pending, s_head_row;
+    __shared__ AccT s_running, s_running_next, s_head_v;
+    __shared__ double sh_red[kMaxRed * 32];
+    __shared__ int am_last;
+
+    const int tid = threadIdx.x;
+    const int lane = tid & (V - 1);
+    const int group = tid / V;
+    const unsigned mask = group_mask<V>(tid);
+    const int rows = A.rows;
+    const int64_t total = (int64_t)rows + nnz;
+    const int64_t D0 = (int64_t)blockIdx.x * per_cta;
+    const int64_t D1 = D0 + per_cta < total ? D0 + per_cta : total;
+    double red[NR > 0 ? NR : 1] = {};
+
+    if (tid == 0) {
+        int2 st = make_int2(rows, (int)nnz);
+        if (D0 < total) st = coords ? coords[blockIdx.x] : merge_path_search(D0, A.row_ptr, rows, nnz);
+        s_i = st.x;
+        s_j = st.y;
+        // the row open at the CTA's start is the previous CTA's tail: its
+        // piece here always goes through the carries
+        s_head_pending = (blockIdx.x > 0 && D0 < total && st.x < rows) ? 1 : 0;
+        s_head_row = -1;
+        s_head_v = AccT(0);
+        s_running = AccT(0);
+    }
+    __syncthreads();
+    for (int64_t d = D0; d < D1;) {
+        const int64_t d_end = d + ITEMS < D1 ? d + ITEMS : D1;
+        const int i = s_i, j = s_j;
+        // row_ptr[i .. i + nrw) and the products of nonzeros [j, jz)
+        const int nrw = min(ITEMS + 2, rows + 1 - i);
+        for (int t = tid; t < nrw; t += THREADS) rp_s[t] = __ldg(A.row_ptr + i + t);
+        const int jz = (int)min((int64_t)j + ITEMS, nnz);
+        int cj[IPT];
+        typename Op::VecT xj[IPT];
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int k = j + q * THREADS + tid;
+            cj[q] = k < jz ? ld_stream(A.col_ind + k) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int k = j + q * THREADS + tid;
+            xj[q] = k < jz ? __ldg(x + cj[q]) : typename Op::VecT(0);
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const int k = j + q * THREADS + tid;
+            if (k < jz) prod_s[k - j] = AccT(ld_stream(A.val + k)) * AccT(xj[q]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // end point of the sub-tile on the path, searched in shared memory
+            int64_t lo = d_end - nnz > i ? d_end - nnz : i;
+            int64_t hi = d_end - j < rows ? d_end - j : rows;
+            while (lo < hi) {
+                const int64_t mid = (lo + hi) >> 1;
+                if ((int64_t)rp_s[mid + 1 - i] <= d_end - mid - 1)
+                    lo = mid + 1;
+                else
+                    hi = mid;
+            }
+            s_ie = (int)lo;
+            s_je = (int)(d_end - lo);
+            s_running_next = AccT(0);
+        }
+        __syncthreads();
+        const int ie = s_ie, je = s_je;
+        // rows [i, ie) end in this sub-tile; row ie (if any) stays open
+        const int nr = ie - i + (ie < rows ? 1 : 0);
+        for (int rr = group; rr < nr; rr += NGROUPS) {
+            const int r = i + rr;
+            const int a = max(rp_s[rr], j) - j;
+            const int b = (r < ie ? rp_s[rr + 1] : je) - j;
+            AccT sum = AccT(0);
+            for (int k = a + lane; k < b; k += V) sum += prod_s[k];
+            if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+            if (lane == 0) {
+                if (r == i) sum += s_running;
+                if (r < ie) {
+                    if (r == i && s_head_pending) {
+                        s_head_row = r;
+                        s_head_v = sum;
+                    } else {
+                        op.row(r, sum, red);
+                    }
+                } else {
+                    s_running_next = sum;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_running = ie < rows ? s_running_next : AccT(0);
+            if (ie > i) s_head_pending = 0;
+            s_i = ie;
+            s_j = je;
+        }
+        __syncthreads();
+        d = d_end;
+    }
+    // publish carries and partial sums; the last CTA fixes up and finishes
+    double tot[NR > 0 ? NR : 1];
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        block_sum<NR, THREADS>(r2, tot, sh_red);
+    }
+    if (tid == 0) {
+        MergeCarry mc;
+        mc.head_row = s_head_row;
+        mc.head_v = (double)s_head_v;
+        const bool open_tail = D0 < total && s_i < rows;
+        mc.tail_row = open_tail ? s_i : -1;
+        mc.tail_v = open_tail ? (double)s_running : 0.0;
+        carries[blockIdx.x] = mc;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) partials[blockIdx.x * NR + q] = tot[q];
+        __threadfence();
+        const unsigned t = atomicAdd(ticket, 1u);
+        am_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    const int G = (int)gridDim.x;
+    double fred[NR > 0 ? NR : 1] = {};
+    for (int c = tid; c < G; c += THREADS) {
+        const int r = __ldcg(&carries[c].tail_row);
+        if (r < 0 || (c > 0 && __ldcg(&carries[c - 1].tail_row) == r)) continue;
+        // this CTA holds the first piece of row r: add the later pieces in order
+        AccT v = AccT(__ldcg(&carries[c].tail_v));
+        for (int k = c + 1; k < G; ++k) {
+            if (__ldcg(&carries[k].head_row) == r) {
+                v += AccT(__ldcg(&carries[k].head_v));
+                break;
+            }
+            if (__ldcg(&carries[k].tail_row) != r) break;
+            v += AccT(__ldcg(&carries[k].tail_v));
+        }
+        op.row(r, v, fred);
+    }
+    if constexpr (NR > 0) {
+        double acc[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = fred[q];
+        for (int c = tid; c < G; c += THREADS) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&partials[c * NR + q]);
+        }
+        block_sum<NR, THREADS>(acc, tot, sh_red);
+        if (tid == 0) op.finish(tot);
+    }
+    if (tid == 0) *ticket = 0u;
+}
+
+}  // namespace lilac
