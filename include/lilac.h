@@ -233,6 +233,33 @@ lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_mem where,
 lilac_status lilac_pagerank(lilac_csr AT, void* x, int32_t init_uniform, int32_t iters,
                             double damping, double* l1_per_iter, lilac_mem where, void* stream);
 
+/*
+ * y = A x on CSR arrays the caller already holds on the device, with no
+ * device allocation.  The paper has no counterpart: this is for callers that
+ * must not call cudaMalloc -- e.g. code running while another component owns
+ * the device memory through its own pool and budget, or a latency-critical
+ * loop where cudaMalloc / cudaFree (which can synchronise the device) are
+ * not acceptable -- and that therefore cannot create a handle.
+ *   rows, ncols, nnz   sizes; rows + nnz < 2^31 (else LILAC_ERR_INVALID_ARG)
+ *   row_ptr, col_ind, vals, x, y   device pointers, caller-owned; the arrays
+ *                      must form valid CSR (row_ptr[0] = 0, non-decreasing,
+ *                      row_ptr[rows] = nnz, 0 <= col_ind < ncols): nothing is
+ *                      validated, and invalid arrays are read out of range
+ *   dtype              type of vals, x and y (FP64 accumulates in FP64, FP32 in FP32)
+ *   stream             cudaStream_t; the call is asynchronous
+ * Runs the MERGE kernel with its scratch (carry records, per-CTA partial sums,
+ * arrival counter; 82,176 bytes, at most 2048 CTA ranges) in one fixed array
+ * in device memory that every GPU loading this library holds until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Every call shares the array: calls whose
+ * kernels overlap on the GPU (e.g. on two streams at once) race and give
+ * wrong results.  Each call clears the counter that must start at zero.
+ */
+lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
+                                const int32_t* col_ind, const void* vals, lilac_dtype dtype,
+                                const void* x, void* y, void* stream);
+
 /* Clear a sticky device error of the handle and re-zero its scratch memory. */
 lilac_status lilac_csr_reset_error(lilac_csr A);
 
