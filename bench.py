@@ -1,24 +1,28 @@
 #!/usr/bin/env python
-"""Benchmark of the GB300 SpMV / CG / PageRank library.
+"""Benchmark of the GB300 SpMV / CG / PageRank library (one JSON line on stdout).
 
-Default workload (one JSON line on stdout): unpreconditioned FP64 CG, 75
-iterations, on a random SPD CSR matrix with n = 75,000 and ~181 nonzeros per
-row at uniformly random columns (values U[0,1), symmetrised, diagonal = row
-sum + 20), b = ones, int32 indices.  One step = one full solve through
-lilac_cg (device buffers, resident matrix).  The metric is solves/s;
-the roofline object reports the fused SpMV kernel (q = A p with p.q) against
-the measured HBM copy bandwidth.
+Default workload (cg75k): unpreconditioned FP64 CG, 75 iterations, on a
+random SPD CSR matrix with n = 75,000 and ~181 nonzeros per row at uniformly
+random columns (values U[0,1), symmetrised, diagonal = row sum + 20),
+b = ones, int32 indices.  One step = one full solve through lilac_cg (device
+buffers, resident matrix); the metric is solves/s, and the roofline object
+reports the fused SpMV kernel (q = A p with p.q) against the measured HBM
+copy bandwidth.
 
-Other workloads: --workload spmv2d (2D Laplacian 64x64, 1000 SpMV calls per
-step), pagerank22 (R-MAT scale 22, 20 FP32 PageRank iterations), ir192
-(3D Poisson 192^3, mixed-precision CG to 1e-10).
+Other workloads (--workload):
+  spmv2d      2D Laplacian 64x64 (n = 4,096, nnz = 20,224) FP64, one step = 1000
+              lilac_spmv calls on the resident matrix; metric SpMV GB/s
+  pagerank22  R-MAT scale 22 (4,194,304 vertices, ~65M edges) FP32 PageRank,
+              20 iterations per step; metric SpMV GB/s of the fused iterations
+  ir192       3D Poisson 192^3 (n = 7,077,888), FP32 inner CG + FP64 refinement
+              to 1e-10; metric solves/s, with plain FP64 CG timed beside it
 
 --impl reference times the CPU oracle (sequential FP64 C, the paper's
 baseline kind: sequential code at -O2) on the same workload on the host
-cores, one bounded sample per step.
+cores, one bounded sample per step, rank 0 only.
 
-Multi-GPU: replicas only (each rank solves its own copy; no collective on
-the data path); value = solves of all ranks / max-over-ranks time.
+Multi-GPU: replicas only (each rank runs its own copy; no collective on the
+data path); value = work of all ranks / max-over-ranks time.
 """
 from __future__ import annotations
 
@@ -124,33 +128,61 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def _spmv_bytes(n, ncols, nnz, vb):
+    """Roofline bytes of one SpMV: nnz*(vb+4) + (n+1)*4 + ncols*vb + n*vb."""
+    return nnz * (vb + 4) + (n + 1) * 4 + ncols * vb + n * vb
+
+
+def _kernel_name(M):
+    info = M.info()
+    w = info["vector_width"]
+    return {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {w} lanes/row)",
+            3: f"spmv_staged_kernel ({w} lanes/row)", 4: f"spmv_merge_kernel ({w} lanes/row)",
+            5: f"spmv_slab_kernel ({w} lanes/row)"}.get(info["variant"], "spmv")
+
+
 # --- workloads ------------------------------------------------------------------
 
-class CG75k:
+class Workload:
+    """A benchmark workload: setup / step / check / roofline_sample /
+    e2e_setup / e2e_step / cpu_sample / config; `work_per_step` units of
+    `unit` x seconds per step."""
+    flush_l2 = False
+    work_per_step = 1.0
+
+    def __init__(self, L, torch):
+        self.L, self.torch = L, torch
+
+    def _profiled(self, k, nbytes, what):
+        """Average SpMV launch duration over k steps (lilac_csr_profile:
+        CUDA event pairs on the launching stream, inside the captured graphs)."""
+        L = self.L
+        L.lilac_csr_profile(self.M.handle, True)
+        for _ in range(k):
+            self.step()
+        ms, n = L.lilac_csr_profile(self.M.handle, False)
+        return ms / n, n, nbytes, _kernel_name(self.M) + what
+
+
+class CG75k(Workload):
     name = "cg_spd_n75000_75it"
     unit = "solves/s"
     dtype = "f64"
+    iters = 75
 
     def __init__(self, L, torch):
+        super().__init__(L, torch)
         from paper_2001_07938_gb300 import inputs
-        self.L, self.torch = L, torch
         self.A, self.b = inputs.workload_spd_cg()
-        self.iters = 75
 
     def config(self):
         A = self.A
+        mat = A.nnz * 12 + (A.n + 1) * 4
         return {"workload": self.name, "matrix": "random SPD, ~181 nnz/row, uniform columns",
                 "n": A.n, "nnz": A.nnz, "iterations": self.iters, "precision": "fp64",
                 "index": "int32", "rhs": "ones",
-                "l2": f"inputs larger than L2: matrix {self._mat_bytes() / 1e6:.0f} MB > "
+                "l2": f"inputs larger than L2: matrix {mat / 1e6:.0f} MB > "
                       f"{L2_BYTES / 1e6:.0f} MB L2, no flush"}
-
-    def _mat_bytes(self):
-        return self.A.nnz * 12 + (self.A.n + 1) * 4
-
-    def spmv_bytes(self):
-        A = self.A
-        return A.nnz * (8 + 4) + (A.n + 1) * 4 + A.ncols * 8 + A.n * 8
 
     def setup(self):
         torch, L = self.torch, self.L
@@ -171,15 +203,9 @@ class CG75k:
         return {"iters": info.iters, "true_rel_res": info.true_rel_res}
 
     def roofline_sample(self, k):
-        """Average duration of the fused SpMV (q = A p, p.q) from CUDA events
-        recorded on its stream inside the captured solve graph."""
-        ms, n = 0.0, 0
-        for _ in range(k):
-            st, info = self.M.cg(self.bd, self.xd, max_iter=self.iters, rtol=0.0,
-                                 true_residual=False, profile=True)
-            ms += info.spmv_ms
-            n += info.spmv_launches
-        return ms / n, n
+        A = self.A
+        return self._profiled(k, _spmv_bytes(A.n, A.ncols, A.nnz, 8),
+                              " with the CG epilogue (q = A p, p.q fused)")
 
     def e2e_setup(self):
         torch = self.torch
@@ -213,7 +239,251 @@ class CG75k:
         self.M.close()
 
 
-WORKLOADS = {"cg75k": CG75k}
+class SpMV2D(Workload):
+    name = "spmv_laplacian2d_m64_1000calls"
+    unit = "GB/s"
+    dtype = "f64"
+    flush_l2 = True
+    calls = 1000
+
+    def __init__(self, L, torch):
+        super().__init__(L, torch)
+        from paper_2001_07938_gb300 import inputs
+        self.A, self.x = inputs.workload_laplacian2d_spmv(64)
+        self.work_per_step = self.calls * self.spmv_bytes() / 1e9
+
+    def spmv_bytes(self):
+        A = self.A
+        return _spmv_bytes(A.n, A.ncols, A.nnz, 8)
+
+    def config(self):
+        A = self.A
+        return {"workload": self.name, "matrix": "2D 5-point Laplacian, 64x64 grid",
+                "n": A.n, "nnz": A.nnz, "calls_per_step": self.calls, "precision": "fp64",
+                "index": "int32", "x": "uniform [-1,1], seed 0",
+                "l2": "L2 flushed (256 MB write) between steps; within a step the 325 KB "
+                      "matrix stays L2-resident, which is the workload (1000 repeated calls)"}
+
+    def setup(self):
+        torch, L = self.torch, self.L
+        self.M = L.CsrMatrix.from_csr(self.A)
+        self.xd = torch.from_numpy(self.x).cuda()
+        self.yd = torch.empty(self.A.n, dtype=torch.float64, device="cuda")
+        self.launches_per_step = self.calls
+        self.px, self.py = self.xd.data_ptr(), self.yd.data_ptr()
+
+    def step(self):
+        L, h = self.L, self.M.handle
+        for _ in range(self.calls):
+            L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE)
+
+    def check(self):
+        return {"calls_per_step": self.calls, "us_per_call_note": "ms_per_step / 1000 calls"}
+
+    def roofline_sample(self, k):
+        torch = self.torch
+        stream = torch.cuda.current_stream()
+        n = 50 * k
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n)]
+        L, h = self.L, self.M.handle
+        for i in range(n):
+            evs[2 * i].record(stream)
+            L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE)
+            evs[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(n))
+        return ms / n, n, self.spmv_bytes(), _kernel_name(self.M)
+
+    def e2e_setup(self):
+        torch = self.torch
+        self.xh = torch.from_numpy(self.x).pin_memory()
+        self.yh = torch.empty(self.A.n, dtype=torch.float64).pin_memory()
+        self.e2e_bytes = (self.calls * self.A.ncols * 8, self.calls * self.A.n * 8)
+
+    def e2e_step(self):
+        L, h = self.L, self.M.handle
+        px, py = self.xh.data_ptr(), self.yh.data_ptr()
+        for _ in range(self.calls):
+            L.lilac_spmv(h, px, py, L.LILAC_MEM_HOST)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        A, x = self.A, self.x
+        t0 = time.perf_counter()
+        n = 0
+        while time.perf_counter() - t0 < min(budget_s, 2.0) or n == 0:
+            oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
+            n += 1
+        t = (time.perf_counter() - t0) / n
+        return self.spmv_bytes() / t / 1e9, f"{n} oracle SpMV calls on the same matrix"
+
+    def close(self):
+        self.M.close()
+
+
+class PageRank22(Workload):
+    name = "pagerank_rmat22_20it"
+    unit = "GB/s"
+    dtype = "f32"
+    iters = 20
+
+    def __init__(self, L, torch):
+        super().__init__(L, torch)
+        from paper_2001_07938_gb300 import inputs
+        self.A = inputs.workload_rmat_pagerank()
+        self.work_per_step = self.iters * self.iter_bytes() / 1e9
+
+    def iter_bytes(self):
+        """Per iteration: SpMV roofline bytes (FP32) + the dangling bitmap."""
+        A = self.A
+        return _spmv_bytes(A.n, A.ncols, A.nnz, 4) + A.n // 8
+
+    def config(self):
+        A = self.A
+        return {"workload": self.name,
+                "matrix": "R-MAT a=.57 b=c=.19, relabelled, no self-loops/duplicates, transposed",
+                "n": A.n, "nnz": A.nnz, "iterations": self.iters, "damping": 0.85,
+                "precision": "fp32 (D, L1 in fp64)", "index": "int32",
+                "l2": f"inputs larger than L2: matrix {A.nnz * 8 / 1e6:.0f} MB, no flush"}
+
+    def setup(self):
+        torch, L = self.torch, self.L
+        self.M = L.CsrMatrix.from_csr(self.A)
+        self.xd = torch.empty(self.A.n, dtype=torch.float32, device="cuda")
+        self.launches_per_step = 1 + self.iters
+
+    def step(self):
+        L = self.L
+        L.lilac_pagerank(self.M.handle, self.xd.data_ptr(), 1, self.iters, 0.85, None,
+                         L.LILAC_MEM_DEVICE)
+
+    def check(self):
+        l1 = self.M.pagerank(self.xd, iters=self.iters)
+        return {"l1_last": float(l1[-1]), "sum_x": float(self.xd.double().sum().item())}
+
+    def roofline_sample(self, k):
+        return self._profiled(k, self.iter_bytes(),
+                              " with the PageRank epilogue (teleport, L1, dangling sum)")
+
+    def e2e_setup(self):
+        self.xh = self.torch.empty(self.A.n, dtype=self.torch.float32).pin_memory()
+        self.e2e_bytes = (0, self.A.n * 4)  # starts from 1/N on the device; result copied back
+
+    def e2e_step(self):
+        L = self.L
+        L.lilac_pagerank(self.M.handle, self.xh.data_ptr(), 1, self.iters, 0.85, None,
+                         L.LILAC_MEM_HOST)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        A = self.A
+        t0 = time.perf_counter()
+        oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=1)
+        t1 = time.perf_counter() - t0
+        k = int(max(1, min(self.iters, budget_s / max(t1, 1e-9))))
+        if k > 1:
+            t0 = time.perf_counter()
+            oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=k)
+            t1 = (time.perf_counter() - t0) / k
+        return self.iter_bytes() / t1 / 1e9, f"{k} oracle PageRank iterations"
+
+    def close(self):
+        self.M.close()
+
+
+class IR192(Workload):
+    name = "cg_mixed_poisson3d_m192_to_1e-10"
+    unit = "solves/s"
+    dtype = "f32 inner / f64 refinement"
+
+    def __init__(self, L, torch):
+        super().__init__(L, torch)
+        from paper_2001_07938_gb300 import inputs
+        self.A, self.b = inputs.workload_poisson3d_ir()
+        self.fp64_iters = None
+
+    def config(self):
+        A = self.A
+        return {"workload": self.name, "matrix": "3D 7-point Poisson, 192^3 grid, FP32 values",
+                "n": A.n, "nnz": A.nnz, "rtol": 1e-10, "b": "uniform [-1,1], seed 1",
+                "index": "int32",
+                "l2": f"inputs larger than L2 ({A.nnz * 8 / 1e6:.0f} MB matrix), no flush"}
+
+    def setup(self):
+        torch, L = self.torch, self.L
+        self.M = L.CsrMatrix.from_csr(self.A)
+        self.bd = torch.from_numpy(self.b).cuda()
+        self.xd = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
+        self.opts = L.lilac_cg_opts_default()
+        self.opts.precision, self.opts.rtol, self.opts.max_iter = 1, 1e-10, 30
+        self.opts.inner_max_iter, self.opts.inner_rtol = 4000, 1e-5
+        st, info = L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(),
+                              L.LILAC_MEM_DEVICE, self.opts, want_info=True)
+        self.launches_per_step = info.kernel_launches
+
+    def step(self):
+        L = self.L
+        L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(), L.LILAC_MEM_DEVICE,
+                   self.opts, want_info=False)
+
+    def check(self):
+        L, torch = self.L, self.torch
+        st, info = L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(),
+                              L.LILAC_MEM_DEVICE, self.opts, want_info=True)
+        res = {"status": L.lilac_status_string(st), "inner_iters": info.iters,
+               "refinements": info.refinements, "true_rel_res": info.true_rel_res}
+        # plain FP64 CG on the same system: the comparator
+        M64 = L.CsrMatrix.from_csr(self.A.astype(np.float64))
+        x64 = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
+        M64.cg(self.bd, x64, max_iter=4000, rtol=1e-10)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st64, i64 = M64.cg(self.bd, x64, max_iter=4000, rtol=1e-10)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        M64.close()
+        self.fp64_iters = i64.iters
+        res["plain_fp64"] = {"solves_per_s": 1.0 / t64, "iters": i64.iters,
+                             "true_rel_res": i64.true_rel_res}
+        return res
+
+    def roofline_sample(self, k):
+        A = self.A
+        return self._profiled(k, _spmv_bytes(A.n, A.ncols, A.nnz, 4),
+                              " with the FP32 CG epilogue (q = A p, p.q fused)")
+
+    def e2e_setup(self):
+        torch = self.torch
+        self.bh = torch.from_numpy(self.b).pin_memory()
+        self.xh = torch.zeros(self.A.n, dtype=torch.float64).pin_memory()
+        self.e2e_bytes = (self.A.n * 8, self.A.n * 8)
+
+    def e2e_step(self):
+        L = self.L
+        L.lilac_cg(self.M.handle, self.bh.data_ptr(), self.xh.data_ptr(), L.LILAC_MEM_HOST,
+                   self.opts, want_info=False)
+
+    def cpu_sample(self, budget_s):
+        """Oracle FP64 CG: k iterations timed, scaled to the FP64 CG iteration
+        count to 1e-10 (a full oracle solve takes far longer than a step)."""
+        import oracle
+        A, b = self.A, self.b
+        t0 = time.perf_counter()
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=2, rtol=0.0)
+        t_it = (time.perf_counter() - t0) / 2
+        k = int(max(1, min(200, budget_s / max(t_it, 1e-9))))
+        t0 = time.perf_counter()
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=k, rtol=0.0)
+        t_it = (time.perf_counter() - t0) / k
+        n_it = self.fp64_iters or 1400
+        return 1.0 / (t_it * n_it), (f"{k} oracle FP64 CG iterations, scaled to {n_it} "
+                                     "iterations (the FP64 CG iteration count to 1e-10)")
+
+    def close(self):
+        self.M.close()
+
+
+WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192": IR192}
 
 
 # --- the two arms ---------------------------------------------------------------
@@ -230,28 +500,23 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    from paper_2001_07938_gb300 import inputs  # noqa: F401
     oracle.build()
-
-    class _NoTorch:
-        pass
-
     wl = WORKLOADS[args.workload](None, None)
     steps, warm = args.steps, args.warmup
     budget = max(0.5, 120.0 / max(1, steps + warm))
-    vals, samples = [], ""
+    vals, sample = [], ""
     for i in range(warm + steps):
-        v, samples = wl.cpu_sample(budget)
+        v, sample = wl.cpu_sample(budget)
         if i >= warm:
             vals.append(v)
     value = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": wl.unit,
             "n_gpus": args.gpus, "steps": steps, "warmup": warm,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+            "ms_per_step": 1000.0 * wl.work_per_step / value, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl.name, "n": wl.A.n, "nnz": wl.A.nnz},
             "cpu_baseline": {"value": value, "unit": wl.unit, "cores": 1, "kind": "oracle",
-                             "sample": samples},
+                             "sample": sample},
             "e2e": {"value": value, "unit": wl.unit, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -281,9 +546,17 @@ def run_lilac(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    def max_over_ranks(v):
+        if ws > 1:
+            t = torch.tensor([v], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
     wl = WORKLOADS[args.workload](L, torch)
     wl.setup()
     stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None
     for _ in range(args.warmup):
         wl.step()
     barrier()
@@ -291,42 +564,33 @@ def run_lilac(args):
     barrier()
 
     K = args.steps
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     if clocks:
         clocks.start()
         time.sleep(0.3)
     barrier()
-    evs[0].record(stream)
     for k in range(K):
+        if flush is not None:
+            flush.fill_(k & 0xFF)  # L2 flush between timed steps, outside the step's events
+        ev0[k].record(stream)
         wl.step()
-        evs[k + 1].record(stream)
+        ev1[k].record(stream)
     barrier()
     clk = clocks.stop() if clocks else None
-    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(K)]
-    total_ms = evs[0].elapsed_time(evs[K])
-    if ws > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * K / (total_ms / 1000.0)
+    step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
+    total_ms = max_over_ranks(sum(step_ms))
+    value = ws * K * wl.work_per_step / (total_ms / 1000.0)
 
-    # dominant kernel: fused SpMV, CUDA events on its own stream
-    kr = min(K, 5)
-    spmv_ms, n_spmv = wl.roofline_sample(kr)
-    minfo = wl.M.info()
-    kname = {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {minfo['vector_width']} lanes/row)",
-             3: f"spmv_staged_kernel ({minfo['vector_width']} lanes/row)",
-             4: f"spmv_merge_kernel ({minfo['vector_width']} lanes/row)",
-             5: "spmv_slab_kernel (x slabs in shared memory)"}.get(minfo["variant"], "spmv")
+    # dominant kernel: CUDA events on its own stream
+    kern_ms, n_kern, kern_bytes, kname = wl.roofline_sample(min(K, 5))
     peak, peak_kind = _peaks()
-    achieved = wl.spmv_bytes() / (spmv_ms / 1000.0) / 1e9
-    traffic = _ncu_traffic(f"spmv_cg_{args.workload}")
+    achieved = kern_bytes / (kern_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": kname + " with the CG epilogue (q = A p, p.q fused)",
-                "algorithmic_bytes_per_launch": wl.spmv_bytes(),
-                "avg_launch_ms": spmv_ms, "launches_timed": n_spmv,
+                "frac": achieved / peak, "traffic": _ncu_traffic(args.workload), "kernel": kname,
+                "algorithmic_bytes_per_launch": kern_bytes, "avg_launch_ms": kern_ms,
+                "launches_timed": n_kern,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
 
     # end to end through the C ABI with pinned host buffers
@@ -340,15 +604,10 @@ def run_lilac(args):
         wl.e2e_step()
     e1.record(stream)
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e = {"value": ws * K / (e2e_ms / 1000.0), "unit": wl.unit,
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": ws * K * wl.work_per_step / (e2e_ms / 1000.0), "unit": wl.unit,
            "h2d_bytes_per_step": wl.e2e_bytes[0], "d2h_bytes_per_step": wl.e2e_bytes[1]}
 
-    line = None
     if rank == 0:
         cpu = None
         if not args.no_cpu_baseline and ws == 1:

@@ -260,6 +260,16 @@ lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz, const 
                                 const int32_t* col_ind, const void* vals, lilac_dtype dtype,
                                 const void* x, void* y, void* stream);
 
+/*
+ * Kernel timing switch.  enable != 0 starts timing every SpMV launch that
+ * later lilac_cg / lilac_pagerank calls on this handle make (CUDA event pairs
+ * recorded on the launching stream, also inside captured graphs; the calls
+ * then synchronise their stream) and clears the totals.  enable == 0 stops
+ * and returns, in *spmv_ms and *spmv_launches (both nullable), the summed
+ * duration and number of the SpMV launches timed since it was enabled.
+ */
+lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms, int64_t* spmv_launches);
+
 /* Clear a sticky device error of the handle and re-zero its scratch memory. */
 lilac_status lilac_csr_reset_error(lilac_csr A);
 

@@ -57,24 +57,8 @@ struct Prof {
     int kernels = 0;  // all kernels launched by the solve
 };
 
-static lilac_status ensure_prof_events(lilac_csr A, int pairs) {
-    while ((int)A->prof_events.size() < 2 * pairs) {
-        cudaEvent_t e;
-        LILAC_CUDA_TRY(cudaEventCreate(&e));
-        A->prof_events.push_back(e);
-    }
-    return LILAC_OK;
-}
-
-// Add the durations of the first `pairs` event pairs (after a synchronize).
 static lilac_status collect_prof(lilac_csr A, int pairs, Prof& prof) {
-    for (int i = 0; i < pairs; ++i) {
-        float ms = 0.f;
-        LILAC_CUDA_TRY(cudaEventElapsedTime(&ms, A->prof_events[2 * i], A->prof_events[2 * i + 1]));
-        prof.ms += ms;
-        prof.launches += 1;
-    }
-    return LILAC_OK;
+    return collect_prof_events(A, pairs, &prof.ms, &prof.launches);
 }
 
 // Enqueue `nit` iterations of CG on the work set W (vectors of type T; the
@@ -327,7 +311,7 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
     CgState hs{};
     lilac_status st;
     Prof prof;
-    prof.on = o.profile != 0 && info != nullptr;
+    prof.on = (o.profile != 0 && info != nullptr) || A->profiling;
     if (o.precision == 0) {
         st = cg_f64(A, bd, xd, o, s, &hs, prof);
         if (st == LILAC_OK && (info || o.rtol > 0.0 || where == LILAC_MEM_HOST)) {
@@ -346,6 +330,10 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
         st = cg_mixed(A, bd, xd, o, s, &hs, &local, prof);
     }
     if (st != LILAC_OK) return st;
+    if (A->profiling) {
+        A->prof_ms_acc += prof.ms;
+        A->prof_launches_acc += prof.launches;
+    }
     local.spmv_ms = prof.ms;
     local.spmv_launches = prof.launches;
     local.kernel_launches = prof.kernels;

@@ -72,6 +72,25 @@ lilac_status check_device_status(lilac_csr A, cudaStream_t stream) {
     return LILAC_OK;
 }
 
+lilac_status ensure_prof_events(lilac_csr A, int pairs) {
+    while ((int)A->prof_events.size() < 2 * pairs) {
+        cudaEvent_t e;
+        LILAC_CUDA_TRY(cudaEventCreate(&e));
+        A->prof_events.push_back(e);
+    }
+    return LILAC_OK;
+}
+
+lilac_status collect_prof_events(lilac_csr A, int pairs, double* ms, int* launches) {
+    for (int i = 0; i < pairs; ++i) {
+        float t = 0.f;
+        LILAC_CUDA_TRY(cudaEventElapsedTime(&t, A->prof_events[2 * i], A->prof_events[2 * i + 1]));
+        *ms += t;
+        *launches += 1;
+    }
+    return LILAC_OK;
+}
+
 // Column range check and max(col_ind) (the ncols invariant).  out[0] = max
 // column, out[1] = 1 if some column is negative or >= ncols (ncols >= 0).
 __global__ void csr_columns_kernel(int64_t nnz, const int* __restrict__ col, int ncols, int* out) {
@@ -538,6 +557,22 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
     if (vector_width) A->vwidth = vector_width;
     if (variant == LILAC_VARIANT_SCALAR) A->vwidth = 1;
     if (variant == LILAC_VARIANT_VECTOR && A->vwidth < 2) A->vwidth = 2;
+    return LILAC_OK;
+}
+
+lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms,
+                               int64_t* spmv_launches) {
+    if (!A) {
+        set_last_error("NULL handle");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    if (spmv_ms) *spmv_ms = A->prof_ms_acc;
+    if (spmv_launches) *spmv_launches = A->prof_launches_acc;
+    if (enable) {
+        A->prof_ms_acc = 0.0;
+        A->prof_launches_acc = 0;
+    }
+    A->profiling = enable != 0;
     return LILAC_OK;
 }
 

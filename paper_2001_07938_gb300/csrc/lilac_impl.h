@@ -133,6 +133,9 @@ struct lilac_csr_s {
     cudaStream_t capture_stream = nullptr;
     std::map<lilac::GraphKey, cudaGraphExec_t> graphs;
     std::vector<cudaEvent_t> prof_events;  // pairs around timed SpMV launches
+    bool profiling = false;                // lilac_csr_profile switch
+    double prof_ms_acc = 0.0;
+    int64_t prof_launches_acc = 0;
     // host copies
     std::vector<int32_t> h_row_ptr;
     int64_t h2d_bytes = 0;
@@ -165,6 +168,10 @@ lilac_status ensure_slab(lilac_csr A, cudaStream_t stream);
 lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
 bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status check_device_status(lilac_csr A, cudaStream_t stream);
+// Event pairs for timing SpMV launches (pair i = events 2i, 2i+1).
+lilac_status ensure_prof_events(lilac_csr A, int pairs);
+// Sum the durations of the first `pairs` pairs (their work must be complete).
+lilac_status collect_prof_events(lilac_csr A, int pairs, double* ms, int* launches);
 int vec_grid(const lilac_csr_s* A, int64_t n);
 
 }  // namespace lilac

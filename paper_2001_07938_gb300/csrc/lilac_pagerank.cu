@@ -44,7 +44,10 @@ static lilac_status pagerank_impl(lilac_csr A, T* x, int init_uniform, int iters
     LILAC_TRY(prepare_spmv<Op>(A));
     uint64_t dbits;
     std::memcpy(&dbits, &damping, sizeof(dbits));
-    GraphKey key{G_PR + (init_uniform ? 1 : 0), x, nullptr, iters, dbits, A->variant, A->vwidth, A->ws_gen};
+    const bool prof = A->profiling;
+    if (prof) LILAC_TRY(ensure_prof_events(A, iters));
+    GraphKey key{G_PR + (init_uniform ? 1 : 0) + (prof ? 2 : 0), x, nullptr, iters, dbits,
+                 A->variant, A->vwidth, A->ws_gen};
     LILAC_TRY(run_maybe_graph(A, key, true, s, [&](cudaStream_t cs) -> lilac_status {
         pr_start_kernel<T><<<vec_grid(A, n), kVecThreads, 0, cs>>>(
             n, x, init_uniform, has_out, FinPrStart{st, damping, n}, A->scratch());
@@ -53,13 +56,25 @@ static lilac_status pagerank_impl(lilac_csr A, T* x, int init_uniform, int iters
         T* dst = y;
         for (int t = 0; t < iters; ++t) {
             Op op{dst, src, has_out, st, l1, T(damping), n};
+            if (prof)
+                LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * t], cs, cudaEventRecordExternal));
             LILAC_TRY(launch_spmv(A, val, src, op, cs));
+            if (prof)
+                LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * t + 1], cs, cudaEventRecordExternal));
             std::swap(src, dst);
         }
         if (src != x)
             LILAC_CUDA_TRY(cudaMemcpyAsync(x, src, sizeof(T) * (size_t)n, cudaMemcpyDeviceToDevice, cs));
         return LILAC_OK;
     }));
+    if (prof) {
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+        int launches = 0;
+        double ms = 0.0;
+        LILAC_TRY(collect_prof_events(A, iters, &ms, &launches));
+        A->prof_ms_acc += ms;
+        A->prof_launches_acc += launches;
+    }
     if (l1_host && iters > 0) {
         LILAC_CUDA_TRY(cudaMemcpyAsync(l1_host, l1, sizeof(double) * (size_t)iters,
                                        cudaMemcpyDeviceToHost, s));

@@ -41,7 +41,7 @@ EXPORTS = (
     "lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy", "lilac_csr_info",
     "lilac_csr_set_variant", "lilac_spmv", "lilac_cg_opts_default", "lilac_cg",
     "lilac_pagerank", "lilac_csr_reset_error", "lilac_status_string", "lilac_last_error",
-    "lilac_version", "lilac_spmv_noalloc",
+    "lilac_version", "lilac_spmv_noalloc", "lilac_csr_profile",
 )
 
 
@@ -112,6 +112,7 @@ def _lib():
         lib.lilac_pagerank.argtypes = [vp, vp, i32, i32, dbl, vp, c.c_int, vp]
         lib.lilac_csr_reset_error.argtypes = [vp]
         lib.lilac_spmv_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, c.c_int, vp, vp, vp]
+        lib.lilac_csr_profile.argtypes = [vp, i32, c.POINTER(dbl), c.POINTER(i64)]
         lib.lilac_status_string.argtypes = [c.c_int]
         lib.lilac_status_string.restype = c.c_char_p
         lib.lilac_last_error.argtypes = []
@@ -120,7 +121,8 @@ def _lib():
         lib.lilac_version.restype = i32
         for name in ("lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy",
                      "lilac_csr_info", "lilac_csr_set_variant", "lilac_spmv", "lilac_cg",
-                     "lilac_pagerank", "lilac_csr_reset_error", "lilac_spmv_noalloc"):
+                     "lilac_pagerank", "lilac_csr_reset_error", "lilac_spmv_noalloc",
+                     "lilac_csr_profile"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -233,6 +235,14 @@ def lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where, strea
     _check(_lib().lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where,
                                  stream if stream is not None else current_stream()),
            "lilac_pagerank")
+
+
+def lilac_csr_profile(A, enable):
+    """Start (enable=True) or stop SpMV launch timing; returns (ms, launches) so far."""
+    ms, n = ctypes.c_double(0.0), ctypes.c_int64(0)
+    _check(_lib().lilac_csr_profile(A, int(enable), ctypes.byref(ms), ctypes.byref(n)),
+           "lilac_csr_profile")
+    return ms.value, n.value
 
 
 def lilac_spmv_noalloc(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, x, y, stream=None):
