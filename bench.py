@@ -555,6 +555,10 @@ def run_lilac(args):
 
     wl = WORKLOADS[args.workload](L, torch)
     wl.setup()
+    if args.variant:
+        name, _, width = args.variant.partition(":")
+        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5}
+        wl.M.set_variant(codes[name], int(width or 0))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None
     for _ in range(args.warmup):
@@ -639,6 +643,8 @@ def main():
     ap.add_argument("--impl", choices=["lilac", "reference"], default="lilac")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cg75k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="",
+                    help="force the SpMV kernel instead of the tuner's choice, e.g. slab:4")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -109,13 +109,16 @@ lilac_status launch_merge(lilac_csr_s* A, const typename Op::ValT* val, const ty
 }
 
 template <int V, class Op>
+using SlabLayoutOf = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
+                                kSlabTileRows, kSlabWidth, kSlabBlockRows, kSlabStages>;
+
+template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
-    using L = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
-                         kSlabTileRows, kSlabWidth, kSlabBlockRows>;
+    using L = SlabLayoutOf<V, Op>;
     int& bps = bps_slot<V + 64, Op, true>(A->device);
     if (bps == 0) {
         auto kern = spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth,
-                                     kSlabBlockRows, Op>;
+                                     kSlabBlockRows, kSlabStages, Op>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)L::kSmemBytes));
         bps = occupancy_per_sm(kern, kSlabThreads, L::kSmemBytes);
@@ -126,24 +129,21 @@ lilac_status prepare_slab(lilac_csr_s* A) {
 template <int V, class Op>
 lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    using L = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
-                         kSlabTileRows, kSlabWidth, kSlabBlockRows>;
+    using L = SlabLayoutOf<V, Op>;
     // the regrouped copy holds the handle's own values; another value array
     // (e.g. an FP32 copy) or an x that bulk copies cannot read go to STAGED
     const bool own_vals = (const void*)val == A->val.p;
     if (!A->slab_built || !own_vals || (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
         return launch_staged<V, Op>(A, val, x, op, stream);
     LILAC_TRY(prepare_slab<V, Op>(A));
-    const int bps = bps_slot<V + 64, Op, true>(A->device);
-    int64_t grid = (int64_t)A->sm_count * bps;
-    if (grid > A->slab_nblocks) grid = A->slab_nblocks;
-    if (grid > kMaxCtas) grid = kMaxCtas;
-    if (grid < 1) grid = 1;
-    spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth, kSlabBlockRows, Op>
-        <<<(unsigned)grid, kSlabThreads, L::kSmemBytes, stream>>>(
+    spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth, kSlabBlockRows,
+                     kSlabStages, Op>
+        <<<(unsigned)A->slab_grid, kSlabThreads, L::kSmemBytes, stream>>>(
             A->slab_val.as<typename Op::ValT>(), A->slab_col.as<int>(), A->slab_lrp.as<int>(),
-            A->slab_tiles.as<SlabTile>(), A->slab_blocks.as<SlabBlock>(), A->slab_nblocks,
-            A->ncols, x, op, A->scratch());
+            A->slab_tiles.as<SlabTile>(), A->slab_cta_tiles.as<int2>(), A->slab_cta_slabs.as<int2>(),
+            A->slab_blocks.as<SlabBlock>(), A->slab_nblocks, A->slab_nslabs, A->rows, A->ncols,
+            A->slab_P.as<typename Op::AccT>(), A->slab_cnt.as<unsigned>(),
+            A->slab_block_red.as<double>(), x, op, A->scratch());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
 }

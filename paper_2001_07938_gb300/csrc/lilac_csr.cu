@@ -235,7 +235,8 @@ lilac::Scratch lilac_csr_s::scratch() const {
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
                                   &slab_val, &slab_col, &slab_lrp, &slab_tiles, &slab_blocks,
-                                  &slab_perm, &merge_coords, &merge_carries,
+                                  &slab_perm, &merge_coords, &merge_carries, &slab_cta_tiles,
+                                  &slab_cta_slabs, &slab_P, &slab_cnt, &slab_block_red,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
@@ -389,8 +390,8 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
     for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
     for (int w : {1, 4, 16}) cands.push_back({LILAC_VARIANT_MERGE, w});
-    // SLAB is not a candidate yet: every CTA still loads all of x slab by
-    // slab, and on the matrices it targets it measured slower than VECTOR.
+    // SLAB is selectable (lilac_csr_set_variant) but not a tuning candidate:
+    // on the matrices it targets it measured slower than VECTOR.
     // row-per-group kernels serialise a long row in one group: only for
     // rows no longer than a few tiles
     if (A->max_row_len <= 4 * kTileNnz) {
@@ -441,6 +442,8 @@ static void free_handle(lilac_csr A) {
     lilac::DevBuf* all[] = {&A->row_ptr, &A->col_ind, &A->val, &A->val32, &A->tiles, &A->longs,
                             &A->slab_val, &A->slab_col, &A->slab_lrp, &A->slab_tiles,
                             &A->slab_blocks, &A->slab_perm, &A->merge_coords, &A->merge_carries,
+                            &A->slab_cta_tiles, &A->slab_cta_slabs, &A->slab_P, &A->slab_cnt,
+                            &A->slab_block_red,
                             &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
                             &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
                             &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,

@@ -32,12 +32,13 @@ constexpr int kTileNnz = LILAC_TILE_NNZ;
 constexpr int kTileRows = LILAC_TILE_ROWS;
 constexpr int kRowsThreads = 256;
 // SLAB kernel shape: 512 threads, tiles of 2048 nonzeros touching at most
-// 512 rows, column slabs of 8192, row blocks of at most 2048 rows.
+// 256 rows, column slabs of 8192, row blocks of 512 rows, 3 pipeline stages.
 constexpr int kSlabThreads = 512;
 constexpr int kSlabTileNnz = 2048;
-constexpr int kSlabTileRows = 512;
+constexpr int kSlabTileRows = 256;
 constexpr int kSlabWidth = 8192;
-constexpr int kSlabBlockRows = 2048;
+constexpr int kSlabBlockRows = 512;
+constexpr int kSlabStages = 3;
 // MERGE kernel shape: 256 threads, sub-tiles of 2048 path items, about four
 // CTAs per SM.
 constexpr int kMergeThreads = 256;
@@ -115,7 +116,8 @@ struct lilac_csr_s {
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
     // SLAB regrouped copy (built on first use)
     lilac::DevBuf slab_val, slab_col, slab_lrp, slab_tiles, slab_blocks, slab_perm;
-    int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0;
+    lilac::DevBuf slab_cta_tiles, slab_cta_slabs, slab_P, slab_cnt, slab_block_red;
+    int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0, slab_grid = 0;
     bool slab_built = false;
     // MERGE partition (computed at create): start of each CTA's path range
     lilac::DevBuf merge_coords, merge_carries;

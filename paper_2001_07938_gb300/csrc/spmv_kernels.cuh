@@ -56,18 +56,42 @@ __global__ void __launch_bounds__(THREADS)
     const unsigned mask = group_mask<V>(threadIdx.x);
     for (int r = group; r < A.rows; r += ngroups) {
         const int kb = A.row_ptr[r], ke = A.row_ptr[r + 1];
-        // four independent gathers in flight per lane
+        // four independent gathers in flight per lane; the indices and values
+        // of the next four are loaded while those gathers are outstanding
         AccT s0 = AccT(0), s1 = AccT(0), s2 = AccT(0), s3 = AccT(0);
         int k = kb + lane;
-        for (; k + 3 * V < ke; k += 4 * V) {
-            const int c0 = ld_stream(A.col_ind + k), c1 = ld_stream(A.col_ind + k + V);
-            const int c2 = ld_stream(A.col_ind + k + 2 * V), c3 = ld_stream(A.col_ind + k + 3 * V);
+        int c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+        typename Op::ValT v0{}, v1{}, v2{}, v3{};
+        if (k + 3 * V < ke) {
+            c0 = ld_stream(A.col_ind + k);
+            c1 = ld_stream(A.col_ind + k + V);
+            c2 = ld_stream(A.col_ind + k + 2 * V);
+            c3 = ld_stream(A.col_ind + k + 3 * V);
+            v0 = ld_stream(A.val + k);
+            v1 = ld_stream(A.val + k + V);
+            v2 = ld_stream(A.val + k + 2 * V);
+            v3 = ld_stream(A.val + k + 3 * V);
+        }
+        while (k + 3 * V < ke) {
             const typename Op::VecT x0 = __ldg(x + c0), x1 = __ldg(x + c1);
             const typename Op::VecT x2 = __ldg(x + c2), x3 = __ldg(x + c3);
-            s0 += AccT(ld_stream(A.val + k)) * AccT(x0);
-            s1 += AccT(ld_stream(A.val + k + V)) * AccT(x1);
-            s2 += AccT(ld_stream(A.val + k + 2 * V)) * AccT(x2);
-            s3 += AccT(ld_stream(A.val + k + 3 * V)) * AccT(x3);
+            const typename Op::ValT w0 = v0, w1 = v1, w2 = v2, w3 = v3;
+            const int kn = k + 4 * V;
+            if (kn + 3 * V < ke) {
+                c0 = ld_stream(A.col_ind + kn);
+                c1 = ld_stream(A.col_ind + kn + V);
+                c2 = ld_stream(A.col_ind + kn + 2 * V);
+                c3 = ld_stream(A.col_ind + kn + 3 * V);
+                v0 = ld_stream(A.val + kn);
+                v1 = ld_stream(A.val + kn + V);
+                v2 = ld_stream(A.val + kn + 2 * V);
+                v3 = ld_stream(A.val + kn + 3 * V);
+            }
+            s0 += AccT(w0) * AccT(x0);
+            s1 += AccT(w1) * AccT(x1);
+            s2 += AccT(w2) * AccT(x2);
+            s3 += AccT(w3) * AccT(x3);
+            k = kn;
         }
         for (; k < ke; k += V) s0 += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
         AccT sum = (s0 + s1) + (s2 + s3);
@@ -266,8 +290,8 @@ __global__ void __launch_bounds__(THREADS)
                 }
             }
         }
-        // shared-memory writes of this tile are ordered before the bulk copy
-        // that will overwrite the stage
+        // this thread's shared-memory writes (in-place products) are ordered
+        // before the bulk copy that will overwrite the stage
         fence_proxy_async_smem();
         __syncthreads();  // stage st is free for the copy issued in iteration i + 1
     }
@@ -292,97 +316,100 @@ namespace lilac {
 // SLAB kernel: x read from shared memory instead of L2.
 //
 // The matrix is regrouped once (lilac_slab.cu) into row blocks x column
-// slabs: within a row block, all nonzeros whose column lies in slab s
-// (columns [s*W, (s+1)*W)) are stored together, row by row, with local
-// column indices col - s*W and a per-(block, slab) row-pointer array.  A CTA
-// takes a row block, keeps slab s of x in shared memory (two slab buffers,
-// the next one loaded by a bulk copy while the current one is used), streams
-// the block's nonzeros slab by slab in tiles (double-buffered bulk copies as
-// in the STAGED kernel), gathers x from shared memory, and adds each row's
-// partial sums into a per-row accumulator in shared memory.  When the block
-// is done, the epilogue runs once per row.  Gathers never leave the SM, so
-// the kernel streams the matrix at HBM speed when rows have many nonzeros
-// per column slab.
+// slabs: the nonzeros of row block b whose columns lie in slab s (columns
+// [s*W, (s+1)*W)) form unit (b, s), stored contiguously, row by row, with
+// local column indices col - s*W and a row-pointer array per unit.  Units are
+// ordered slab by slab and dealt to CTAs in nnz-balanced contiguous runs, so a
+// CTA touches at most two slabs: it loads those slabs of x into shared memory
+// once (bulk copies), then streams its units' nonzeros in tiles through an
+// NST-stage bulk-copy pipeline, gathering x from shared memory and adding each
+// row's pieces into a per-row accumulator in shared memory.  At the end of a
+// unit the accumulators go to the partial array P[s][row]; the CTA that
+// completes the last unit of a row block (arrival counter) adds P over the
+// slabs in slab order and runs the epilogue for the block's rows.  Gathers
+// never leave the SM; the extra traffic is P (written and read once).
 struct SlabTile {
-    int k0, k1;      // nonzeros [k0, k1) of the regrouped arrays
-    int lrp_idx;     // index in the row-pointer array of the tile's first row
-    int rl0;         // block-local index of that row
-    int nrows;       // rows [rl0, rl0 + nrows) overlap the tile
-    int slab;        // column slab
-    int next_slab;   // if this is the first tile of its slab: the slab after it (-1: none)
-    int first;       // 1: first tile of its slab within the block
+    int k0, k1;    // nonzeros [k0, k1) of the regrouped arrays
+    int lrp_idx;   // index in the row-pointer array of the tile's first row
+    int rl0;       // block-local index of that row
+    int nrows;     // rows [rl0, rl0 + nrows) overlap the tile
+    int slab;      // column slab
+    int block;     // row block
+    int last;      // 1: last tile of its unit
 };
 
 struct SlabBlock {
-    int r0, nrows, tile_begin, tile_end;
+    int r0, nrows;  // rows [r0, r0 + nrows)
+    int need;       // number of non-empty units of the block
+    int pad;
 };
 
-template <class ValT, class VecT, class AccT, int TN, int TRS, int W, int RB>
+template <class ValT, class VecT, class AccT, int TN, int TRS, int W, int RB, int NST>
 struct SlabLayout {
     static constexpr size_t kXBytes = sizeof(VecT) * W;
-    static constexpr size_t kYBytes = sizeof(AccT) * RB;
+    static constexpr size_t kYBytes = (sizeof(AccT) * RB + 15) / 16 * 16;
     static constexpr int kValElems = TN + 8;
     static constexpr int kRpElems = TRS + 8;
     static constexpr size_t kValBytes = sizeof(ValT) * kValElems;
     static constexpr size_t kColBytes = sizeof(int) * kValElems;
     static constexpr size_t kRpBytes = sizeof(int) * kRpElems;
     static constexpr size_t kStageBytes = kValBytes + kColBytes + kRpBytes;
-    static constexpr size_t kProdBytes = sizeof(AccT) == sizeof(ValT) ? 0 : sizeof(AccT) * kValElems;
+    static constexpr size_t kProdBytes = sizeof(AccT) * kValElems;  // products: own buffer
     static constexpr size_t kStageOff = 2 * kXBytes + kYBytes;
-    static constexpr size_t kSmemBytes = kStageOff + 2 * kStageBytes + kProdBytes;
+    static constexpr size_t kSmemBytes = kStageOff + NST * kStageBytes + kProdBytes;
 };
 
-template <int V, int THREADS, int TN, int TRS, int W, int RB, class Op>
+template <int V, int THREADS, int TN, int TRS, int W, int RB, int NST, class Op>
 __global__ void __launch_bounds__(THREADS, 1)
     spmv_slab_kernel(const typename Op::ValT* __restrict__ sval, const int* __restrict__ scol,
                      const int* __restrict__ lrp, const SlabTile* __restrict__ tiles,
-                     const SlabBlock* __restrict__ blocks, int nblocks, int ncols,
-                     const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
+                     const int2* __restrict__ cta_tiles, const int2* __restrict__ cta_slabs,
+                     const SlabBlock* __restrict__ blocks, int nblocks, int nslabs, int rows,
+                     int ncols, typename Op::AccT* __restrict__ P, unsigned* __restrict__ cnt,
+                     double* __restrict__ block_red, const typename Op::VecT* __restrict__ x,
+                     Op op, Scratch s) {
     if (op.skip()) return;
     using ValT = typename Op::ValT;
     using VecT = typename Op::VecT;
     using AccT = typename Op::AccT;
-    using L = SlabLayout<ValT, VecT, AccT, TN, TRS, W, RB>;
+    using L = SlabLayout<ValT, VecT, AccT, TN, TRS, W, RB, NST>;
     constexpr int NR = Op::NR;
     constexpr int NGROUPS = THREADS / V;
     constexpr int IPT = TN / THREADS;
     static_assert(TN % THREADS == 0, "tile nonzeros must be a multiple of the block size");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[2];   // matrix stages
-    __shared__ __align__(8) uint64_t xbar[2];  // x slab buffers
-    __shared__ SlabTile sdesc[2];
+    __shared__ __align__(8) uint64_t bar[NST];
+    __shared__ __align__(8) uint64_t xbar[2];
+    __shared__ SlabTile sdesc[NST];
+    __shared__ double sh_red[kMaxRed * 32];
+    __shared__ int s_last;
 
     VecT* xs[2] = {reinterpret_cast<VecT*>(smem), reinterpret_cast<VecT*>(smem + L::kXBytes)};
     AccT* yacc = reinterpret_cast<AccT*>(smem + 2 * L::kXBytes);
     auto stage_ptr = [&](int st) { return smem + L::kStageOff + st * L::kStageBytes; };
-    AccT* prod_extra = reinterpret_cast<AccT*>(smem + L::kStageOff + 2 * L::kStageBytes);
+    AccT* prod_extra = reinterpret_cast<AccT*>(smem + L::kStageOff + NST * L::kStageBytes);
 
-    double red[NR > 0 ? NR : 1] = {};
     const int tid = threadIdx.x;
     const int lane = tid & (V - 1);
     const int group = tid / V;
     const unsigned mask = group_mask<V>(tid);
+    const int2 ct = cta_tiles[blockIdx.x];   // tiles [ct.x, ct.y)
+    const int2 cs2 = cta_slabs[blockIdx.x];  // slabs held in buffers 0 and 1 (-1: none)
 
     uint64_t policy = 0;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < NST; ++q) mbar_init(&bar[q], 1);
         mbar_init(&xbar[0], 1);
         mbar_init(&xbar[1], 1);
         fence_mbar_init();
         policy = l2_policy_evict_first();
     }
+    for (int r = tid; r < RB; r += THREADS) yacc[r] = AccT(0);
     __syncthreads();
 
-    // per-buffer completed-load counts (the same in every thread)
-    uint32_t xloads[2] = {0u, 0u};
-    uint32_t sloads[2] = {0u, 0u};
-    int xslab[2] = {-1, -1};
-    bool failed = false;
-
-    // Thread 0: load x slab `sl` into buffer b (16-byte-aligned bulk part by
-    // the copy engine, the last < 16 bytes by plain loads).
+    // Thread 0: x slab `sl` into buffer b (16-byte-aligned bulk part by the
+    // copy engine, the last < 16 bytes by plain loads before the arrive).
     auto issue_x = [&](int sl, int b) {
         const int c0 = sl * W;
         const int ne = min(W, ncols - c0);
@@ -392,7 +419,6 @@ __global__ void __launch_bounds__(THREADS, 1)
         mbar_arrive_expect_tx(&xbar[b], bulk);
         if (bulk) bulk_g2s(xs[b], x + c0, bulk, &xbar[b], l2_policy_evict_normal());
     };
-
     auto issue_tile = [&](int ti, int st) {
         const SlabTile t = tiles[ti];
         sdesc[st] = t;
@@ -411,89 +437,150 @@ __global__ void __launch_bounds__(THREADS, 1)
         bulk_g2s(base + L::kValBytes + L::kColBytes, lrp + ra, nr * 4u, &bar[st], policy);
     };
 
-    for (int blk = blockIdx.x; blk < nblocks && !failed; blk += gridDim.x) {
-        const SlabBlock B = blocks[blk];
-        for (int r = tid; r < B.nrows; r += THREADS) yacc[r] = AccT(0);
-        const int tb = B.tile_begin, te = B.tile_end;
-        if (tb < te) {
-            const SlabTile t0 = tiles[tb];
-            xslab[0] = t0.slab;
-            xslab[1] = t0.next_slab;
-            if (tid == 0) {
-                fence_proxy_async_smem();
-                issue_x(t0.slab, 0);
-                if (t0.next_slab >= 0) issue_x(t0.next_slab, 1);
-                issue_tile(tb, 0);
-            }
-            ++xloads[0];
-            if (t0.next_slab >= 0) ++xloads[1];
-        }
-        for (int i = tb; i < te; ++i) {
-            const int st = (i - tb) & 1;
-            if (i + 1 < te && tid == 0) {
-                fence_proxy_async_smem();
-                issue_tile(i + 1, st ^ 1);
-            }
-            ++sloads[st];
-            bool ok = mbar_wait_bounded(&bar[st], (sloads[st] - 1u) & 1u);
-            const SlabTile t = sdesc[st];
-            // x buffer of this tile; on the first tile of a slab (not the
-            // block's first), the other buffer held the previous slab, whose
-            // tiles are all done: load the slab after this one into it
-            const int xb = xslab[0] == t.slab ? 0 : 1;
-            if (t.first && i > tb && t.next_slab >= 0) {
-                if (tid == 0) issue_x(t.next_slab, xb ^ 1);
-                xslab[xb ^ 1] = t.next_slab;
-                ++xloads[xb ^ 1];
-            }
-            ok = ok && mbar_wait_bounded(&xbar[xb], (xloads[xb] - 1u) & 1u);
-            if (!__syncthreads_and(ok ? 1 : 0)) {
-                failed = true;
-                break;
-            }
-            unsigned char* base = stage_ptr(st);
-            const ValT* vs = reinterpret_cast<const ValT*>(base);
-            const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
-            const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
-            AccT* prod = L::kProdBytes ? prod_extra : reinterpret_cast<AccT*>(base);
-            const VecT* xv = xs[xb];
-            const int ka = t.k0 & ~3;
-            const int kb0 = t.k0 - ka, ke0 = t.k1 - ka;
-            // Phase A: products, x from shared memory
+    const int ntile = ct.y - ct.x;
+    if (tid == 0) {
+        if (cs2.x >= 0) issue_x(cs2.x, 0);
+        if (cs2.y >= 0) issue_x(cs2.y, 1);
+        for (int q = 0; q < NST - 1 && q < ntile; ++q) issue_tile(ct.x + q, q);
+    }
+    bool failed = false;
+    bool xready[2] = {false, false};
+    uint32_t uses[NST];
 #pragma unroll
-            for (int j = 0; j < IPT; ++j) {
-                const int k = kb0 + j * THREADS + tid;
-                if (k < ke0) prod[k] = AccT(vs[k]) * AccT(xv[cs[k]]);
-            }
-            __syncthreads();
-            // Phase B: each row's part of the tile, added to its accumulator
-            const int ra = t.lrp_idx & ~3;
-            for (int rr = group; rr < t.nrows; rr += NGROUPS) {
-                const int a = max(rps[t.lrp_idx - ra + rr], t.k0) - ka;
-                const int b = min(rps[t.lrp_idx - ra + rr + 1], t.k1) - ka;
-                AccT sum = AccT(0);
-                for (int k = a + lane; k < b; k += V) sum += prod[k];
-                if constexpr (V > 1) sum = group_sum<V>(sum, mask);
-                if (lane == 0 && b > a) yacc[t.rl0 + rr] += sum;
-            }
+    for (int q = 0; q < NST; ++q) uses[q] = 0u;
+    for (int i = 0; i < ntile; ++i) {
+        const int st = i % NST;
+        if (tid == 0 && i + NST - 1 < ntile) {
             fence_proxy_async_smem();
-            __syncthreads();
+            issue_tile(ct.x + i + NST - 1, (i + NST - 1) % NST);
         }
-        if (failed) break;
-        // epilogue: one call per row of the block
+        ++uses[st];
+        bool ok = mbar_wait_bounded(&bar[st], (uses[st] - 1u) & 1u);
+        const SlabTile t = sdesc[st];
+        const int xb = t.slab == cs2.x ? 0 : 1;
+        if (!xready[xb]) {
+            ok = ok && mbar_wait_bounded(&xbar[xb], 0u);
+            xready[xb] = true;
+        }
+        if (!__syncthreads_and(ok ? 1 : 0)) {
+            failed = true;
+            break;
+        }
+        unsigned char* base = stage_ptr(st);
+        const ValT* vs = reinterpret_cast<const ValT*>(base);
+        const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
+        const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
+        AccT* prod = prod_extra;
+        const VecT* xv = xs[xb];
+        const int ka = t.k0 & ~3;
+        const int kb0 = t.k0 - ka, ke0 = t.k1 - ka;
+        // Phase A: products, x from shared memory
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int k = kb0 + j * THREADS + tid;
+            if (k < ke0) prod[k] = AccT(vs[k]) * AccT(xv[cs[k]]);
+        }
         __syncthreads();
-        for (int r = tid; r < B.nrows; r += THREADS) op.row(B.r0 + r, yacc[r], red);
+        // Phase B: each row's part of the tile, into its accumulator
+        const int ra = t.lrp_idx & ~3;
+        for (int rr = group; rr < t.nrows; rr += NGROUPS) {
+            const int a = max(rps[t.lrp_idx - ra + rr], t.k0) - ka;
+            const int b = min(rps[t.lrp_idx - ra + rr + 1], t.k1) - ka;
+            AccT sum = AccT(0);
+            for (int k = a + lane; k < b; k += V) sum += prod[k];
+            if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+            if (lane == 0 && b > a) yacc[t.rl0 + rr] += sum;
+        }
         __syncthreads();
+        if (t.last) {
+            // end of unit (t.block, t.slab): accumulators -> P, then arrival
+            const SlabBlock B = blocks[t.block];
+            AccT* Pp = P + (size_t)t.slab * rows + B.r0;
+            for (int r = tid; r < B.nrows; r += THREADS) {
+                Pp[r] = yacc[r];
+                yacc[r] = AccT(0);
+            }
+            __syncthreads();
+            if (tid == 0) {
+                __threadfence();  // cumulative: publishes the block's P writes
+                const unsigned c = atomicAdd(&cnt[t.block], 1u);
+                s_last = (c == (unsigned)B.need - 1u) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                // this CTA finished the block: sum the slabs in order, epilogue
+                __threadfence();
+                double red[NR > 0 ? NR : 1] = {};
+                for (int r = tid; r < B.nrows; r += THREADS) {
+                    AccT v = AccT(0);
+                    for (int sl = 0; sl < nslabs; ++sl) v += __ldcg(&P[(size_t)sl * rows + B.r0 + r]);
+                    op.row(B.r0 + r, v, red);
+                }
+                if constexpr (NR > 0) {
+                    double tot[NR];
+                    double r2[NR];
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) r2[q] = red[q];
+                    block_sum<NR, THREADS>(r2, tot, sh_red);
+                    if (tid == 0) {
+#pragma unroll
+                        for (int q = 0; q < NR; ++q) block_red[t.block * kMaxRed + q] = tot[q];
+                    }
+                }
+                if (tid == 0) cnt[t.block] = 0u;
+                __syncthreads();
+            }
+        }
     }
     if (failed) {
         if (tid == 0) atomicExch(s.status, DEV_TIMEOUT);
         return;
     }
-    if constexpr (NR > 0) {
-        double r2[NR];
+    // blocks without any nonzero: their rows are 0 (done by CTA 0's range)
+    if (blockIdx.x == 0) {
+        double red[NR > 0 ? NR : 1] = {};
+        for (int b = 0; b < nblocks; ++b) {
+            const SlabBlock B = blocks[b];
+            if (B.need != 0) continue;
+            for (int r = tid; r < B.nrows; r += THREADS) op.row(B.r0 + r, AccT(0), red);
+            if constexpr (NR > 0) {
+                double tot[NR];
+                double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
-        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+                for (int q = 0; q < NR; ++q) r2[q] = red[q];
+                block_sum<NR, THREADS>(r2, tot, sh_red);
+                if (tid == 0) {
+#pragma unroll
+                    for (int q = 0; q < NR; ++q) block_red[b * kMaxRed + q] = tot[q];
+                }
+#pragma unroll
+                for (int q = 0; q < NR; ++q) red[q] = 0.0;
+            }
+        }
+    }
+    if constexpr (NR > 0) {
+        // grid sum over the per-block sums, in block order
+        if (tid == 0) {
+            __threadfence();
+            const unsigned t = atomicAdd(s.ticket, 1u);
+            s_last = (t == gridDim.x - 1) ? 1 : 0;
+        }
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        double acc[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] = 0.0;
+        for (int b = tid; b < nblocks; b += THREADS) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&block_red[b * kMaxRed + q]);
+        }
+        double tot[NR];
+        block_sum<NR, THREADS>(acc, tot, sh_red);
+        if (tid == 0) {
+            op.finish(tot);
+            *s.ticket = 0u;
+        }
     }
 }
 
