@@ -270,6 +270,37 @@ lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz, const 
  */
 lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms, int64_t* spmv_launches);
 
+/*
+ * Batched execution: many FP64 problems of uneven size in one persistent
+ * launch per phase (north of the paper, which issues one library call per
+ * detected loop; batching many small problems addresses the paper's finding
+ * that small sizes are not profitable alone, Section 6.2).  The work list
+ * holds (problem, tile) items built from each handle's tile schedule; every
+ * reduction of a problem is kept per item and added in item order, so a
+ * problem's result is bitwise the same alone and in any batch.
+ */
+typedef struct lilac_batch_s* lilac_batch;
+
+/* Create a batch context on the current device (work lists, workspace arena,
+ * captured rounds).  Not thread-safe; one context per host thread. */
+lilac_status lilac_batch_create(lilac_batch* out);
+lilac_status lilac_batch_destroy(lilac_batch B); /* NULL is a no-op */
+
+/* y[i] = A[i] x[i] for i < count: FP64 handles, device vectors (y[i] of
+ * A[i]'s rows, x[i] of its columns); A[i] may repeat.  Asynchronous on
+ * `stream` after a short synchronous set-up of the work lists. */
+lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
+                              const double* const* x, double* const* y, void* stream);
+
+/* FP64 CG on count systems A[i] x[i] = b[i] at once (x0 = 0), each stopping
+ * at ||r|| <= rtol ||b|| (rtol <= 0: exactly max_iter iterations); iterations
+ * of all systems run together in captured rounds of 16, with one host check
+ * per round.  infos (nullable) receives per-system iterations, status and
+ * recursive relative residual.  Returns OK or the first non-OK status. */
+lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
+                            const double* const* b, double* const* x, int32_t max_iter,
+                            double rtol, lilac_cg_info* infos, void* stream);
+
 /* Clear a sticky device error of the handle and re-zero its scratch memory. */
 lilac_status lilac_csr_reset_error(lilac_csr A);
 

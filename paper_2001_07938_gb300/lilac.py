@@ -41,7 +41,8 @@ EXPORTS = (
     "lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy", "lilac_csr_info",
     "lilac_csr_set_variant", "lilac_spmv", "lilac_cg_opts_default", "lilac_cg",
     "lilac_pagerank", "lilac_csr_reset_error", "lilac_status_string", "lilac_last_error",
-    "lilac_version", "lilac_spmv_noalloc", "lilac_csr_profile",
+    "lilac_version", "lilac_spmv_noalloc", "lilac_csr_profile", "lilac_batch_create",
+    "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg",
 )
 
 
@@ -113,6 +114,11 @@ def _lib():
         lib.lilac_csr_reset_error.argtypes = [vp]
         lib.lilac_spmv_noalloc.argtypes = [i32, i32, i64, vp, vp, vp, c.c_int, vp, vp, vp]
         lib.lilac_csr_profile.argtypes = [vp, i32, c.POINTER(dbl), c.POINTER(i64)]
+        lib.lilac_batch_create.argtypes = [c.POINTER(vp)]
+        lib.lilac_batch_destroy.argtypes = [vp]
+        lib.lilac_batch_spmv.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), vp]
+        lib.lilac_batch_cg.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), i32,
+                                       dbl, c.POINTER(lilac_cg_info), vp]
         lib.lilac_status_string.argtypes = [c.c_int]
         lib.lilac_status_string.restype = c.c_char_p
         lib.lilac_last_error.argtypes = []
@@ -122,7 +128,8 @@ def _lib():
         for name in ("lilac_csr_create", "lilac_csr_update_values", "lilac_csr_destroy",
                      "lilac_csr_info", "lilac_csr_set_variant", "lilac_spmv", "lilac_cg",
                      "lilac_pagerank", "lilac_csr_reset_error", "lilac_spmv_noalloc",
-                     "lilac_csr_profile"):
+                     "lilac_csr_profile", "lilac_batch_create", "lilac_batch_destroy",
+                     "lilac_batch_spmv", "lilac_batch_cg"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -235,6 +242,49 @@ def lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where, strea
     _check(_lib().lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where,
                                  stream if stream is not None else current_stream()),
            "lilac_pagerank")
+
+
+class Batch:
+    """Owns a lilac_batch context (batched SpMV / CG over FP64 handles)."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(_lib().lilac_batch_create(ctypes.byref(h)), "lilac_batch_create")
+        self.handle = h
+
+    @staticmethod
+    def _ptrs(seq):
+        arr = (ctypes.c_void_p * max(1, len(seq)))()
+        for i, a in enumerate(seq):
+            arr[i] = a if isinstance(a, int) else _ptr_where(a)[0]
+        return arr
+
+    def spmv(self, mats, xs, ys, stream=None):
+        n = len(mats)
+        hs = self._ptrs([m.handle.value for m in mats])
+        _check(_lib().lilac_batch_spmv(self.handle, n, hs, self._ptrs(xs), self._ptrs(ys),
+                                       stream if stream is not None else current_stream()),
+               "lilac_batch_spmv")
+
+    def cg(self, mats, bs, xs, max_iter=1000, rtol=1e-10, stream=None):
+        n = len(mats)
+        infos = (lilac_cg_info * max(1, n))()
+        st = _lib().lilac_batch_cg(self.handle, n, self._ptrs([m.handle.value for m in mats]),
+                                   self._ptrs(bs), self._ptrs(xs), max_iter, rtol, infos,
+                                   stream if stream is not None else current_stream())
+        _check(st, "lilac_batch_cg", (LILAC_OK, LILAC_ERR_NOT_CONVERGED, LILAC_ERR_BREAKDOWN))
+        return st, [infos[i] for i in range(n)]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().lilac_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lilac_csr_profile(A, enable):
