@@ -301,6 +301,79 @@ lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
                             const double* const* b, double* const* x, int32_t max_iter,
                             double rtol, lilac_cg_info* infos, void* stream);
 
+/*
+ * Request server: continuous batching of SpMV and FP64 CG requests over a
+ * pool of matrices kept resident on the device under a memory budget -- the
+ * paper's marshaling (upload once, keep resident, free when needed; Section
+ * 3.3, Section 4.2) applied to a stream of requests.  Single-threaded: the
+ * caller submits requests as they arrive and calls lilac_server_step in its
+ * loop.  Each step admits queued requests in arrival order while the budget
+ * and the active limit allow (uploading a matrix on first use and evicting
+ * the least recently used idle matrix when memory is needed), runs every
+ * admitted SpMV request in one batched launch, advances every active CG solve
+ * by iters_per_round iterations in one captured graph, and retires finished
+ * requests (result copied to the caller's host buffer).  A request's result
+ * is bitwise the same whatever else is in flight.
+ */
+typedef struct lilac_server_s* lilac_server;
+
+typedef struct {
+    int64_t hbm_budget_bytes; /* resident matrices + request workspaces (default 120 GiB) */
+    int32_t max_active;       /* requests in flight at most (default 256) */
+    int32_t iters_per_round;  /* CG iterations per step (default 16) */
+    int32_t pad;
+} lilac_server_opts;
+
+typedef enum { LILAC_REQ_SPMV = 0, LILAC_REQ_CG = 1 } lilac_req_kind;
+
+typedef struct {
+    int32_t kind;      /* lilac_req_kind */
+    int32_t matrix;    /* id from lilac_server_add_matrix */
+    int32_t nvec;      /* SpMV: number of vectors (>= 1) */
+    int32_t max_iter;  /* CG: iteration cap (>= 1) */
+    double rtol;       /* CG: stop at ||r|| <= rtol ||b|| (<= 0: run max_iter) */
+    const double* in;  /* host: SpMV x, nvec x ncols (vector-major); CG b, rows */
+    double* out;       /* host: SpMV y, nvec x rows; CG x, rows; written before completion */
+    int64_t tag;       /* caller's id, returned in the completion */
+} lilac_request;
+
+typedef struct {
+    int64_t tag;
+    int32_t status;    /* lilac_status of the request */
+    int32_t iters;     /* CG iterations */
+    double rel_res;    /* CG recursive ||r|| / ||b|| */
+    double arrival;    /* lilac_server_now() at submit */
+    double finish;     /* lilac_server_now() at retirement */
+} lilac_completion;
+
+typedef struct {
+    int64_t submitted, completed, rounds, uploads, upload_bytes, evictions, budget_waits;
+    int64_t resident_bytes, pool_bytes;
+    int32_t queued, active;
+} lilac_server_stats_t;
+
+void lilac_server_opts_default(lilac_server_opts* o);
+/* Create on the current device; `stream` carries all of the server's work. */
+lilac_status lilac_server_create(const lilac_server_opts* o, void* stream, lilac_server* out);
+/* Free everything (in-flight requests are dropped).  NULL is a no-op. */
+lilac_status lilac_server_destroy(lilac_server S);
+/* Register an FP64 CSR matrix by its host arrays, which must stay valid and
+ * unchanged until the server is destroyed (they are uploaded on demand). */
+lilac_status lilac_server_add_matrix(lilac_server S, int32_t rows, int32_t ncols, int64_t nnz,
+                                     const int32_t* row_ptr, const int32_t* col_ind,
+                                     const double* vals, int32_t* id);
+/* Queue a request (host only; `in` and `out` must stay valid until its
+ * completion is polled).  Errors: INVALID_ARG, BUDGET (matrix alone exceeds it). */
+lilac_status lilac_server_submit(lilac_server S, const lilac_request* r);
+/* One round (admission, batched launches, retirement); synchronizes the
+ * server's stream.  *pending (nullable) = requests queued or active after it. */
+lilac_status lilac_server_step(lilac_server S, int32_t* pending);
+/* Take up to max completions (oldest first); *n receives how many. */
+lilac_status lilac_server_poll(lilac_server S, lilac_completion* out, int32_t max, int32_t* n);
+lilac_status lilac_server_stats(lilac_server S, lilac_server_stats_t* st);
+/* The server's clock (seconds, monotonic). */
+double lilac_server_now(void);
+
 /* Clear a sticky device error of the handle and re-zero its scratch memory. */
 lilac_status lilac_csr_reset_error(lilac_csr A);
 

@@ -70,7 +70,7 @@ __device__ __forceinline__ double batch_sum_parts(const double* part, int n, con
 }
 
 // SpMV phase: y = A x (BK_SPMV) or q = A p with p.q -> alpha (BK_CG).
-__global__ void __launch_bounds__(kBatchThreads)
+static __global__ void __launch_bounds__(kBatchThreads)
     batch_spmv_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
                       const int* __restrict__ nitems_dev) {
     constexpr int THREADS = kBatchThreads;
@@ -184,7 +184,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 //   PHASE 1: update  x += alpha p, r -= alpha q, rr' = r.r -> beta, convergence
 //   PHASE 2: direction p = r + beta p
 template <int PHASE>
-__global__ void __launch_bounds__(kBatchThreads)
+static __global__ void __launch_bounds__(kBatchThreads)
     batch_vec_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
                      const int* __restrict__ nitems_dev) {
     constexpr int THREADS = kBatchThreads;

@@ -42,8 +42,13 @@ EXPORTS = (
     "lilac_csr_set_variant", "lilac_spmv", "lilac_cg_opts_default", "lilac_cg",
     "lilac_pagerank", "lilac_csr_reset_error", "lilac_status_string", "lilac_last_error",
     "lilac_version", "lilac_spmv_noalloc", "lilac_csr_profile", "lilac_batch_create",
-    "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg",
+    "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_opts_default",
+    "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
+    "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
+    "lilac_server_now",
 )
+
+LILAC_REQ_SPMV, LILAC_REQ_CG = 0, 1
 
 
 class lilac_csr_info_t(ctypes.Structure):
@@ -70,6 +75,30 @@ class lilac_cg_info(ctypes.Structure):
                 ("rel_res", ctypes.c_double), ("true_rel_res", ctypes.c_double),
                 ("spmv_ms", ctypes.c_double), ("spmv_launches", ctypes.c_int32),
                 ("kernel_launches", ctypes.c_int32)]
+
+
+class lilac_server_opts(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("iters_per_round", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
+class lilac_request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("matrix", ctypes.c_int32), ("nvec", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("tag", ctypes.c_int64)]
+
+
+class lilac_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int64), ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("rel_res", ctypes.c_double), ("arrival", ctypes.c_double),
+                ("finish", ctypes.c_double)]
+
+
+class lilac_server_stats_t(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("submitted", "completed", "rounds", "uploads",
+                                              "upload_bytes", "evictions", "budget_waits",
+                                              "resident_bytes", "pool_bytes")] + \
+               [("queued", ctypes.c_int32), ("active", ctypes.c_int32)]
 
 
 class LilacError(RuntimeError):
@@ -119,6 +148,17 @@ def _lib():
         lib.lilac_batch_spmv.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), vp]
         lib.lilac_batch_cg.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), i32,
                                        dbl, c.POINTER(lilac_cg_info), vp]
+        lib.lilac_server_opts_default.argtypes = [c.POINTER(lilac_server_opts)]
+        lib.lilac_server_opts_default.restype = None
+        lib.lilac_server_create.argtypes = [c.POINTER(lilac_server_opts), vp, c.POINTER(vp)]
+        lib.lilac_server_destroy.argtypes = [vp]
+        lib.lilac_server_add_matrix.argtypes = [vp, i32, i32, i64, vp, vp, vp, c.POINTER(i32)]
+        lib.lilac_server_submit.argtypes = [vp, c.POINTER(lilac_request)]
+        lib.lilac_server_step.argtypes = [vp, c.POINTER(i32)]
+        lib.lilac_server_poll.argtypes = [vp, c.POINTER(lilac_completion), i32, c.POINTER(i32)]
+        lib.lilac_server_stats.argtypes = [vp, c.POINTER(lilac_server_stats_t)]
+        lib.lilac_server_now.argtypes = []
+        lib.lilac_server_now.restype = dbl
         lib.lilac_status_string.argtypes = [c.c_int]
         lib.lilac_status_string.restype = c.c_char_p
         lib.lilac_last_error.argtypes = []
@@ -129,7 +169,9 @@ def _lib():
                      "lilac_csr_info", "lilac_csr_set_variant", "lilac_spmv", "lilac_cg",
                      "lilac_pagerank", "lilac_csr_reset_error", "lilac_spmv_noalloc",
                      "lilac_csr_profile", "lilac_batch_create", "lilac_batch_destroy",
-                     "lilac_batch_spmv", "lilac_batch_cg"):
+                     "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_create",
+                     "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
+                     "lilac_server_step", "lilac_server_poll", "lilac_server_stats"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -278,6 +320,79 @@ class Batch:
     def close(self):
         if getattr(self, "handle", None):
             _lib().lilac_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owns a lilac_server (continuous batching of SpMV / CG requests)."""
+
+    def __init__(self, hbm_budget_bytes=None, max_active=None, iters_per_round=None, stream=None):
+        o = lilac_server_opts()
+        _lib().lilac_server_opts_default(ctypes.byref(o))
+        if hbm_budget_bytes is not None:
+            o.hbm_budget_bytes = int(hbm_budget_bytes)
+        if max_active is not None:
+            o.max_active = int(max_active)
+        if iters_per_round is not None:
+            o.iters_per_round = int(iters_per_round)
+        h = ctypes.c_void_p()
+        _check(_lib().lilac_server_create(ctypes.byref(o), stream if stream is not None
+                                          else current_stream(), ctypes.byref(h)),
+               "lilac_server_create")
+        self.handle = h
+        self._keep = {}  # host arrays the server reads later
+
+    def add_matrix(self, A):
+        rp = np.ascontiguousarray(A.row_ptr, np.int32)
+        ci = np.ascontiguousarray(A.col_ind, np.int32)
+        v = np.ascontiguousarray(A.vals, np.float64)
+        mid = ctypes.c_int32()
+        _check(_lib().lilac_server_add_matrix(self.handle, A.n, A.ncols, A.nnz, rp.ctypes.data,
+                                              ci.ctypes.data, v.ctypes.data, ctypes.byref(mid)),
+               "lilac_server_add_matrix")
+        self._keep[("m", mid.value)] = (rp, ci, v)
+        return mid.value
+
+    def submit(self, kind, matrix, inp, out, tag, nvec=1, max_iter=1000, rtol=1e-10):
+        r = lilac_request(kind, matrix, nvec, max_iter, rtol, inp.ctypes.data, out.ctypes.data, tag)
+        _check(_lib().lilac_server_submit(self.handle, ctypes.byref(r)), "lilac_server_submit")
+        self._keep[("r", tag)] = (inp, out)
+
+    def step(self):
+        n = ctypes.c_int32()
+        _check(_lib().lilac_server_step(self.handle, ctypes.byref(n)), "lilac_server_step")
+        return n.value
+
+    def poll(self, max_n=4096):
+        buf = (lilac_completion * max_n)()
+        n = ctypes.c_int32()
+        _check(_lib().lilac_server_poll(self.handle, buf, max_n, ctypes.byref(n)), "lilac_server_poll")
+        out = []
+        for i in range(n.value):
+            c = buf[i]
+            out.append({"tag": c.tag, "status": c.status, "iters": c.iters, "rel_res": c.rel_res,
+                        "arrival": c.arrival, "finish": c.finish})
+            self._keep.pop(("r", c.tag), None)
+        return out
+
+    def stats(self):
+        st = lilac_server_stats_t()
+        _check(_lib().lilac_server_stats(self.handle, ctypes.byref(st)), "lilac_server_stats")
+        return {f: getattr(st, f) for f, _ in lilac_server_stats_t._fields_}
+
+    @staticmethod
+    def now():
+        return float(_lib().lilac_server_now())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().lilac_server_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

@@ -1,0 +1,121 @@
+"""The request server: every request of a mixed SpMV / CG stream completes
+with the oracle's result (SpMV tolerance; CG true residual <= 1e-10), a
+request's result is bitwise the same alone and in the mix, and a small
+device-memory budget forces evictions and waiting without changing results."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2001_07938_gb300 import inputs
+from paper_2001_07938_gb300 import lilac as L
+from lilac_testutil import spmv_tolerance, torch_cuda, true_rel_residual
+
+pytestmark = pytest.mark.gpu
+
+
+def _pool():
+    return [inputs.laplacian2d(20), inputs.laplacian2d(37), inputs.banded_spd(3000, 8, 1.0, 1),
+            inputs.banded_spd(12000, 30, 1.0, 2), inputs.spd_random(5000, 12, 20.0, 3),
+            inputs.laplacian3d(12)]
+
+
+def _requests(pool, n, seed):
+    """(kind, matrix index, input, tag) for a seeded mix of SpMV and CG requests."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for t in range(n):
+        mi = int(rng.integers(len(pool)))
+        A = pool[mi]
+        if rng.random() < 0.5:
+            k = int(rng.integers(1, 4))
+            x = inputs.uniform(1000 + t, k * A.ncols)
+            out.append(("spmv", mi, x, k, t))
+        else:
+            b = inputs.uniform(2000 + t, A.n)
+            out.append(("cg", mi, b, 1, t))
+    return out
+
+
+def _serve(pool, reqs, budget=None, burst=7):
+    torch_cuda()
+    S = L.Server(hbm_budget_bytes=budget, iters_per_round=8)
+    ids = [S.add_matrix(A) for A in pool]
+    outs, results = {}, {}
+    i = 0
+    while i < len(reqs) or len(results) < len(reqs):
+        for kind, mi, inp, k, tag in reqs[i:i + burst]:
+            A = pool[mi]
+            if kind == "spmv":
+                out = np.full(k * A.n, np.nan)
+                S.submit(L.LILAC_REQ_SPMV, ids[mi], inp, out, tag, nvec=k)
+            else:
+                out = np.full(A.n, np.nan)
+                S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, tag, max_iter=5000, rtol=1e-10)
+            outs[tag] = out
+        i += burst
+        S.step()
+        for c in S.poll():
+            results[c["tag"]] = c
+    stats = S.stats()
+    S.close()
+    return outs, results, stats
+
+
+def _check(pool, reqs, outs, results):
+    for kind, mi, inp, k, tag in reqs:
+        A, out, c = pool[mi], outs[tag], results[tag]
+        assert c["status"] == L.LILAC_OK, (tag, c)
+        assert c["finish"] >= c["arrival"]
+        if kind == "spmv":
+            for j in range(k):
+                x = inp[j * A.ncols:(j + 1) * A.ncols]
+                y = out[j * A.n:(j + 1) * A.n]
+                ref = oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
+                assert np.all(np.abs(y - ref) <= spmv_tolerance(A, x, False)), tag
+        else:
+            assert true_rel_residual(A, inp, out) <= 1e-10, tag
+
+
+def test_mixed_stream_matches_oracle():
+    pool = _pool()
+    reqs = _requests(pool, 60, seed=0)
+    outs, results, stats = _serve(pool, reqs)
+    assert stats["completed"] == 60 and stats["submitted"] == 60
+    _check(pool, reqs, outs, results)
+
+
+def test_same_result_alone_and_in_the_mix():
+    pool = _pool()
+    reqs = _requests(pool, 40, seed=1)
+    outs_mix, _, _ = _serve(pool, reqs)
+    for probe in [r for r in reqs if r[0] == "cg"][:3] + [r for r in reqs if r[0] == "spmv"][:3]:
+        outs_alone, _, _ = _serve(pool, [probe])
+        np.testing.assert_array_equal(outs_alone[probe[4]], outs_mix[probe[4]])
+
+
+def test_small_budget_evicts_and_waits_but_results_hold():
+    pool = _pool()
+    reqs = _requests(pool, 40, seed=2)
+    budget = 13 << 20  # the largest matrix fits, the whole pool (~18 MB) does not
+    outs, results, stats = _serve(pool, reqs, budget=budget, burst=40)
+    _check(pool, reqs, outs, results)
+    assert stats["evictions"] > 0 and stats["uploads"] > len(pool)
+
+
+def test_invalid_requests_are_rejected():
+    torch_cuda()
+    S = L.Server()
+    A = inputs.laplacian2d(8)
+    mid = S.add_matrix(A)
+    x = np.zeros(A.n)
+    with pytest.raises(L.LilacError):
+        S.submit(L.LILAC_REQ_SPMV, mid + 5, x, x, 0)
+    with pytest.raises(L.LilacError):
+        S.submit(L.LILAC_REQ_SPMV, mid, x, x, 0, nvec=0)
+    big = L.Server(hbm_budget_bytes=1 << 10)
+    bid = big.add_matrix(A)
+    with pytest.raises(L.LilacError) as e:
+        big.submit(L.LILAC_REQ_CG, bid, x, x, 0)
+    assert e.value.status == L.LILAC_ERR_BUDGET
+    S.close()
+    big.close()
