@@ -486,6 +486,151 @@ class IR192(Workload):
 WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192": IR192}
 
 
+# --- served request stream ------------------------------------------------------
+
+def served_stream(n_req=2000, n_mats=32, n_lo=1e3, n_hi=2e5, kmax=8, seed=0):
+    """Seeded request stream: a pool of 2D/3D Laplacians and banded SPD matrices
+    (half-bandwidth 8..64) with n log-uniform in [n_lo, n_hi]; requests pick a
+    matrix with Zipf(1.1) popularity; half are SpMV batches of k in [1, kmax]
+    vectors, half CG solves to 1e-10 (b uniform in [-1, 1])."""
+    from paper_2001_07938_gb300 import inputs
+    rng = np.random.default_rng(seed)
+    pool = []
+    for i in range(n_mats):
+        n = float(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+        kind = i % 3
+        if kind == 0:
+            pool.append(inputs.laplacian2d(max(4, int(round(n ** 0.5)))))
+        elif kind == 1:
+            pool.append(inputs.laplacian3d(max(3, int(round(n ** (1 / 3))))))
+        else:
+            pool.append(inputs.banded_spd(int(n), int(rng.integers(8, 65)), 1.0, seed=100 + i))
+    w = 1.0 / np.arange(1, n_mats + 1) ** 1.1
+    w /= w.sum()
+    reqs = []
+    for t in range(n_req):
+        mi = int(rng.choice(n_mats, p=w))
+        A = pool[mi]
+        if rng.random() < 0.5:
+            k = int(rng.integers(1, kmax + 1))
+            reqs.append(("spmv", mi, inputs.uniform(10_000 + t, k * A.ncols), k))
+        else:
+            reqs.append(("cg", mi, inputs.uniform(20_000 + t, A.n), 1))
+    return pool, reqs
+
+
+def run_served(args):
+    import torch
+    from paper_2001_07938_gb300 import build as lbuild
+    from paper_2001_07938_gb300 import lilac as L
+    torch.cuda.set_device(0)
+    lbuild.build()
+    L.load()
+    pool, reqs = served_stream(n_req=args.served_requests)
+    N = len(reqs)
+    n_cg = sum(1 for r in reqs if r[0] == "cg")
+    # plain: one request at a time through lilac_spmv / lilac_cg (FP64), matrices resident
+    Ms = [L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE) for A in pool]
+    outs_plain = []
+
+    def plain_one(r):
+        kind, mi, inp, k = r
+        A, M = pool[mi], Ms[mi]
+        if kind == "spmv":
+            out = np.empty(k * A.n)
+            for j in range(k):
+                M.spmv(inp[j * A.ncols:(j + 1) * A.ncols], out[j * A.n:(j + 1) * A.n])
+        else:
+            out = np.zeros(A.n)
+            M.cg(inp, out, max_iter=20000, rtol=1e-10, true_residual=False)
+        return out
+
+    for r in reqs[:20]:  # warm-up (graph capture per matrix)
+        plain_one(r)
+    service = []
+    t_all = time.perf_counter()
+    for r in reqs:
+        t0 = time.perf_counter()
+        outs_plain.append(plain_one(r))
+        service.append(time.perf_counter() - t0)
+    plain_makespan = time.perf_counter() - t_all
+    for M in Ms:
+        M.close()
+    cap = N / plain_makespan
+    lam = args.served_load * cap
+    rng = np.random.default_rng(1)
+    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+    fin, lat_plain = 0.0, []
+    for a, sv in zip(arrivals, service):  # FIFO single server, exact from service times
+        fin = max(fin, a) + sv
+        lat_plain.append(fin - a)
+
+    def serve(timed_arrivals):
+        S = L.Server(iters_per_round=args.served_round)
+        ids = [S.add_matrix(A) for A in pool]
+        outs = [None] * N
+        lat = [0.0] * N
+        got = 0
+        t0 = L.Server.now()
+        i = 0
+        while got < N:
+            now = L.Server.now() - t0
+            while i < N and (timed_arrivals is None or timed_arrivals[i] <= now):
+                kind, mi, inp, k = reqs[i]
+                A = pool[mi]
+                out = np.empty(k * A.n) if kind == "spmv" else np.zeros(A.n)
+                outs[i] = out
+                if kind == "spmv":
+                    S.submit(L.LILAC_REQ_SPMV, ids[mi], inp, out, i, nvec=k)
+                else:
+                    S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, i, max_iter=20000, rtol=1e-10)
+                i += 1
+            pending = S.step()
+            for c in S.poll():
+                # latency from the scheduled arrival when arrivals are timed
+                a = c["arrival"] if timed_arrivals is None else t0 + timed_arrivals[c["tag"]]
+                lat[c["tag"]] = c["finish"] - a
+                got += 1
+            if pending == 0 and i < N and timed_arrivals is not None:
+                time.sleep(max(0.0, min(0.01, timed_arrivals[i] - (L.Server.now() - t0))))
+        makespan = L.Server.now() - t0
+        st = S.stats()
+        S.close()
+        return outs, lat, makespan, st
+
+    serve(None)  # warm-up: graph capture, pool blocks
+    outs_s, _, served_makespan, st_sat = serve(None)
+    _, lat_served, _, st_poisson = serve(arrivals)
+    # agreement of the two systems (library only): relative max difference
+    diff = max(float(np.max(np.abs(a - b)) / max(1e-300, float(np.max(np.abs(b)))))
+               for a, b in zip(outs_s, outs_plain))
+    value = N / served_makespan
+    line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1,
+            "steps": 1, "warmup": 1, "ms_per_step": served_makespan * 1000,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "served_stream", "requests": N, "cg_requests": n_cg,
+                       "matrices": len(pool), "n_range": [1e3, 2e5], "zipf": 1.1,
+                       "spmv_vectors": "1..8", "rtol": 1e-10,
+                       "arrivals": f"Poisson at {args.served_load} x plain capacity",
+                       "iters_per_round": args.served_round,
+                       "note": "scaled-down stream (10,000 requests, n up to 2e6 in the full recipe)"},
+            "served": {"requests_per_s": value, "cg_solves_per_s": n_cg / served_makespan,
+                       "latency_ms": {"p50": 1000 * float(np.percentile(lat_served, 50)),
+                                      "p99": 1000 * float(np.percentile(lat_served, 99))},
+                       "rounds": st_sat["rounds"], "uploads": st_sat["uploads"]},
+            "plain": {"requests_per_s": cap, "cg_solves_per_s": n_cg / plain_makespan,
+                      "latency_ms": {"p50": 1000 * float(np.percentile(lat_plain, 50)),
+                                     "p99": 1000 * float(np.percentile(lat_plain, 99))}},
+            "served_vs_plain_throughput": value / cap,
+            "max_rel_diff_served_vs_plain": diff,
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0, "note": "requests carry host buffers end to end"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # --- the two arms ---------------------------------------------------------------
 
 def _dist():
@@ -641,8 +786,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lilac", "reference"], default="lilac")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="cg75k")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="cg75k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--served-requests", type=int, default=2000)
+    ap.add_argument("--served-load", type=float, default=0.8)
+    ap.add_argument("--served-round", type=int, default=16)
     ap.add_argument("--variant", default="",
                     help="force the SpMV kernel instead of the tuner's choice, e.g. slab:4")
     args = ap.parse_args()
@@ -650,6 +798,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_lilac(args)
 
 
