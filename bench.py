@@ -326,11 +326,14 @@ class PageRank22(Workload):
     unit = "GB/s"
     dtype = "f32"
     iters = 20
+    scale = 22  # --rmat-scale: smaller graphs of the same recipe for profiling
 
     def __init__(self, L, torch):
         super().__init__(L, torch)
         from paper_2001_07938_gb300 import inputs
-        self.A = inputs.workload_rmat_pagerank()
+        if self.scale != 22:
+            self.name = f"pagerank_rmat{self.scale}_20it"
+        self.A = inputs.workload_rmat_pagerank(scale=self.scale)
         self.work_per_step = self.iters * self.iter_bytes() / 1e9
 
     def iter_bytes(self):
@@ -788,6 +791,8 @@ def main():
     ap.add_argument("--impl", choices=["lilac", "reference"], default="lilac")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served"], default="cg75k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rmat-scale", type=int, default=22,
+                    help="R-MAT scale of the pagerank22 workload (22 is the benchmark size)")
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-load", type=float, default=0.8)
     ap.add_argument("--served-round", type=int, default=16)
@@ -796,6 +801,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    PageRank22.scale = args.rmat_scale
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "served":

@@ -77,8 +77,9 @@ typedef enum {
     LILAC_VARIANT_VECTOR = 2, /* V lanes per row, V in {2,4,8,16,32}; V = 32 is warp-per-row */
     LILAC_VARIANT_STAGED = 3, /* nnz-balanced row tiles staged in shared memory by bulk
                                  asynchronous copies; rows longer than a tile are split */
-    LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) over CTAs, rows that
-                                 cross CTAs finished from carries; lanes per row 1, 4 or 16 */
+    LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) over CTAs; each thread
+                                 walks 8 consecutive path items, rows split between threads or
+                                 CTAs are finished from carries; no lanes-per-row setting */
     LILAC_VARIANT_SLAB = 5    /* row blocks x column slabs, built once per matrix: x is read
                                  from shared memory, one slab of columns at a time; x must be
                                  16-byte aligned (else STAGED runs) */
@@ -146,8 +147,9 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
 
 /* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR,
  * STAGED and SLAB, lanes per row (power of two 1..32; 0 keeps the current
- * one).  Affects later calls.  Choosing SLAB builds its regrouped copy of the
- * matrix on first use (synchronous; errors OOM, CUDA). */
+ * one; SCALAR and MERGE use 1 whatever is passed).  Affects later calls.
+ * Choosing SLAB builds its regrouped copy of the matrix on first use
+ * (synchronous; errors OOM, CUDA). */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
 
 /*

@@ -91,17 +91,28 @@ lilac_status launch_staged(lilac_csr_s* A, const typename Op::ValT* val, const t
     return LILAC_OK;
 }
 
+// Resident CTAs per SM of a MERGE instantiation.  No shared-memory carveout
+// is requested: the driver then sizes shared memory to what the resident CTAs
+// use and leaves the rest to L1 (a larger carveout starves the x gathers in
+// flight, measured at half the speed on a random-column graph).
+template <class Kernel>
+int merge_setup(Kernel kern) {
+    return occupancy_per_sm(kern, kMergeThreads, 0);
+}
+
 template <int V, class Op>
 lilac_status prepare_merge(lilac_csr_s* A) {
-    (void)A;
+    int& bps = bps_slot<V + 128, Op, false>(A->device);
+    if (bps == 0) bps = merge_setup(spmv_merge_kernel<kMergeThreads, kMergeItems, Op>);
     return LILAC_OK;
 }
 
 template <int V, class Op>
 lilac_status launch_merge(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                           const Op& op, cudaStream_t stream) {
+    LILAC_TRY(prepare_merge<V, Op>(A));
     CsrView<typename Op::ValT> view{A->row_ptr.as<int>(), A->col_ind.as<int>(), val, A->rows};
-    spmv_merge_kernel<V, kMergeThreads, kMergeItems, Op><<<(unsigned)A->merge_grid, kMergeThreads, 0, stream>>>(
+    spmv_merge_kernel<kMergeThreads, kMergeItems, Op><<<(unsigned)A->merge_grid, kMergeThreads, 0, stream>>>(
         view, A->nnz, A->merge_coords.as<int2>(), A->merge_per_cta, x, op, A->partials.as<double>(),
         A->merge_carries.as<MergeCarry>(), A->ticket.as<unsigned>());
     LILAC_CUDA_TRY(cudaGetLastError());
@@ -150,13 +161,8 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
 
 #define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, ...)     \
     switch (A->variant) {                                                   \
-        case LILAC_VARIANT_MERGE:                                           \
-            switch (A->vwidth) {                                            \
-                case 1: return FN_MERGE<1, Op>(__VA_ARGS__);                \
-                case 2:                                                     \
-                case 4: return FN_MERGE<4, Op>(__VA_ARGS__);                \
-                default: return FN_MERGE<16, Op>(__VA_ARGS__);              \
-            }                                                               \
+        case LILAC_VARIANT_MERGE: /* thread-sequential: no lanes per row */ \
+            return FN_MERGE<1, Op>(__VA_ARGS__);                            \
         case LILAC_VARIANT_SLAB:                                            \
             switch (A->vwidth) {                                            \
                 case 1:                                                     \

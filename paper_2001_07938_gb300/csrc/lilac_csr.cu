@@ -167,13 +167,13 @@ static void build_tiles(const std::vector<int32_t>& rp, int rows, std::vector<Ti
     }
 }
 
-// Merge-path partition of (rows + nnz) path items over about four CTAs per
-// SM, each range at least one sub-tile long; the start point of every range
+// Merge-path partition of (rows + nnz) path items over `ctas` CTAs (the
+// resident count), each range at least one sub-tile long; the start point of every range
 // is found on the host once (the same search the kernel would do).
 static void build_merge_partition(const std::vector<int32_t>& rp, int rows, int64_t nnz,
-                                  int sm_count, std::vector<int2>& coords, int64_t& per_cta) {
+                                  int ctas, std::vector<int2>& coords, int64_t& per_cta) {
     const int64_t total = (int64_t)rows + nnz;
-    const int64_t target = std::max<int64_t>(1, (int64_t)sm_count * 4);
+    const int64_t target = std::max<int64_t>(1, (int64_t)ctas);
     per_cta = std::max<int64_t>(kMergeItems, (total + target - 1) / target);
     const int64_t G = std::max<int64_t>(1, (total + per_cta - 1) / per_cta);
     coords.resize((size_t)G);
@@ -352,7 +352,14 @@ static lilac_status create_impl(int32_t rows, int32_t ncols, int64_t nnz, const 
     // MERGE partition
     {
         std::vector<int2> coords;
-        build_merge_partition(rp, rows, nnz, A->sm_count, coords, A->merge_per_cta);
+        // as many CTA ranges as the kernel keeps resident (8 per SM with FP32
+        // sums, 5 with FP64)
+        const int per_sm =
+            dtype == LILAC_F64
+                ? merge_setup(spmv_merge_kernel<kMergeThreads, kMergeItems, OpStore<double, double>>)
+                : merge_setup(spmv_merge_kernel<kMergeThreads, kMergeItems, OpStore<float, float>>);
+        build_merge_partition(rp, rows, nnz, std::min(A->sm_count * per_sm, kMaxCtas), coords,
+                              A->merge_per_cta);
         A->merge_grid = (int)coords.size();
         LILAC_TRY(A->merge_coords.alloc(sizeof(int2) * coords.size()));
         LILAC_TRY(A->merge_carries.alloc(sizeof(MergeCarry) * coords.size()));
@@ -389,7 +396,7 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     std::vector<Cand> cands;
     cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
     for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
-    for (int w : {1, 4, 16}) cands.push_back({LILAC_VARIANT_MERGE, w});
+    cands.push_back({LILAC_VARIANT_MERGE, 1});
     // SLAB is selectable (lilac_csr_set_variant) but not a tuning candidate:
     // on the matrices it targets it measured slower than VECTOR.
     // row-per-group kernels serialise a long row in one group: only for
@@ -558,7 +565,7 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
     }
     A->variant = variant;
     if (vector_width) A->vwidth = vector_width;
-    if (variant == LILAC_VARIANT_SCALAR) A->vwidth = 1;
+    if (variant == LILAC_VARIANT_SCALAR || variant == LILAC_VARIANT_MERGE) A->vwidth = 1;
     if (variant == LILAC_VARIANT_VECTOR && A->vwidth < 2) A->vwidth = 2;
     return LILAC_OK;
 }

@@ -39,10 +39,16 @@ constexpr int kSlabTileRows = 256;
 constexpr int kSlabWidth = 8192;
 constexpr int kSlabBlockRows = 512;
 constexpr int kSlabStages = 3;
-// MERGE kernel shape: 256 threads, sub-tiles of 2048 path items, about four
-// CTAs per SM.
-constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 2048;
+// MERGE kernel shape: 256 threads, sub-tiles of 2048 path items (8 per
+// thread); overridable at build time.
+#ifndef LILAC_MERGE_THREADS
+#define LILAC_MERGE_THREADS 256
+#endif
+#ifndef LILAC_MERGE_ITEMS
+#define LILAC_MERGE_ITEMS 2048
+#endif
+constexpr int kMergeThreads = LILAC_MERGE_THREADS;
+constexpr int kMergeItems = LILAC_MERGE_ITEMS;
 constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
 
 void set_last_error(const std::string& msg);

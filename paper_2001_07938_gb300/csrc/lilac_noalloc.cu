@@ -74,7 +74,7 @@ lilac_status noalloc_launch(int32_t rows, int64_t nnz, const int32_t* row_ptr, c
     LILAC_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
     CsrView<T> view{row_ptr, col_ind, vals, rows};
     // CTA start points are searched in the kernel (coords = nullptr)
-    spmv_merge_kernel<4, kMergeThreads, kMergeItems, OpStore<T, T>><<<(unsigned)G, kMergeThreads, 0, s>>>(
+    spmv_merge_kernel<kMergeThreads, kMergeItems, OpStore<T, T>><<<(unsigned)G, kMergeThreads, 0, s>>>(
         view, nnz, nullptr, per_cta, x, OpStore<T, T>{y},
         reinterpret_cast<double*>(scratch + kNoAllocPartialOff), reinterpret_cast<MergeCarry*>(scratch),
         ticket);

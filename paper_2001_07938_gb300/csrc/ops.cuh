@@ -18,9 +18,13 @@ struct OpStore {
     using VecT = T;
     using AccT = T;
     static constexpr int NR = 0;
+    static constexpr bool kTwoPhase = true;
     T* __restrict__ y;
     __device__ bool skip() const { return false; }
+    __device__ void begin() {}
     __device__ void row(int r, AccT s, double*) const { y[r] = s; }
+    __device__ void store(int r, AccT s) const { y[r] = s; }
+    __device__ void reduce(int, double*) const {}
     __device__ void finish(const double*) const {}
 };
 
@@ -52,13 +56,19 @@ struct OpCgPq {
     using VecT = T;
     using AccT = T;
     static constexpr int NR = 1;
+    static constexpr bool kTwoPhase = true;
     T* __restrict__ q;
     const T* __restrict__ p;
     CgState* st;
     __device__ bool skip() const { return cg_done(st); }
+    __device__ void begin() {}
     __device__ void row(int r, AccT s, double* red) const {
         q[r] = s;
         red[0] += double(p[r]) * double(s);
+    }
+    __device__ void store(int r, AccT s) const { q[r] = s; }
+    __device__ void reduce(int r, double* red) const {
+        red[0] += double(p[r]) * double(__ldcg(q + r));
     }
     __device__ void finish(const double* tot) const {
         const double pq = tot[0];
@@ -84,12 +94,14 @@ struct OpResidual {
     using VecT = double;
     using AccT = double;
     static constexpr int NR = 2;
+    static constexpr bool kTwoPhase = false;
     double* __restrict__ r;
     double* __restrict__ p;  // INIT only
     const double* __restrict__ b;
     CgState* st;
     double rtol;
     __device__ bool skip() const { return false; }
+    __device__ void begin() {}
     __device__ void row(int i, AccT s, double* red) const {
         const double bi = b[i];
         const double ri = bi - s;
@@ -280,6 +292,7 @@ struct OpPageRank {
     using VecT = T;
     using AccT = T;
     static constexpr int NR = 2;
+    static constexpr bool kTwoPhase = true;
     T* __restrict__ y;
     const T* __restrict__ x;
     const unsigned* __restrict__ has_out;
@@ -287,12 +300,21 @@ struct OpPageRank {
     double* l1;  // device, one entry per iteration
     T damping;
     int n;
+    T tele;  // set by begin()
     __device__ bool skip() const { return false; }
+    // Teleport term, written by the previous launch; read once per thread
+    // (every thread reads it before its CTA takes a ticket, and this launch's
+    // finish() writes it only after the last ticket).
+    __device__ void begin() { tele = T(__ldcg(&st->teleport)); }
     __device__ void row(int r, AccT s, double* red) const {
-        // written by the previous launch; this launch's finish() runs after every row()
-        const T tele = T(__ldcg(&st->teleport));
         const T yi = damping * s + tele;
         y[r] = yi;
+        red[0] += fabs(double(yi) - double(x[r]));
+        if (is_dangling(has_out, r)) red[1] += double(yi);
+    }
+    __device__ void store(int r, AccT s) const { y[r] = damping * s + tele; }
+    __device__ void reduce(int r, double* red) const {
+        const T yi = __ldcg(y + r);
         red[0] += fabs(double(yi) - double(x[r]));
         if (is_dangling(has_out, r)) red[1] += double(yi);
     }

@@ -11,7 +11,12 @@
 //   using ValT (matrix value type), VecT (x / y type), AccT (row accumulator)
 //   static constexpr int NR                 number of FP64 reductions (0..kMaxRed)
 //   __device__ bool skip() const            true: the whole launch is a no-op
+//   __device__ void begin()                 every thread, once, before any row()
 //   __device__ void row(int r, AccT s, double* red) const
+//   static constexpr bool kTwoPhase   true: also store(r, s) (writes only) and
+//       reduce(r, red) (reads back what store wrote); row() == store + reduce.
+//       The MERGE kernel stores while it walks and reduces later, one row per
+//       thread, so the walk never waits on the epilogue's loads.
 //   __device__ void finish(const double* tot) const   (last CTA, thread 0; NR > 0)
 #pragma once
 
@@ -47,6 +52,7 @@ __global__ void __launch_bounds__(THREADS)
     spmv_rows_kernel(CsrView<typename Op::ValT> A, const typename Op::VecT* __restrict__ x,
                      Op op, Scratch s) {
     if (op.skip()) return;
+    op.begin();
     using AccT = typename Op::AccT;
     constexpr int NR = Op::NR;
     double red[NR > 0 ? NR : 1] = {};
@@ -145,6 +151,7 @@ __global__ void __launch_bounds__(THREADS)
                        int ntiles, const LongRow* __restrict__ longs, int nlong,
                        const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
     if (op.skip()) return;
+    op.begin();
     using ValT = typename Op::ValT;
     using AccT = typename Op::AccT;
     using L = StagedLayout<ValT, AccT, TN, TR>;
@@ -369,6 +376,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                      double* __restrict__ block_red, const typename Op::VecT* __restrict__ x,
                      Op op, Scratch s) {
     if (op.skip()) return;
+    op.begin();
     using ValT = typename Op::ValT;
     using VecT = typename Op::VecT;
     using AccT = typename Op::AccT;
@@ -594,10 +602,15 @@ namespace lilac {
 // row-end list (row_ptr[1..rows]) with the nonzero indices (0..nnz-1) has
 // rows + nnz items; CTA c takes items [c*P, (c+1)*P), so every CTA gets the
 // same mix of row ends and nonzeros whatever the row lengths.  A CTA walks
-// its items in sub-tiles of ITEMS: products of the sub-tile's nonzeros go to
-// shared memory, the sub-tile's end point on the path is found by a search
-// in shared memory, and groups of V lanes sum each row's piece.  A row that
-// is still open at the end of a sub-tile carries its sum to the next one.
+// its items in sub-tiles of ITEMS: the products of the sub-tile's nonzeros go
+// to shared memory, then every thread takes ITEMS/THREADS consecutive path
+// items (its start found by a merge-path search in shared memory) and walks
+// them in order: a nonzero adds its product to the running row sum, a row end
+// closes the row.  A row that starts before the thread's first item (the
+// thread's first closed row, or the row still open at its end) gets the
+// pieces of the earlier threads through a segmented scan keyed by row, so a
+// row of any length costs the same per item as a short one.  A row still open
+// at the end of a sub-tile carries its sum to the next one.
 // Across CTAs, each CTA records a head piece (its first row, which is open
 // at the CTA's start, if it ends in this CTA) and a tail piece (the row
 // open at its end); the last CTA to finish adds, for each row that crosses
@@ -626,30 +639,52 @@ __device__ __forceinline__ int2 merge_path_search(int64_t d, const int* __restri
     return make_int2((int)lo, (int)(d - lo));
 }
 
-template <int V, int THREADS, int ITEMS, class Op>
-__global__ void __launch_bounds__(THREADS)
+// The MERGE kernel runs in little shared memory (~17 KB per CTA with FP32
+// sums, ~25 KB with FP64), which leaves most of the unified L1 / shared array
+// to L1: the x gathers in flight need it (a large shared carveout measured at
+// half the speed on a random-column graph).  Plain stores keep a full SM of
+// CTAs resident (2048 threads, 32 registers).
+#ifndef LILAC_MERGE_RED_THREADS_PER_SM
+#define LILAC_MERGE_RED_THREADS_PER_SM 1024
+#endif
+template <class Op, int THREADS>
+constexpr int merge_min_blocks() {
+    // epilogues with reductions keep more values live (the deferred
+    // reductions overlap the next gathers): half an SM of threads with up to
+    // 64 registers each measured faster than a full SM with spills
+    return (Op::NR > 0 ? LILAC_MERGE_RED_THREADS_PER_SM : 2048) / THREADS;
+}
+
+template <int THREADS, int ITEMS, class Op>
+__global__ void __launch_bounds__(THREADS, merge_min_blocks<Op, THREADS>())
     spmv_merge_kernel(CsrView<typename Op::ValT> A, int64_t nnz, const int2* __restrict__ coords,
                       int64_t per_cta, const typename Op::VecT* __restrict__ x, Op op,
                       double* __restrict__ partials, MergeCarry* __restrict__ carries,
                       unsigned* __restrict__ ticket) {
     using AccT = typename Op::AccT;
     constexpr int NR = Op::NR;
-    constexpr int NGROUPS = THREADS / V;
     constexpr int IPT = ITEMS / THREADS;
-    static_assert(ITEMS % THREADS == 0, "items per sub-tile must be a multiple of the block size");
+    constexpr int NWARPS = THREADS / 32;
+    static_assert(ITEMS % THREADS == 0 && THREADS % 32 == 0,
+                  "items per sub-tile must be a multiple of the block size, a multiple of 32");
     if (op.skip()) return;
+    op.begin();
 
     __shared__ int rp_s[ITEMS + 2];
     __shared__ AccT prod_s[ITEMS];
-    __shared__ int s_i, s_j, s_ie, s_je, s_head_pending, s_head_row;
-    __shared__ AccT s_running, s_running_next, s_head_v;
+    __shared__ int w_key[NWARPS];
+    __shared__ AccT w_val[NWARPS];
+    // path point, carried row sum and head flag at the start of a sub-tile,
+    // double-buffered by sub-tile parity (one barrier per sub-tile hands over)
+    __shared__ int s_i[2], s_j[2], s_head_pending[2];
+    __shared__ AccT s_running[2];
+    __shared__ int s_head_row;
+    __shared__ AccT s_head_v;
     __shared__ double sh_red[kMaxRed * 32];
     __shared__ int am_last;
 
     const int tid = threadIdx.x;
-    const int lane = tid & (V - 1);
-    const int group = tid / V;
-    const unsigned mask = group_mask<V>(tid);
+    const int lane = tid & 31, warp = tid >> 5;
     const int rows = A.rows;
     const int64_t total = (int64_t)rows + nnz;
     const int64_t D0 = (int64_t)blockIdx.x * per_cta;
@@ -659,23 +694,43 @@ __global__ void __launch_bounds__(THREADS)
     if (tid == 0) {
         int2 st = make_int2(rows, (int)nnz);
         if (D0 < total) st = coords ? coords[blockIdx.x] : merge_path_search(D0, A.row_ptr, rows, nnz);
-        s_i = st.x;
-        s_j = st.y;
+        s_i[0] = st.x;
+        s_j[0] = st.y;
         // the row open at the CTA's start is the previous CTA's tail: its
         // piece here always goes through the carries
-        s_head_pending = (blockIdx.x > 0 && D0 < total && st.x < rows) ? 1 : 0;
+        s_head_pending[0] = (blockIdx.x > 0 && D0 < total && st.x < rows) ? 1 : 0;
+        s_running[0] = AccT(0);
         s_head_row = -1;
         s_head_v = AccT(0);
-        s_running = AccT(0);
     }
     __syncthreads();
-    for (int64_t d = D0; d < D1;) {
-        const int64_t d_end = d + ITEMS < D1 ? d + ITEMS : D1;
-        const int i = s_i, j = s_j;
-        // row_ptr[i .. i + nrw) and the products of nonzeros [j, jz)
+    constexpr bool kDeferred = Op::kTwoPhase && NR > 0;
+    constexpr int RPT = (ITEMS + 2 + THREADS - 1) / THREADS;
+    // rows closed by the previous sub-tile whose reductions are still due
+    int prev_i = 0, prev_n = 0, prev_head = 0;
+    int p = 0;
+    for (int64_t d = D0; d < D1; d += ITEMS, p ^= 1) {
+        const int len = (int)(D1 - d < ITEMS ? D1 - d : ITEMS);
+        const int i = s_i[p], j = s_j[p];
+        const AccT running = s_running[p];
+        const int head_pending = s_head_pending[p];
+        // row_ptr[i .. i + nrw): the sub-tile closes at most `len` rows
         const int nrw = min(ITEMS + 2, rows + 1 - i);
-        for (int t = tid; t < nrw; t += THREADS) rp_s[t] = __ldg(A.row_ptr + i + t);
-        const int jz = (int)min((int64_t)j + ITEMS, nnz);
+        // (with deferred reductions the row_ptr loads stay in registers until
+        // the gathers are issued; otherwise they go straight to shared memory,
+        // which needs fewer registers)
+        int rv[kDeferred ? RPT : 1];
+        if constexpr (kDeferred) {
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int t = q * THREADS + tid;
+                rv[q] = t < nrw ? __ldg(A.row_ptr + i + t) : 0;
+            }
+        } else {
+            for (int t = tid; t < nrw; t += THREADS) rp_s[t] = __ldg(A.row_ptr + i + t);
+        }
+        // products of nonzeros [j, jz): the sub-tile holds at most `len` of them
+        const int jz = (int)min((int64_t)j + len, nnz);
         int cj[IPT];
         typename Op::VecT xj[IPT];
 #pragma unroll
@@ -688,61 +743,122 @@ __global__ void __launch_bounds__(THREADS)
             const int k = j + q * THREADS + tid;
             xj[q] = k < jz ? __ldg(x + cj[q]) : typename Op::VecT(0);
         }
+        if constexpr (kDeferred) {
+            // reductions of the rows the previous sub-tile closed: their loads
+            // overlap this sub-tile's gathers
+            for (int q = tid; q < prev_n; q += THREADS)
+                if (q > 0 || !prev_head) op.reduce(prev_i + q, red);
+#pragma unroll
+            for (int q = 0; q < RPT; ++q) {
+                const int t = q * THREADS + tid;
+                if (t < nrw) rp_s[t] = rv[q];
+            }
+        }
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
             const int k = j + q * THREADS + tid;
             if (k < jz) prod_s[k - j] = AccT(ld_stream(A.val + k)) * AccT(xj[q]);
         }
         __syncthreads();
-        if (tid == 0) {
-            // end point of the sub-tile on the path, searched in shared memory
-            int64_t lo = d_end - nnz > i ? d_end - nnz : i;
-            int64_t hi = d_end - j < rows ? d_end - j : rows;
+        // this thread's path items [o0, o1) of the sub-tile; its start point
+        // (r, k), r + k = d + o0, by a merge-path search in shared memory
+        const int o0 = min(tid * IPT, len), o1 = min(o0 + IPT, len);
+        int r, k;
+        {
+            const int64_t dd = d + o0;
+            int64_t lo = dd - nnz > i ? dd - nnz : i;
+            int64_t hi = dd - j < rows ? dd - j : rows;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                if ((int64_t)rp_s[mid + 1 - i] <= d_end - mid - 1)
+                if ((int64_t)rp_s[mid + 1 - i] <= dd - mid - 1)
                     lo = mid + 1;
                 else
                     hi = mid;
             }
-            s_ie = (int)lo;
-            s_je = (int)(d_end - lo);
-            s_running_next = AccT(0);
+            r = (int)lo;
+            k = (int)(dd - lo);
         }
-        __syncthreads();
-        const int ie = s_ie, je = s_je;
-        // rows [i, ie) end in this sub-tile; row ie (if any) stays open
-        const int nr = ie - i + (ie < rows ? 1 : 0);
-        for (int rr = group; rr < nr; rr += NGROUPS) {
-            const int r = i + rr;
-            const int a = max(rp_s[rr], j) - j;
-            const int b = (r < ie ? rp_s[rr + 1] : je) - j;
-            AccT sum = AccT(0);
-            for (int k = a + lane; k < b; k += V) sum += prod_s[k];
-            if constexpr (V > 1) sum = group_sum<V>(sum, mask);
-            if (lane == 0) {
-                if (r == i) sum += s_running;
-                if (r < ie) {
-                    if (r == i && s_head_pending) {
-                        s_head_row = r;
-                        s_head_v = sum;
-                    } else {
-                        op.row(r, sum, red);
-                    }
+        // walk: rows closed after the first one are complete here; the first
+        // (row r at the start) waits for the earlier threads' pieces
+        AccT acc = AccT(0), first_v = AccT(0);
+        int first_r = -1;
+        for (int o = o0; o < o1; ++o) {
+            if (k < rp_s[r + 1 - i]) {
+                acc += prod_s[k - j];
+                ++k;
+            } else {
+                if (first_r < 0) {
+                    first_r = r;
+                    first_v = acc;
+                } else if constexpr (Op::kTwoPhase) {
+                    op.store(r, acc);
                 } else {
-                    s_running_next = sum;
+                    op.row(r, acc, red);
                 }
+                acc = AccT(0);
+                ++r;
             }
         }
-        __syncthreads();
-        if (tid == 0) {
-            s_running = ie < rows ? s_running_next : AccT(0);
-            if (ie > i) s_head_pending = 0;
-            s_i = ie;
-            s_j = je;
+        // inclusive segmented scan of the open-row pieces, keyed by row (keys
+        // do not decrease with the thread index): within the warp ...
+        const int key = r;
+        AccT v = acc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const AccT vu = __shfl_up_sync(0xffffffffu, v, off);
+            const int ku = __shfl_up_sync(0xffffffffu, key, off);
+            if (lane >= off && ku == key) v += vu;
+        }
+        if (lane == 31) {
+            w_key[warp] = key;
+            w_val[warp] = v;
         }
         __syncthreads();
-        d = d_end;
+        // ... then across the earlier warps' totals
+        AccT pre = AccT(0);
+        int pre_key = -1;
+        for (int w = 0; w < warp; ++w) {
+            const int kw = w_key[w];
+            pre = kw == pre_key ? pre + w_val[w] : w_val[w];
+            pre_key = kw;
+        }
+        const AccT full = (warp > 0 && key == pre_key) ? v + pre : v;
+        // pieces of row r before this thread = the previous thread's scan
+        const AccT up = __shfl_up_sync(0xffffffffu, full, 1);
+        const AccT incoming = lane > 0 ? up : (warp > 0 ? pre : AccT(0));
+        if (first_r >= 0) {
+            AccT sum = incoming + first_v;
+            if (first_r == i) sum = running + sum;
+            if (first_r == i && head_pending) {
+                s_head_row = i;
+                s_head_v = sum;
+            } else if constexpr (Op::kTwoPhase) {
+                op.store(first_r, sum);
+            } else {
+                op.row(first_r, sum, red);
+            }
+        }
+        if (tid == THREADS - 1) {
+            // the last thread ends where the sub-tile ends
+            s_i[p ^ 1] = r;
+            s_j[p ^ 1] = k;
+            s_running[p ^ 1] = r == i ? running + full : full;
+            s_head_pending[p ^ 1] = r > i ? 0 : head_pending;
+        }
+        __syncthreads();
+        if constexpr (kDeferred) {
+            // the reductions over the rows closed here, [i, ie), run in the next
+            // sub-tile (or below), consecutive rows on consecutive threads; the
+            // barrier made the stores visible.  The CTA's open first row is
+            // finished from the carries instead.
+            prev_i = i;
+            prev_n = s_i[p ^ 1] - i;
+            prev_head = head_pending;
+        }
+    }
+    if constexpr (kDeferred) {
+        for (int q = tid; q < prev_n; q += THREADS)
+            if (q > 0 || !prev_head) op.reduce(prev_i + q, red);
     }
     // publish carries and partial sums; the last CTA fixes up and finishes
     double tot[NR > 0 ? NR : 1];
@@ -756,9 +872,9 @@ __global__ void __launch_bounds__(THREADS)
         MergeCarry mc;
         mc.head_row = s_head_row;
         mc.head_v = (double)s_head_v;
-        const bool open_tail = D0 < total && s_i < rows;
-        mc.tail_row = open_tail ? s_i : -1;
-        mc.tail_v = open_tail ? (double)s_running : 0.0;
+        const bool open_tail = D0 < total && s_i[p] < rows;
+        mc.tail_row = open_tail ? s_i[p] : -1;
+        mc.tail_v = open_tail ? (double)s_running[p] : 0.0;
         carries[blockIdx.x] = mc;
 #pragma unroll
         for (int q = 0; q < NR; ++q) partials[blockIdx.x * NR + q] = tot[q];

@@ -89,6 +89,30 @@ def test_one_huge_row_and_tiny_shapes():
     _check_all_variants(one, np.float64)
 
 
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_merge_empty_runs_and_rows_across_ctas(dtype):
+    """MERGE: runs of empty rows longer than a CTA's path range, rows whose
+    nonzeros span many sub-tiles and CTAs, tiny rows between them, an empty
+    tail; every row closed exactly once, and the same bits on a second call."""
+    rng = np.random.default_rng(1)
+    lens = np.concatenate([np.zeros(50_000, np.int64), [400_000], rng.integers(0, 4, 200_000),
+                           np.zeros(30_000, np.int64), [90_000], rng.integers(0, 40, 30_000),
+                           np.zeros(1_000, np.int64)])
+    rp = np.concatenate([[0], np.cumsum(lens)]).astype(np.int32)
+    nnz = int(rp[-1])
+    ncols = 50_000
+    A = inputs.CSR(len(lens), ncols, rp, rng.integers(0, ncols, nnz).astype(np.int32),
+                   rng.uniform(-1, 1, nnz)).astype(dtype)
+    x = inputs.uniform(23, ncols, dtype=dtype)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_MERGE, 0)
+    y1 = _run(M, x, dtype)
+    y2 = _run(M, x, dtype)
+    M.close()
+    assert_spmv_close(A, x.astype(np.float64), y1, dtype == np.float32, "merge extremes")
+    assert np.array_equal(y1, y2)
+
+
 def test_all_empty_rows_and_zero_rows():
     torch = torch_cuda()
     A = inputs.CSR(1000, 10, np.zeros(1001, np.int32), np.zeros(0, np.int32), np.zeros(0))
