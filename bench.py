@@ -398,6 +398,7 @@ class IR192(Workload):
     name = "cg_mixed_poisson3d_m192_to_1e-10"
     unit = "solves/s"
     dtype = "f32 inner / f64 refinement"
+    precision = 2  # --ir-precision: 2 reliable updates, 1 restarted refinement
 
     def __init__(self, L, torch):
         super().__init__(L, torch)
@@ -410,6 +411,9 @@ class IR192(Workload):
         return {"workload": self.name, "matrix": "3D 7-point Poisson, 192^3 grid, FP32 values",
                 "n": A.n, "nnz": A.nnz, "rtol": 1e-10, "b": "uniform [-1,1], seed 1",
                 "index": "int32",
+                "mixed_precision": ("FP32 CG with FP64 reliable updates (residual replacement)"
+                                    if self.precision == 2 else
+                                    "FP32 inner CG restarted by FP64 iterative refinement"),
                 "l2": f"inputs larger than L2 ({A.nnz * 8 / 1e6:.0f} MB matrix), no flush"}
 
     def setup(self):
@@ -417,12 +421,19 @@ class IR192(Workload):
         self.M = L.CsrMatrix.from_csr(self.A)
         self.bd = torch.from_numpy(self.b).cuda()
         self.xd = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
-        self.opts = L.lilac_cg_opts_default()
-        self.opts.precision, self.opts.rtol, self.opts.max_iter = 1, 1e-10, 30
-        self.opts.inner_max_iter, self.opts.inner_rtol = 4000, 1e-5
+        self.opts = self._opts(self.precision)
         st, info = L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(),
                               L.LILAC_MEM_DEVICE, self.opts, want_info=True)
         self.launches_per_step = info.kernel_launches
+
+    def _opts(self, precision):
+        o = self.L.lilac_cg_opts_default()
+        o.precision, o.rtol = precision, 1e-10
+        if precision == 1:
+            o.max_iter, o.inner_max_iter, o.inner_rtol = 30, 4000, 1e-5
+        else:
+            o.max_iter, o.ru_delta = 20000, 0.1
+        return o
 
     def step(self):
         L = self.L
@@ -435,6 +446,20 @@ class IR192(Workload):
                               L.LILAC_MEM_DEVICE, self.opts, want_info=True)
         res = {"status": L.lilac_status_string(st), "inner_iters": info.iters,
                "refinements": info.refinements, "true_rel_res": info.true_rel_res}
+        # the other mixed-precision form on the same handle, timed once
+        other = 1 if self.precision == 2 else 2
+        oo = self._opts(other)
+        L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(), L.LILAC_MEM_DEVICE, oo,
+                   want_info=False)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st2, i2 = L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(),
+                             L.LILAC_MEM_DEVICE, oo, want_info=True)
+        torch.cuda.synchronize()
+        res[f"precision_{other}"] = {"solves_per_s": 1.0 / (time.perf_counter() - t0),
+                                     "status": L.lilac_status_string(st2), "iters": i2.iters,
+                                     "refinements": i2.refinements,
+                                     "true_rel_res": i2.true_rel_res}
         # plain FP64 CG on the same system: the comparator
         M64 = L.CsrMatrix.from_csr(self.A.astype(np.float64))
         x64 = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
@@ -793,6 +818,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--rmat-scale", type=int, default=22,
                     help="R-MAT scale of the pagerank22 workload (22 is the benchmark size)")
+    ap.add_argument("--ir-precision", type=int, choices=[1, 2], default=2,
+                    help="mixed-precision CG of the ir192 workload")
     ap.add_argument("--served-requests", type=int, default=2000)
     ap.add_argument("--served-load", type=float, default=0.8)
     ap.add_argument("--served-round", type=int, default=16)
@@ -802,6 +829,7 @@ def main():
     if args.warmup < 3:
         args.warmup = 3
     PageRank22.scale = args.rmat_scale
+    IR192.precision = args.ir_precision
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "served":

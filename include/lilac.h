@@ -167,9 +167,12 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
 lilac_status lilac_spmv(lilac_csr A, const void* x, void* y, lilac_mem where, void* stream);
 
 typedef struct {
-    int32_t max_iter;       /* iteration cap (FP64 CG) or outer-refinement cap (mixed) */
+    int32_t max_iter;       /* iteration cap (precisions 0 and 2) or outer-refinement cap (1) */
     double rtol;            /* stop when ||r|| <= rtol ||b||; <= 0: run exactly max_iter */
-    int32_t precision;      /* 0: FP64 CG.  1: FP32 inner CG + FP64 iterative refinement */
+    int32_t precision;      /* 0: FP64 CG.  1: FP32 inner CG + FP64 iterative refinement.
+                               2: FP32 CG with FP64 reliable updates (x += d and the
+                               residual replaced by b - A x, both in FP64, whenever the
+                               FP32 residual fell by ru_delta; the search direction is kept) */
     double inner_rtol;      /* mixed: inner stop ||r_in|| <= inner_rtol ||r_outer|| */
     int32_t inner_max_iter; /* mixed: inner iteration cap per refinement */
     int32_t use_x0;         /* 1: start from x as given; 0: start from x = 0 */
@@ -178,11 +181,12 @@ typedef struct {
     int32_t check_every;    /* iterations between host convergence checks when rtol > 0 */
     int32_t profile;        /* 1: time every SpMV launch of the solve with CUDA events
                                (reported in lilac_cg_info; needs info) */
+    double ru_delta;        /* precision 2: replacement threshold in (0, 1) */
 } lilac_cg_opts;
 
 typedef struct {
     int32_t iters;          /* CG iterations done (all inner iterations when mixed) */
-    int32_t refinements;    /* mixed: outer refinement steps */
+    int32_t refinements;    /* precision 1: outer refinement steps; 2: residual replacements */
     int32_t status;         /* lilac_status of the solve */
     int32_t pad;
     double rel_res;         /* recursive (FP64 CG) or outer true (mixed) ||r|| / ||b|| */
@@ -194,7 +198,7 @@ typedef struct {
 
 /* Fill *o with the defaults: max_iter 1000, rtol 1e-10, FP64, inner_rtol
  * 1e-5, inner_max_iter 1000, use_x0 0, true_residual 1, use_graph 1,
- * check_every 32, profile 0. */
+ * check_every 32, profile 0, ru_delta 0.1. */
 void lilac_cg_opts_default(lilac_cg_opts* o);
 
 /*
@@ -205,10 +209,10 @@ void lilac_cg_opts_default(lilac_cg_opts* o);
  * fused into one pass; p = r + beta p.  The scalars stay on the device.
  *   b, x    rows FP64 elements; x holds x0 on entry if opts->use_x0, the
  *           solution on exit.  `where` as in lilac_spmv.
- *   opts    NULL: defaults.  precision 1 needs ncols == rows; the inner
- *           solves use FP32 values (the handle's, or an FP32 copy derived
- *           once from FP64 values) and the FP64 residual b - A x uses the
- *           handle's own values.
+ *   opts    NULL: defaults.  Precisions 1 and 2 run the FP32 iterations on
+ *           FP32 values (the handle's, or an FP32 copy derived once from
+ *           FP64 values) and compute the FP64 residual b - A x with the
+ *           handle's own values; their rel_res is that FP64 residual.
  *   info    nullable; if given, the call synchronizes `stream` at the end.
  * Returns OK, NOT_CONVERGED (rtol > 0 not reached), BREAKDOWN, or an error.
  * With rtol > 0 the call synchronizes `stream` every check_every iterations.

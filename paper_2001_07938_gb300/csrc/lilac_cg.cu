@@ -46,7 +46,7 @@ static lilac_status ensure_cg_work(lilac_csr A, CgWork& W, bool f32) {
     return LILAC_OK;
 }
 
-enum GraphKind { G_CG64_FIXED = 1, G_CG64_CHUNK = 2, G_CG32_CHUNK = 3 };
+enum GraphKind { G_CG64_FIXED = 1, G_CG64_CHUNK = 2, G_CG32_CHUNK = 3, G_CGRU_CHUNK = 4 };
 
 // Profiling of the SpMV launches (opts->profile): event pairs recorded on the
 // launching stream around every SpMV, also inside captured graphs.
@@ -252,6 +252,107 @@ static lilac_status cg_mixed(lilac_csr A, const double* b, double* x, const lila
     return LILAC_OK;
 }
 
+// Mixed precision with reliable updates: one FP32 CG (FP32 values and
+// vectors, FP64 scalars) whose residual is replaced by the FP64 residual
+// b - A x whenever it has fallen by ru_delta, with x accumulated in FP64.
+// One iteration is five launches; K3 and K4 return at once unless a
+// replacement is due:
+//   K1  q = A p, p.q -> alpha            (FP32 values)
+//   K2  d += alpha p, r -= alpha q, r.r  -> beta, or flag a replacement
+//   K3  x += d, d = 0                    (FP64 x)
+//   K4  r = float(b - A x), ||b - A x||  (handle values, FP64) -> beta, convergence
+//   K5  p = r + beta p
+template <class V>
+static lilac_status enqueue_iters_ru(lilac_csr A, const float* val32, const V* val, const double* b,
+                                     double* x, float* d, CgWork& W, int nit, cudaStream_t s,
+                                     bool profile) {
+    const int n = A->rows;
+    const int vg = vec_grid(A, n);
+    CgState* st = W.state.as<CgState>();
+    float* r = W.r.as<float>();
+    float* p = W.p.as<float>();
+    float* q = W.q.as<float>();
+    for (int it = 0; it < nit; ++it) {
+        if (profile)
+            LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it], s, cudaEventRecordExternal));
+        LILAC_TRY(launch_spmv(A, val32, p, OpCgPq<float, float>{q, p, st}, s));
+        if (profile)
+            LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
+        cg_update_kernel<float><<<vg, kVecThreads, 0, s>>>(n, d, r, p, q, FinCgUpdateRU{st},
+                                                           A->scratch());
+        ru_apply_kernel<<<vg, kVecThreads, 0, s>>>(n, x, d, st);
+        LILAC_TRY(launch_spmv(A, val, x, OpResidualRU<V>{r, b, st}, s));
+        cg_direction_kernel<float><<<vg, kVecThreads, 0, s>>>(n, r, p, st);
+    }
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+template <class V>
+static lilac_status cg_mixed_ru_impl(lilac_csr A, const V* val, const double* b, double* x,
+                                     const lilac_cg_opts& o, cudaStream_t s, CgState* hs,
+                                     lilac_cg_info* info, Prof& prof) {
+    LILAC_TRY(make_val32(A, s));
+    const float* val32 = A->dtype == LILAC_F32 ? A->val.as<float>() : A->val32.as<float>();
+    CgWork& W = A->cg32;
+    LILAC_TRY(ensure_cg_work(A, W, true));
+    const int n = A->rows;
+    if (!A->cg_outer_r.p || A->cg_outer_r.bytes < sizeof(double) * (size_t)std::max(1, n))
+        LILAC_TRY(A->ws_alloc(A->cg_outer_r, sizeof(double) * (size_t)std::max(1, n)));
+    if (!A->ir_x.p || A->ir_x.bytes < sizeof(float) * (size_t)std::max(1, n))
+        LILAC_TRY(A->ws_alloc(A->ir_x, sizeof(float) * (size_t)std::max(1, n)));
+    double* r64 = A->cg_outer_r.as<double>();
+    float* d = A->ir_x.as<float>();
+    CgState* st = W.state.as<CgState>();
+    LILAC_TRY(prepare_spmv<OpResidual<V, RES_OUTER>>(A));
+    LILAC_TRY(prepare_spmv<OpResidualRU<V>>(A));
+    LILAC_TRY(prepare_spmv<OpCgPq<float, float>>(A));
+    if (!o.use_x0) LILAC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+    cg_state_reset_kernel<<<1, 1, 0, s>>>(st, o.max_iter);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    {
+        OpResidual<V, RES_OUTER> op{r64, nullptr, b, st, o.rtol};
+        LILAC_TRY(launch_spmv(A, val, x, op, s));
+    }
+    const double delta = o.ru_delta;
+    ru_start_kernel<<<vec_grid(A, n), kVecThreads, 0, s>>>(n, r64, W.r.as<float>(), W.p.as<float>(), d,
+                                                           FinRuStart{st, delta * delta}, A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    prof.kernels += 3;
+    const int chunk = o.check_every;
+    const uint64_t pflag = prof.on ? 1 : 0;
+    if (prof.on) LILAC_TRY(ensure_prof_events(A, chunk));
+    LILAC_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    int launched = 0;
+    while (!hs->done && launched < o.max_iter) {
+        const int nit = std::min(chunk, o.max_iter - launched);
+        GraphKey key{G_CGRU_CHUNK, b, x, nit, pflag, A->variant, A->vwidth, A->ws_gen};
+        LILAC_TRY(run_maybe_graph(A, key, o.use_graph != 0, s, [&](cudaStream_t cs) {
+            return enqueue_iters_ru<V>(A, val32, val, b, x, d, W, nit, cs, prof.on);
+        }));
+        launched += nit;
+        prof.kernels += 5 * nit;
+        LILAC_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+        if (prof.on) LILAC_TRY(collect_prof(A, nit, prof));
+    }
+    info->iters = hs->iters;
+    info->refinements = hs->updates;
+    info->status = hs->done ? hs->status : LILAC_ERR_NOT_CONVERGED;
+    const double rr = hs->true_rr >= 0.0 ? hs->true_rr : hs->rr;
+    info->rel_res = hs->bb > 0.0 ? std::sqrt(rr / hs->bb) : 0.0;
+    info->true_rel_res = info->rel_res;  // the last FP64 residual b - A x
+    return LILAC_OK;
+}
+
+static lilac_status cg_mixed_ru(lilac_csr A, const double* b, double* x, const lilac_cg_opts& o,
+                                cudaStream_t s, CgState* hs, lilac_cg_info* info, Prof& prof) {
+    if (A->dtype == LILAC_F64)
+        return cg_mixed_ru_impl<double>(A, A->val.as<double>(), b, x, o, s, hs, info, prof);
+    return cg_mixed_ru_impl<float>(A, A->val.as<float>(), b, x, o, s, hs, info, prof);
+}
+
 }  // namespace lilac
 
 using namespace lilac;
@@ -268,6 +369,7 @@ extern "C" void lilac_cg_opts_default(lilac_cg_opts* o) {
     o->use_graph = 1;
     o->check_every = 32;
     o->profile = 0;
+    o->ru_delta = 0.1;
 }
 
 extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_mem where,
@@ -276,9 +378,10 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
     lilac_cg_opts o;
     lilac_cg_opts_default(&o);
     if (opts) o = *opts;
-    if ((A->rows > 0 && (!b || !x)) || o.max_iter < 0 || (o.precision != 0 && o.precision != 1) ||
+    if ((A->rows > 0 && (!b || !x)) || o.max_iter < 0 || o.precision < 0 || o.precision > 2 ||
         o.check_every < 1 || (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE) ||
-        (o.precision == 1 && (o.inner_max_iter < 1 || !(o.inner_rtol > 0.0)))) {
+        (o.precision == 1 && (o.inner_max_iter < 1 || !(o.inner_rtol > 0.0))) ||
+        (o.precision == 2 && !(o.ru_delta > 0.0 && o.ru_delta < 1.0))) {
         set_last_error("invalid argument to lilac_cg");
         return LILAC_ERR_INVALID_ARG;
     }
@@ -326,8 +429,10 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
                                      ? std::sqrt(hs.true_rr / hs.bb)
                                      : (o.true_residual && hs.bb == 0.0 ? 0.0 : -1.0);
         }
-    } else {
+    } else if (o.precision == 1) {
         st = cg_mixed(A, bd, xd, o, s, &hs, &local, prof);
+    } else {
+        st = cg_mixed_ru(A, bd, xd, o, s, &hs, &local, prof);
     }
     if (st != LILAC_OK) return st;
     if (A->profiling) {
@@ -341,9 +446,9 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
         LILAC_CUDA_TRY(cudaMemcpyAsync(x, xd, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    if (info || o.rtol > 0.0 || o.precision == 1) LILAC_TRY(check_device_status(A, s));
+    if (info || o.rtol > 0.0 || o.precision != 0) LILAC_TRY(check_device_status(A, s));
     if (info) *info = local;
-    if (info || o.rtol > 0.0 || o.precision == 1) {
+    if (info || o.rtol > 0.0 || o.precision != 0) {
         if (local.status == LILAC_ERR_BREAKDOWN || local.status == LILAC_ERR_NOT_CONVERGED)
             return (lilac_status)local.status;
     }

@@ -43,6 +43,11 @@ struct CgState {
     int max_iter;
     int done;        // 1: later iteration kernels are no-ops
     int status;      // lilac_status of the solve so far
+    // mixed precision with reliable updates
+    double rr_anchor;  // FP32 residual r.r right after the last replacement
+    double delta2;     // replace when r.r <= delta2 * rr_anchor
+    int update;        // 1: this iteration replaces r by the FP64 residual
+    int updates;       // replacements done
 };
 
 __device__ __forceinline__ bool cg_done(const CgState* st) {
@@ -195,10 +200,10 @@ struct FinCgUpdate {
     }
 };
 
-template <class T>
+template <class T, class Fin>
 static __global__ void __launch_bounds__(kVecThreads)
     cg_update_kernel(int n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                     const T* __restrict__ q, FinCgUpdate<T> fin, Scratch s) {
+                     const T* __restrict__ q, Fin fin, Scratch s) {
     if (cg_done(fin.st)) return;
     const T alpha = T(fin.st->alpha);
     double red[1] = {0.0};
@@ -219,6 +224,114 @@ static __global__ void __launch_bounds__(kVecThreads)
     const T beta = T(st->beta);
     for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
         p[i] = r[i] + beta * p[i];
+}
+
+// ---------------------------------------------------------------------------
+// Mixed precision with reliable updates (residual replacement, in the manner
+// of van der Vorst & Ye, "Residual replacement strategies for Krylov subspace
+// iterative methods for the convergence of true residuals", SISC 2000): one
+// FP32 CG whose correction d accumulates in FP32; when its recursive residual
+// has fallen by delta since the last replacement (or reaches the tolerance,
+// or the iteration cap), x += d in FP64, d = 0, and r is replaced by
+// float(b - A x) computed in FP64, keeping the search direction.
+
+// K2 epilogue: flag a replacement instead of taking beta from the recursive r.
+struct FinCgUpdateRU {
+    CgState* st;
+    __device__ void finish(const double* tot) const {
+        const double rr_new = tot[0];
+        const int it = st->iters + 1;
+        st->iters = it;
+        if (rr_new <= st->delta2 * st->rr_anchor || rr_new == 0.0 ||
+            (st->tol2 >= 0.0 && rr_new <= st->tol2) || it >= st->max_iter) {
+            st->update = 1;  // st->rr keeps the previous r.r for beta
+        } else {
+            st->beta = rr_new / st->rr;
+            st->rr = rr_new;
+        }
+    }
+};
+
+__device__ __forceinline__ bool ru_due(const CgState* st) {
+    return *reinterpret_cast<const volatile int*>(&st->update) != 0 && !cg_done(st);
+}
+
+// x += d (FP64), d = 0, when a replacement is due.
+static __global__ void __launch_bounds__(kVecThreads)
+    ru_apply_kernel(int n, double* __restrict__ x, float* __restrict__ d, const CgState* st) {
+    if (!ru_due(st)) return;
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+        x[i] += double(d[i]);
+        d[i] = 0.0f;
+    }
+}
+
+// r = float(b - A x) with b - A x in FP64 (values of any type promoted);
+// ||b - A x||^2 decides convergence, float(r).float(r) gives beta.
+template <class V>
+struct OpResidualRU {
+    using ValT = V;
+    using VecT = double;
+    using AccT = double;
+    static constexpr int NR = 2;
+    static constexpr bool kTwoPhase = false;
+    float* __restrict__ r;
+    const double* __restrict__ b;
+    CgState* st;
+    __device__ bool skip() const { return !ru_due(st); }
+    __device__ void begin() {}
+    __device__ void row(int i, AccT s, double* red) const {
+        const double ri = b[i] - s;
+        const float rf = float(ri);
+        r[i] = rf;
+        red[0] += ri * ri;
+        red[1] += double(rf) * double(rf);
+    }
+    __device__ void finish(const double* tot) const {
+        st->true_rr = tot[0];
+        st->updates += 1;
+        st->update = 0;
+        if (tot[0] == 0.0 || (st->tol2 >= 0.0 && tot[0] <= st->tol2)) {
+            st->done = 1;
+            st->status = LILAC_OK;
+        } else if (st->iters >= st->max_iter) {
+            st->done = 1;
+            st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+        } else {
+            st->beta = tot[1] / st->rr;  // r.r before this iteration
+            st->rr = tot[1];
+            st->rr_anchor = tot[1];
+        }
+    }
+};
+
+// Start: r = p = float(r64), d = 0, r.r (after an FP64 residual r64 = b - A x0).
+struct FinRuStart {
+    CgState* st;
+    double delta2;
+    __device__ void finish(const double* tot) const {
+        st->rr = tot[0];
+        st->rr_anchor = tot[0];
+        st->delta2 = delta2;
+        st->update = 0;
+        st->updates = 0;
+        st->iters = 0;
+        st->true_rr = st->bb > 0.0 ? -1.0 : 0.0;
+    }
+};
+
+static __global__ void __launch_bounds__(kVecThreads)
+    ru_start_kernel(int n, const double* __restrict__ r64, float* __restrict__ r,
+                    float* __restrict__ p, float* __restrict__ d, FinRuStart fin, Scratch s) {
+    double red[1] = {0.0};
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+        const float rf = float(r64[i]);
+        r[i] = rf;
+        p[i] = rf;
+        d[i] = 0.0f;
+        red[0] += double(rf) * double(rf);
+    }
+    grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
 }
 
 // Mixed precision: x += d / scale (FP64), after an inner FP32 solve of

@@ -66,7 +66,8 @@ class lilac_cg_opts(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("inner_rtol", ctypes.c_double),
                 ("inner_max_iter", ctypes.c_int32), ("use_x0", ctypes.c_int32),
                 ("true_residual", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("check_every", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("ru_delta", ctypes.c_double)]
 
 
 class lilac_cg_info(ctypes.Structure):
@@ -474,9 +475,10 @@ class CsrMatrix:
 
     def cg(self, b, x, *, max_iter=1000, rtol=1e-10, precision=0, inner_rtol=1e-5,
            inner_max_iter=1000, use_x0=False, true_residual=True, use_graph=True,
-           check_every=32, want_info=True, profile=False, stream=None):
+           check_every=32, want_info=True, profile=False, ru_delta=0.1, stream=None):
         o = lilac_cg_opts_default()
         o.profile = int(profile)
+        o.ru_delta = ru_delta
         o.max_iter, o.rtol, o.precision = max_iter, rtol, precision
         o.inner_rtol, o.inner_max_iter = inner_rtol, inner_max_iter
         o.use_x0, o.true_residual, o.use_graph = int(use_x0), int(true_residual), int(use_graph)
