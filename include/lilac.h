@@ -80,9 +80,13 @@ typedef enum {
     LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) over CTAs; each thread
                                  walks 8 consecutive path items, rows split between threads or
                                  CTAs are finished from carries; no lanes-per-row setting */
-    LILAC_VARIANT_SLAB = 5    /* row blocks x column slabs, built once per matrix: x is read
+    LILAC_VARIANT_SLAB = 5,   /* row blocks x column slabs, built once per matrix: x is read
                                  from shared memory, one slab of columns at a time; x must be
                                  16-byte aligned (else STAGED runs) */
+    LILAC_VARIANT_JDS = 6     /* jagged diagonal storage (Section 3.2), built once per matrix:
+                                 rows sorted by length, one thread per row, nonzero d of all
+                                 rows stored together; on another value array (an FP32 copy)
+                                 STAGED runs */
 } lilac_variant;
 
 /* lilac_csr_create flags.  By default create times the candidate SpMV
@@ -151,6 +155,21 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
  * Choosing SLAB builds its regrouped copy of the matrix on first use
  * (synchronous; errors OOM, CUDA). */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
+
+/*
+ * The handle's jagged diagonal storage (the JDS format of Section 3.2), built
+ * on first use of LILAC_VARIANT_JDS or by this call (synchronous), copied to
+ * host buffers (NULL pointers are skipped):
+ *   perm     rows entries: perm[r] = slot of row r; rows are sorted by length,
+ *            longest first, rows of equal length in row order
+ *   jd_ptr   max_row_len + 1 entries: jagged diagonal d holds the d-th nonzero
+ *            of every row longer than d, at [jd_ptr[d], jd_ptr[d+1]), by slot
+ *   col_ind, vals  nnz entries (vals in the handle's dtype), JDS order
+ *   nzcnt    rows entries: nonzeros of the row in slot s
+ * Errors: INVALID_ARG, OOM, CUDA.
+ */
+lilac_status lilac_csr_jds(lilac_csr A, int32_t* perm, int32_t* jd_ptr, int32_t* col_ind,
+                           void* vals, int32_t* nzcnt);
 
 /*
  * y = A x (the paper's spmv_csr computation, Section 3.2):

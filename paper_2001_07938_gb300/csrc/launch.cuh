@@ -119,6 +119,37 @@ lilac_status launch_merge(lilac_csr_s* A, const typename Op::ValT* val, const ty
     return LILAC_OK;
 }
 
+// JDS: the copy holds the handle's own values; another value array (an FP32
+// copy) goes to STAGED, as does a handle whose copy is not built.
+template <int V, class Op>
+lilac_status prepare_jds(lilac_csr_s* A) {
+    int& bps = bps_slot<V + 192, Op, false>(A->device);
+    if (bps == 0) {
+        auto kern = spmv_jds_kernel<kRowsThreads, Op>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        bps = occupancy_per_sm(kern, kRowsThreads, 0);
+    }
+    return prepare_staged<V, Op>(A);
+}
+
+template <int V, class Op>
+lilac_status launch_jds(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                        const Op& op, cudaStream_t stream) {
+    if (!A->jds_built || (const void*)val != A->val.p) return launch_staged<V, Op>(A, val, x, op, stream);
+    LILAC_TRY(prepare_jds<V, Op>(A));
+    const int bps = bps_slot<V + 192, Op, false>(A->device);
+    int64_t grid = (int64_t)A->sm_count * bps;
+    const int64_t need = ((int64_t)A->rows + kRowsThreads - 1) / kRowsThreads;
+    if (grid > need) grid = need;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) grid = 1;
+    spmv_jds_kernel<kRowsThreads, Op><<<(unsigned)grid, kRowsThreads, 0, stream>>>(
+        A->rows, A->jds_slot_row.as<int>(), A->jds_len.as<int>(), A->jds_ptr.as<int>(),
+        A->jds_col.as<int>(), A->jds_val.as<typename Op::ValT>(), x, op, A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
 template <int V, class Op>
 using SlabLayoutOf = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
                                 kSlabTileRows, kSlabWidth, kSlabBlockRows, kSlabStages>;
@@ -159,10 +190,12 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
     return LILAC_OK;
 }
 
-#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, ...)     \
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, FN_JDS, ...) \
     switch (A->variant) {                                                   \
         case LILAC_VARIANT_MERGE: /* thread-sequential: no lanes per row */ \
             return FN_MERGE<1, Op>(__VA_ARGS__);                            \
+        case LILAC_VARIANT_JDS: /* one thread per row */                    \
+            return FN_JDS<1, Op>(__VA_ARGS__);                              \
         case LILAC_VARIANT_SLAB:                                            \
             switch (A->vwidth) {                                            \
                 case 1:                                                     \
@@ -202,14 +235,15 @@ lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
 
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
-    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge, A)
+    LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge,
+                        prepare_jds, A)
 }
 
 template <class Op>
 lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, A, val, x, op,
-                        stream)
+    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, launch_jds, A, val,
+                        x, op, stream)
 }
 
 // Replay `body` (which enqueues work on the stream it is given) as a CUDA

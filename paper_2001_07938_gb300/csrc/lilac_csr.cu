@@ -240,7 +240,9 @@ int64_t lilac_csr_s::device_bytes() const {
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
-                                  &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out};
+                                  &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out,
+                                  &jds_slot_row, &jds_row_slot, &jds_len, &jds_ptr, &jds_col,
+                                  &jds_val};
     int64_t t = 0;
     for (auto* b : all) t += (int64_t)b->bytes;
     return t;
@@ -405,6 +407,17 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
         for (int w : {4, 8, 16, 32}) cands.push_back({LILAC_VARIANT_VECTOR, w});
         cands.push_back({LILAC_VARIANT_SCALAR, 1});
     }
+    // JDS (one thread per row, rows sorted by length): its copy is built for
+    // the trial and kept only if it wins
+    bool jds_trial = false;
+    if (A->max_row_len <= 1024 && !A->jds_built) {
+        if (ensure_jds(A, stream) == LILAC_OK) {
+            jds_trial = true;
+            cands.push_back({LILAC_VARIANT_JDS, 1});
+        } else {
+            jds_release(A);
+        }
+    }
     cudaEvent_t e0, e1;
     LILAC_CUDA_TRY(cudaEventCreate(&e0));
     LILAC_CUDA_TRY(cudaEventCreate(&e1));
@@ -437,6 +450,10 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     cudaEventDestroy(e1);
     A->variant = bestc.variant;
     A->vwidth = bestc.width;
+    if (jds_trial && bestc.variant != LILAC_VARIANT_JDS) {
+        LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
+        jds_release(A);
+    }
     return LILAC_OK;
 }
 
@@ -457,6 +474,7 @@ static void free_handle(lilac_csr A) {
                             &A->cg32.state, &A->cg_outer_state, &A->cg_outer_r, &A->ir_x, &A->ir_b,
                             &A->pr_y, &A->pr_state, &A->pr_l1, &A->pr_has_out};
     for (auto* b : all) b->release();
+    jds_release(A);
     delete A;
 }
 
@@ -514,6 +532,7 @@ lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem wh
     A->h2d_bytes += (int64_t)(vsz * (size_t)A->nnz);
     A->val32_valid = false;  // derived FP32 copy is stale
     LILAC_TRY(slab_refresh_values(A, s));
+    LILAC_TRY(jds_refresh_values(A, s));
     return LILAC_OK;
 }
 
@@ -553,7 +572,7 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
     }
-    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_SLAB ||
+    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_JDS ||
         (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
                                (vector_width & (vector_width - 1)) != 0))) {
         set_last_error("unsupported variant / width");
@@ -563,9 +582,15 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         DeviceGuard g(A->device);
         LILAC_TRY(ensure_slab(A, nullptr));
     }
+    if (variant == LILAC_VARIANT_JDS) {
+        DeviceGuard g(A->device);
+        LILAC_TRY(ensure_jds(A, nullptr));
+    }
     A->variant = variant;
     if (vector_width) A->vwidth = vector_width;
-    if (variant == LILAC_VARIANT_SCALAR || variant == LILAC_VARIANT_MERGE) A->vwidth = 1;
+    if (variant == LILAC_VARIANT_SCALAR || variant == LILAC_VARIANT_MERGE ||
+        variant == LILAC_VARIANT_JDS)
+        A->vwidth = 1;
     if (variant == LILAC_VARIANT_VECTOR && A->vwidth < 2) A->vwidth = 2;
     return LILAC_OK;
 }

@@ -125,6 +125,11 @@ struct lilac_csr_s {
     lilac::DevBuf slab_cta_tiles, slab_cta_slabs, slab_P, slab_cnt, slab_block_red;
     int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0, slab_grid = 0;
     bool slab_built = false;
+    // JDS copy (built on first use): slot -> row, row -> slot, slot lengths,
+    // jagged diagonal offsets, columns and values in JDS order
+    lilac::DevBuf jds_slot_row, jds_row_slot, jds_len, jds_ptr, jds_col, jds_val;
+    int jds_njd = 0;
+    bool jds_built = false;
     // MERGE partition (computed at create): start of each CTA's path range
     lilac::DevBuf merge_coords, merge_carries;
     int merge_grid = 0;
@@ -173,6 +178,9 @@ struct DeviceGuard {
 lilac_status check_handle(lilac_csr A);
 lilac_status make_val32(lilac_csr A, cudaStream_t stream);
 lilac_status ensure_slab(lilac_csr A, cudaStream_t stream);
+lilac_status ensure_jds(lilac_csr A, cudaStream_t stream);
+lilac_status jds_refresh_values(lilac_csr A, cudaStream_t stream);
+void jds_release(lilac_csr A);
 lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
 bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status check_device_status(lilac_csr A, cudaStream_t stream);

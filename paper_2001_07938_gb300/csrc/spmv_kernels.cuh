@@ -592,6 +592,42 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// JDS kernel (jagged diagonal storage, Section 3.2): slot s holds the s-th
+// longest row (row slot_row[s], len[s] nonzeros); jagged diagonal d stores
+// the d-th nonzero of every slot with len > d, contiguously by slot.  One
+// thread per slot: consecutive threads read consecutive entries of each
+// diagonal (coalesced), and the threads of a warp have about the same row
+// length.  A row's products are added in nonzero order.
+template <int THREADS, class Op>
+__global__ void __launch_bounds__(THREADS)
+    spmv_jds_kernel(int rows, const int* __restrict__ slot_row, const int* __restrict__ len,
+                    const int* __restrict__ jd_ptr, const int* __restrict__ col,
+                    const typename Op::ValT* __restrict__ val,
+                    const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
+    if (op.skip()) return;
+    op.begin();
+    using AccT = typename Op::AccT;
+    constexpr int NR = Op::NR;
+    double red[NR > 0 ? NR : 1] = {};
+    for (int sl = blockIdx.x * THREADS + threadIdx.x; sl < rows; sl += gridDim.x * THREADS) {
+        const int L = __ldg(len + sl);
+        AccT sum = AccT(0);
+#pragma unroll 4
+        for (int d = 0; d < L; ++d) {
+            const int k = __ldg(jd_ptr + d) + sl;
+            sum += AccT(ld_stream(val + k)) * AccT(__ldg(x + ld_stream(col + k)));
+        }
+        op.row(__ldg(slot_row + sl), sum, red);
+    }
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+    }
+}
+
 }  // namespace lilac
 
 namespace lilac {

@@ -31,7 +31,7 @@ LILAC_ERR_UNSUPPORTED = 10
 LILAC_F64, LILAC_F32 = 0, 1
 LILAC_MEM_HOST, LILAC_MEM_DEVICE = 0, 1
 LILAC_VARIANT_AUTO, LILAC_VARIANT_SCALAR, LILAC_VARIANT_VECTOR, LILAC_VARIANT_STAGED, \
-    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB = 0, 1, 2, 3, 4, 5
+    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB, LILAC_VARIANT_JDS = 0, 1, 2, 3, 4, 5, 6
 LILAC_CREATE_NO_TUNE = 0x1
 
 VARIANT_NAMES = {1: "scalar", 2: "vector", 3: "staged", 4: "merge", 5: "slab"}
@@ -45,7 +45,7 @@ EXPORTS = (
     "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_opts_default",
     "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
-    "lilac_server_now",
+    "lilac_server_now", "lilac_csr_jds",
 )
 
 LILAC_REQ_SPMV, LILAC_REQ_CG = 0, 1
@@ -135,6 +135,7 @@ def _lib():
         lib.lilac_csr_destroy.argtypes = [vp]
         lib.lilac_csr_info.argtypes = [vp, c.POINTER(lilac_csr_info_t)]
         lib.lilac_csr_set_variant.argtypes = [vp, i32, i32]
+        lib.lilac_csr_jds.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
         lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
         lib.lilac_cg_opts_default.restype = None
@@ -172,7 +173,8 @@ def _lib():
                      "lilac_csr_profile", "lilac_batch_create", "lilac_batch_destroy",
                      "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_create",
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
-                     "lilac_server_step", "lilac_server_poll", "lilac_server_stats"):
+                     "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
+                     "lilac_csr_jds"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -258,6 +260,12 @@ def lilac_csr_info(A) -> dict:
 
 def lilac_csr_set_variant(A, variant, vector_width=0):
     _check(_lib().lilac_csr_set_variant(A, variant, vector_width), "lilac_csr_set_variant")
+
+
+def lilac_csr_jds(A, perm, jd_ptr, col_ind, vals, nzcnt):
+    """Copy the handle's JDS form into host numpy arrays (None entries skipped)."""
+    p = [a.ctypes.data if a is not None else None for a in (perm, jd_ptr, col_ind, vals, nzcnt)]
+    _check(_lib().lilac_csr_jds(A, *p), "lilac_csr_jds")
 
 
 def lilac_spmv(A, x, y, where, stream=None):
@@ -464,6 +472,16 @@ class CsrMatrix:
 
     def set_variant(self, variant: int, width: int = 0):
         lilac_csr_set_variant(self.handle, variant, width)
+
+    def jds(self):
+        """The handle's JDS form: (perm, jd_ptr, col_ind, vals, nzcnt) as numpy arrays."""
+        inf = self.info()
+        n, nnz = inf["rows"], inf["nnz"]
+        vals = np.empty(nnz, np.float64 if inf["dtype"] == LILAC_F64 else np.float32)
+        out = (np.empty(n, np.int32), np.empty(inf["max_row_len"] + 1, np.int32),
+               np.empty(nnz, np.int32), vals, np.empty(n, np.int32))
+        lilac_csr_jds(self.handle, *out)
+        return out
 
     def spmv(self, x, y, stream=None):
         px, wx = _ptr_where(x)

@@ -55,6 +55,47 @@ def test_paper_example_bit_exact():
     M.close()
 
 
+def test_paper_jds_example_bit_exact():
+    """The handle's JDS form of the paper's CSR example is the paper's printed
+    JDS example (Section 3.2), array for array."""
+    g = load_golden("csr_example_5x5.txt")
+    j = load_golden("jds_example_5x5.txt")
+    A = inputs.CSR(5, 5, np.array(g["row_ptr"], np.int32), np.array(g["col_ind"], np.int32),
+                   np.array(g["val"], np.float64))
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    perm, jd_ptr, col, val, nzcnt = M.jds()
+    M.close()
+    assert perm.tolist() == j["perm"]
+    assert jd_ptr.tolist() == j["jd_ptr"]
+    assert col.tolist() == j["col_ind"]
+    assert val.tolist() == [float(t) for t in j["val"]]
+    assert nzcnt.tolist() == j["nzcnt"]
+
+
+def test_jds_matches_oracle_conversion_and_follows_value_updates():
+    """JDS arrays equal the oracle's CSR-to-JDS conversion (bit-exact) on a
+    matrix with empty rows and ties; the JDS kernel follows
+    lilac_csr_update_values."""
+    torch = torch_cuda()
+    A = inputs.random_csr(4000, 3000, 12, 0.2, seed=11)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_JDS)
+    perm, jd_ptr, col, val, nzcnt = M.jds()
+    J = oracle.csr_to_jds(A.row_ptr, A.col_ind, A.vals)
+    assert np.array_equal(perm, J["perm"]) and np.array_equal(jd_ptr, J["jd_ptr"])
+    assert np.array_equal(col, J["col_ind"]) and np.array_equal(val, J["val"])
+    assert np.array_equal(nzcnt, J["nzcnt"])
+    x = inputs.uniform(5, A.ncols)
+    assert_spmv_close(A, x, _run(M, x, np.float64), False, "jds")
+    v2 = inputs.uniform(6, A.nnz)
+    M2 = inputs.CSR(A.n, A.ncols, A.row_ptr, A.col_ind, v2)
+    v2d = dev(v2)
+    L.lilac_csr_update_values(M.handle, v2d.data_ptr(), L.LILAC_MEM_DEVICE)
+    torch.cuda.synchronize()
+    assert_spmv_close(M2, x, _run(M, x, np.float64), False, "jds after update")
+    M.close()
+
+
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("shape", [(3000, 2500, 40), (777, 5000, 9), (5000, 300, 3)])
 def test_random_with_empty_rows_duplicates_unsorted(dtype, shape):
