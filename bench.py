@@ -511,7 +511,91 @@ class IR192(Workload):
         self.M.close()
 
 
-WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192": IR192}
+class BFS22(Workload):
+    """BFS levels on the R-MAT scale-22 graph (transposed adjacency handle), from
+    the vertex of largest out-degree; GTEPS = edges of the reached component /
+    time (the GAP convention)."""
+    name = "bfs_rmat22"
+    unit = "GTEPS"
+    dtype = "int32"
+
+    def __init__(self, L, torch):
+        super().__init__(L, torch)
+        from paper_2001_07938_gb300 import inputs
+        self.A = inputs.workload_rmat_pagerank()
+        outdeg = np.bincount(self.A.col_ind, minlength=self.A.n)
+        self.src = int(np.argmax(outdeg))
+        self.edges = None
+        self.depth = None
+
+    def config(self):
+        A = self.A
+        return {"workload": self.name, "matrix": "R-MAT scale 22 (as pagerank22), transposed",
+                "n": A.n, "nnz": A.nnz, "source": self.src, "index": "int32",
+                "l2": f"inputs larger than L2: {A.nnz * 8 / 1e6:.0f} MB of indices, no flush"}
+
+    def setup(self):
+        torch, L = self.torch, self.L
+        self.M = L.CsrMatrix.from_csr(self.A)
+        self.lv = torch.empty(self.A.n, dtype=torch.int32, device="cuda")
+        self.depth = self.M.bfs(self.src, self.lv)
+        torch.cuda.synchronize()
+        reached = self.lv.cpu().numpy() >= 0
+        self.edges = int(np.diff(self.A.row_ptr)[reached].sum())
+        self.work_per_step = self.edges / 1e9
+        self.launches_per_step = 1 + 8 * ((self.depth + 8) // 8)
+
+    def step(self):
+        self.M.bfs(self.src, self.lv)
+
+    def check(self):
+        lv = self.lv.cpu().numpy()
+        return {"depth": self.depth, "reached": int((lv >= 0).sum()), "edges": self.edges}
+
+    def roofline_sample(self, k):
+        """Whole BFS timed with events; bytes = the lower bound of its launches:
+        each of depth + 1 level launches streams the row index of every nonzero
+        and reads a level per row, and every column index is read at least once."""
+        torch = self.torch
+        A = self.A
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            self.step()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        nbytes = (self.depth + 1) * (A.nnz * 4 + A.n * 4) + A.nnz * 4
+        return ms, k, nbytes, "bfs_pull_kernel x (depth + 1), whole BFS (lower-bound bytes)"
+
+    def e2e_setup(self):
+        self.lh = self.torch.empty(self.A.n, dtype=self.torch.int32).pin_memory()
+        self.e2e_bytes = (0, self.A.n * 4)
+
+    def e2e_step(self):
+        self.L.lilac_bfs(self.M.handle, self.src, self.lh.data_ptr(), self.L.LILAC_MEM_HOST)
+
+    def close(self):
+        self.M.close()
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        A = self.A
+        rows = np.repeat(np.arange(A.n, dtype=np.int32), np.diff(A.row_ptr))
+        order = np.argsort(A.col_ind, kind="stable")
+        rp = np.zeros(A.n + 1, np.int64)
+        np.cumsum(np.bincount(A.col_ind, minlength=A.n), out=rp[1:])
+        t0 = time.perf_counter()
+        lev = oracle.bfs_levels(rp.astype(np.int32), rows[order], self.src)
+        t = time.perf_counter() - t0
+        if self.edges is None:  # reference arm: no GPU run to take it from
+            self.edges = int(np.diff(A.row_ptr)[lev >= 0].sum())
+            self.work_per_step = self.edges / 1e9
+        return self.edges / t / 1e9, "one full oracle BFS (queue, out-edge lists) from the same source"
+
+
+WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192": IR192,
+             "bfs22": BFS22}
 
 
 # --- served request stream ------------------------------------------------------
@@ -730,7 +814,7 @@ def run_lilac(args):
     wl.setup()
     if args.variant:
         name, _, width = args.variant.partition(":")
-        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5}
+        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6}
         wl.M.set_variant(codes[name], int(width or 0))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None

@@ -259,6 +259,22 @@ lilac_status lilac_pagerank(lilac_csr AT, void* x, int32_t init_uniform, int32_t
                             double damping, double* l1_per_iter, lilac_mem where, void* stream);
 
 /*
+ * Breadth-first search levels from `source` on the TRANSPOSED adjacency
+ * matrix (row v lists the sources u of the edges u -> v, as for
+ * lilac_pagerank; values are ignored): the GAP BFS kernel of Section 5, run
+ * as one masked boolean SpMV per level (an unvisited v joins level L+1 when
+ * one of its in-neighbours is at level L).
+ *   level   rows int32 (host or device per `where`): level of every vertex,
+ *           0 for the source, -1 if unreachable.  The levels are unique, so
+ *           any correct BFS gives the same array.
+ *   depth   nullable: number of levels (1 + the largest level).
+ * Needs rows == ncols.  Synchronizes `stream` every 8 levels.  Errors:
+ * INVALID_ARG (source not a vertex, level NULL), OOM, CUDA.
+ */
+lilac_status lilac_bfs(lilac_csr AT, int32_t source, int32_t* level, lilac_mem where,
+                       int32_t* depth, void* stream);
+
+/*
  * y = A x on CSR arrays the caller already holds on the device, with no
  * device allocation.  The paper has no counterpart: this is for callers that
  * must not call cudaMalloc -- e.g. code running while another component owns

@@ -143,6 +143,8 @@ struct lilac_csr_s {
     lilac::DevBuf cg_outer_state, cg_outer_r, ir_x, ir_b;  // mixed precision outer loop
     lilac::DevBuf pr_y, pr_state, pr_l1, pr_has_out;
     bool pr_has_out_valid = false;
+    // BFS: row index of every nonzero (built on first use), state, staged levels
+    lilac::DevBuf bfs_row, bfs_state, bfs_level;
     cudaStream_t capture_stream = nullptr;
     std::map<lilac::GraphKey, cudaGraphExec_t> graphs;
     std::vector<cudaEvent_t> prof_events;  // pairs around timed SpMV launches

@@ -45,7 +45,7 @@ EXPORTS = (
     "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_opts_default",
     "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
-    "lilac_server_now", "lilac_csr_jds",
+    "lilac_server_now", "lilac_csr_jds", "lilac_bfs",
 )
 
 LILAC_REQ_SPMV, LILAC_REQ_CG = 0, 1
@@ -136,6 +136,7 @@ def _lib():
         lib.lilac_csr_info.argtypes = [vp, c.POINTER(lilac_csr_info_t)]
         lib.lilac_csr_set_variant.argtypes = [vp, i32, i32]
         lib.lilac_csr_jds.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.lilac_bfs.argtypes = [vp, i32, vp, c.c_int, c.POINTER(i32), vp]
         lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
         lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
         lib.lilac_cg_opts_default.restype = None
@@ -174,7 +175,7 @@ def _lib():
                      "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_create",
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
                      "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
-                     "lilac_csr_jds"):
+                     "lilac_csr_jds", "lilac_bfs"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -266,6 +267,14 @@ def lilac_csr_jds(A, perm, jd_ptr, col_ind, vals, nzcnt):
     """Copy the handle's JDS form into host numpy arrays (None entries skipped)."""
     p = [a.ctypes.data if a is not None else None for a in (perm, jd_ptr, col_ind, vals, nzcnt)]
     _check(_lib().lilac_csr_jds(A, *p), "lilac_csr_jds")
+
+
+def lilac_bfs(A, source, level, where, stream=None):
+    """BFS levels from `source` on a transposed adjacency handle; returns the depth."""
+    d = ctypes.c_int32()
+    _check(_lib().lilac_bfs(A, source, level, where, ctypes.byref(d),
+                            stream if stream is not None else current_stream()), "lilac_bfs")
+    return d.value
 
 
 def lilac_spmv(A, x, y, where, stream=None):
@@ -472,6 +481,11 @@ class CsrMatrix:
 
     def set_variant(self, variant: int, width: int = 0):
         lilac_csr_set_variant(self.handle, variant, width)
+
+    def bfs(self, source, level, stream=None):
+        """Levels from `source` into `level` (int32, host numpy or device torch); returns depth."""
+        p, w = _ptr_where(level)
+        return lilac_bfs(self.handle, int(source), p, w, stream)
 
     def jds(self):
         """The handle's JDS form: (perm, jd_ptr, col_ind, vals, nzcnt) as numpy arrays."""
