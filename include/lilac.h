@@ -259,6 +259,49 @@ lilac_status lilac_pagerank(lilac_csr AT, void* x, int32_t init_uniform, int32_t
                             double damping, double* l1_per_iter, lilac_mem where, void* stream);
 
 /*
+ * The paper's harness calling convention: y = A x on the caller's own host
+ * arrays with no handle (spmv_csr, Section 3.1), the marshaling done by the
+ * library (Sections 3.3 and 4.2).
+ *   mode LILAC_HOST_CACHED: the library keeps a resident copy per distinct
+ *        (row_ptr, col_ind, vals, rows, ncols, nnz, dtype) and decides what
+ *        changed since it was uploaded: `version` != 0 is the caller's version
+ *        number of the three arrays (the number of the previous call =
+ *        unchanged, nothing is read); otherwise (version 0, or a new number)
+ *        the library hashes the arrays' contents (a host pass over them) and
+ *        compares with the hashes of the upload.  Changed structure rebuilds
+ *        the copy; changed values alone are re-uploaded.
+ *        At most 32 copies are kept (least recently used evicted).
+ *   mode LILAC_HOST_NAIVE: create, upload, tune, multiply and free on every
+ *        call (the naive insertion the paper measures against, Section 6.3).
+ *   ncols < 0: max(col_ind) + 1.  x (ncols) and y (rows) are host arrays of
+ *   `dtype`; the call synchronizes `stream`.  The paper's page-protection
+ *   change tracking is not reproduced: writes the caller hides behind an
+ *   unchanged version number are not seen.
+ * Thread-safe (one lock around the cache).  Errors as lilac_csr_create and
+ * lilac_spmv.
+ */
+typedef enum { LILAC_HOST_CACHED = 0, LILAC_HOST_NAIVE = 1 } lilac_host_mode;
+
+typedef struct {
+    int64_t calls;             /* lilac_spmv_host calls */
+    int64_t uploads;           /* resident copies created (every call when naive) */
+    int64_t value_updates;     /* calls that re-uploaded values only */
+    int64_t structure_changes; /* calls that found a changed structure */
+    int64_t hits;              /* calls that reused a copy unchanged */
+    int64_t hashed_bytes;      /* host bytes hashed by version-0 calls */
+    int32_t resident;          /* copies held now */
+    int32_t pad;
+} lilac_host_stats_t;
+
+lilac_status lilac_spmv_host(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
+                             const int32_t* col_ind, const void* vals, lilac_dtype dtype,
+                             const void* x, void* y, uint64_t version, uint32_t mode, void* stream);
+/* Counters of the host-convention cache since the last clear. */
+lilac_status lilac_host_cache_stats(lilac_host_stats_t* st);
+/* Free every resident copy of the host-convention cache and zero its counters. */
+lilac_status lilac_host_cache_clear(void);
+
+/*
  * Breadth-first search levels from `source` on the TRANSPOSED adjacency
  * matrix (row v lists the sources u of the edges u -> v, as for
  * lilac_pagerank; values are ignored): the GAP BFS kernel of Section 5, run

@@ -45,8 +45,11 @@ EXPORTS = (
     "lilac_batch_destroy", "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_opts_default",
     "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
-    "lilac_server_now", "lilac_csr_jds", "lilac_bfs",
+    "lilac_server_now", "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host",
+    "lilac_host_cache_stats", "lilac_host_cache_clear",
 )
+
+LILAC_HOST_CACHED, LILAC_HOST_NAIVE = 0, 1
 
 LILAC_REQ_SPMV, LILAC_REQ_CG = 0, 1
 
@@ -102,6 +105,13 @@ class lilac_server_stats_t(ctypes.Structure):
                [("queued", ctypes.c_int32), ("active", ctypes.c_int32)]
 
 
+class lilac_host_stats_t(ctypes.Structure):
+    _fields_ = [("calls", ctypes.c_int64), ("uploads", ctypes.c_int64),
+                ("value_updates", ctypes.c_int64), ("structure_changes", ctypes.c_int64),
+                ("hits", ctypes.c_int64), ("hashed_bytes", ctypes.c_int64),
+                ("resident", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+
 class LilacError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -137,6 +147,10 @@ def _lib():
         lib.lilac_csr_set_variant.argtypes = [vp, i32, i32]
         lib.lilac_csr_jds.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.lilac_bfs.argtypes = [vp, i32, vp, c.c_int, c.POINTER(i32), vp]
+        lib.lilac_spmv_host.argtypes = [i32, i32, i64, vp, vp, vp, c.c_int, vp, vp, c.c_uint64,
+                                        u32, vp]
+        lib.lilac_host_cache_stats.argtypes = [c.POINTER(lilac_host_stats_t)]
+        lib.lilac_host_cache_clear.argtypes = []
         lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
         lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
         lib.lilac_cg_opts_default.restype = None
@@ -175,7 +189,8 @@ def _lib():
                      "lilac_batch_spmv", "lilac_batch_cg", "lilac_server_create",
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
                      "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
-                     "lilac_csr_jds", "lilac_bfs"):
+                     "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host", "lilac_host_cache_stats",
+                     "lilac_host_cache_clear"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -267,6 +282,32 @@ def lilac_csr_jds(A, perm, jd_ptr, col_ind, vals, nzcnt):
     """Copy the handle's JDS form into host numpy arrays (None entries skipped)."""
     p = [a.ctypes.data if a is not None else None for a in (perm, jd_ptr, col_ind, vals, nzcnt)]
     _check(_lib().lilac_csr_jds(A, *p), "lilac_csr_jds")
+
+
+def lilac_spmv_host(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, x, y, version=0,
+                    mode=LILAC_HOST_CACHED, stream=None):
+    """y = A x on host arrays with library-side marshaling (pointers as ints)."""
+    _check(_lib().lilac_spmv_host(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, x, y, version,
+                                  mode, stream if stream is not None else current_stream()),
+           "lilac_spmv_host")
+
+
+def lilac_host_cache_stats() -> dict:
+    st = lilac_host_stats_t()
+    _check(_lib().lilac_host_cache_stats(ctypes.byref(st)), "lilac_host_cache_stats")
+    return {f: getattr(st, f) for f, _ in lilac_host_stats_t._fields_ if f != "pad"}
+
+
+def lilac_host_cache_clear():
+    _check(_lib().lilac_host_cache_clear(), "lilac_host_cache_clear")
+
+
+def spmv_host(A, x, y, version=0, naive=False):
+    """Host-convention SpMV of a CSR record (numpy row_ptr/col_ind/vals, x, y)."""
+    lilac_spmv_host(A.n, A.ncols, A.nnz, A.row_ptr.ctypes.data, A.col_ind.ctypes.data,
+                    A.vals.ctypes.data, _dtype_code(A.vals.dtype), x.ctypes.data, y.ctypes.data,
+                    version, LILAC_HOST_NAIVE if naive else LILAC_HOST_CACHED)
+    return y
 
 
 def lilac_bfs(A, source, level, where, stream=None):
