@@ -271,11 +271,13 @@ class SpMV2D(Workload):
         self.yd = torch.empty(self.A.n, dtype=torch.float64, device="cuda")
         self.launches_per_step = self.calls
         self.px, self.py = self.xd.data_ptr(), self.yd.data_ptr()
+        self.stream = torch.cuda.current_stream().cuda_stream
 
     def step(self):
         L, h = self.L, self.M.handle
+        st = self.stream
         for _ in range(self.calls):
-            L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE)
+            L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE, st)
 
     def check(self):
         return {"calls_per_step": self.calls, "us_per_call_note": "ms_per_step / 1000 calls"}
@@ -511,6 +513,92 @@ class IR192(Workload):
         self.M.close()
 
 
+class SpMM8(Workload):
+    """Y = A X for 8 vectors at once (row-major X), the random SPD n=75,000
+    FP64 matrix: each nonzero is streamed once for all 8 vectors."""
+    name = "spmm_spd_n75000_k8"
+    unit = "GB/s"
+    dtype = "f64"
+    k = 8
+
+    def __init__(self, L, torch):
+        super().__init__(L, torch)
+        from paper_2001_07938_gb300 import inputs
+        self.A, _ = inputs.workload_spd_cg()
+        A = self.A
+        self.nbytes = A.nnz * 12 + (A.n + 1) * 4 + self.k * (A.ncols + A.n) * 8
+        self.work_per_step = self.nbytes / 1e9
+
+    def config(self):
+        A = self.A
+        return {"workload": self.name, "matrix": "random SPD, ~181 nnz/row, uniform columns",
+                "n": A.n, "nnz": A.nnz, "vectors": self.k, "layout": "row-major X, Y",
+                "index": "int32",
+                "l2": f"inputs larger than L2: matrix {A.nnz * 12 / 1e6:.0f} MB, no flush"}
+
+    def setup(self):
+        torch, L = self.torch, self.L
+        self.M = L.CsrMatrix.from_csr(self.A)
+        self.X = torch.rand(self.A.ncols, self.k, dtype=torch.float64, device="cuda")
+        self.Y = torch.empty(self.A.n, self.k, dtype=torch.float64, device="cuda")
+        self.launches_per_step = 1
+
+    def step(self):
+        self.M.spmm(self.X, self.Y, self.k)
+
+    def check(self):
+        torch = self.torch
+        y1 = torch.empty(self.A.n, dtype=torch.float64, device="cuda")
+        x1 = self.X[:, 3].contiguous()
+        self.M.spmv(x1, y1)
+        self.step()
+        torch.cuda.synchronize()
+        d = float((self.Y[:, 3] - y1).abs().max() / y1.abs().max())
+        # the same 8 products through 8 single-vector SpMVs, for the ratio
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xs = [self.X[:, j].contiguous() for j in range(self.k)]
+        e0.record()
+        for _ in range(5):
+            for j in range(self.k):
+                self.M.spmv(xs[j], y1)
+        e1.record()
+        torch.cuda.synchronize()
+        return {"max_rel_diff_vs_spmv_column": d,
+                "k_single_spmv_ms": e0.elapsed_time(e1) / 5}
+
+    def roofline_sample(self, k):
+        torch = self.torch
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(k):
+            self.step()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / k, k, self.nbytes, "spmm_rows_kernel<8> (warp per row)"
+
+    def e2e_setup(self):
+        torch = self.torch
+        self.Xh = self.X.cpu().pin_memory()
+        self.Yh = torch.empty(self.A.n, self.k, dtype=torch.float64).pin_memory()
+        self.e2e_bytes = (self.A.ncols * self.k * 8, self.A.n * self.k * 8)
+
+    def e2e_step(self):
+        self.M.spmm(self.Xh, self.Yh, self.k)
+
+    def cpu_sample(self, budget_s):
+        import oracle
+        A = self.A
+        x = np.random.default_rng(0).random(A.ncols)
+        t0 = time.perf_counter()
+        oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
+        t1 = time.perf_counter() - t0
+        # k oracle SpMVs per SpMM
+        return self.nbytes / (self.k * t1) / 1e9, f"one oracle SpMV timed, x{self.k} for the {self.k} vectors"
+
+    def close(self):
+        self.M.close()
+
+
 class BFS22(Workload):
     """BFS levels on the R-MAT scale-22 graph (transposed adjacency handle), from
     the vertex of largest out-degree; GTEPS = edges of the reached component /
@@ -595,7 +683,7 @@ class BFS22(Workload):
 
 
 WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192": IR192,
-             "bfs22": BFS22}
+             "bfs22": BFS22, "spmm8": SpMM8}
 
 
 # --- served request stream ------------------------------------------------------

@@ -259,6 +259,22 @@ lilac_status lilac_pagerank(lilac_csr AT, void* x, int32_t init_uniform, int32_t
                             double damping, double* l1_per_iter, lilac_mem where, void* stream);
 
 /*
+ * Y = A X for k right-hand sides at once (multi-vector SpMV, 1 <= k <= 32):
+ * every nonzero is streamed once for all k vectors (no counterpart in the
+ * paper, whose spmv_csr takes one vector; it serves batches of SpMV requests).
+ *   X  ncols x k, Y  rows x k, both of the handle's dtype, host or device per
+ *      `where`.  layout LILAC_LAYOUT_ROWS: element (i, j) at [i * k + j] (the
+ *      k values of one row adjacent, the kernel's own layout);
+ *      LILAC_LAYOUT_VECTORS: at [j * n + i] (k separate vectors, as lilac_spmv
+ *      takes them; transposed through device scratch).
+ * Each row's sums use their own summation order (tolerance as lilac_spmv).
+ * Asynchronous for device pointers.  Errors: INVALID_ARG, OOM, CUDA.
+ */
+typedef enum { LILAC_LAYOUT_ROWS = 0, LILAC_LAYOUT_VECTORS = 1 } lilac_layout;
+lilac_status lilac_spmm(lilac_csr A, const void* X, void* Y, int32_t k, int32_t layout,
+                        lilac_mem where, void* stream);
+
+/*
  * The paper's harness calling convention: y = A x on the caller's own host
  * arrays with no handle (spmv_csr, Section 3.1), the marshaling done by the
  * library (Sections 3.3 and 4.2).

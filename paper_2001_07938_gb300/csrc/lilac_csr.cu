@@ -242,7 +242,7 @@ int64_t lilac_csr_s::device_bytes() const {
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
                                   &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out,
                                   &jds_slot_row, &jds_row_slot, &jds_len, &jds_ptr, &jds_col,
-                                  &jds_val, &bfs_row, &bfs_state, &bfs_level};
+                                  &jds_val, &bfs_row, &bfs_state, &bfs_level, &spmm_buf};
     int64_t t = 0;
     for (auto* b : all) t += (int64_t)b->bytes;
     return t;
@@ -473,7 +473,7 @@ static void free_handle(lilac_csr A) {
                             &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
                             &A->cg32.state, &A->cg_outer_state, &A->cg_outer_r, &A->ir_x, &A->ir_b,
                             &A->pr_y, &A->pr_state, &A->pr_l1, &A->pr_has_out, &A->bfs_row,
-                            &A->bfs_state, &A->bfs_level};
+                            &A->bfs_state, &A->bfs_level, &A->spmm_buf};
     for (auto* b : all) b->release();
     jds_release(A);
     delete A;

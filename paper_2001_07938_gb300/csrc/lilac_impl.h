@@ -145,6 +145,8 @@ struct lilac_csr_s {
     bool pr_has_out_valid = false;
     // BFS: row index of every nonzero (built on first use), state, staged levels
     lilac::DevBuf bfs_row, bfs_state, bfs_level;
+    // SpMM: staging / transposition scratch
+    lilac::DevBuf spmm_buf;
     cudaStream_t capture_stream = nullptr;
     std::map<lilac::GraphKey, cudaGraphExec_t> graphs;
     std::vector<cudaEvent_t> prof_events;  // pairs around timed SpMV launches

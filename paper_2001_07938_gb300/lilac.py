@@ -46,8 +46,10 @@ EXPORTS = (
     "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
     "lilac_server_now", "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host",
-    "lilac_host_cache_stats", "lilac_host_cache_clear",
+    "lilac_host_cache_stats", "lilac_host_cache_clear", "lilac_spmm",
 )
+
+LILAC_LAYOUT_ROWS, LILAC_LAYOUT_VECTORS = 0, 1
 
 LILAC_HOST_CACHED, LILAC_HOST_NAIVE = 0, 1
 
@@ -151,6 +153,7 @@ def _lib():
                                         u32, vp]
         lib.lilac_host_cache_stats.argtypes = [c.POINTER(lilac_host_stats_t)]
         lib.lilac_host_cache_clear.argtypes = []
+        lib.lilac_spmm.argtypes = [vp, vp, vp, i32, i32, c.c_int, vp]
         lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
         lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
         lib.lilac_cg_opts_default.restype = None
@@ -190,7 +193,7 @@ def _lib():
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
                      "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
                      "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host", "lilac_host_cache_stats",
-                     "lilac_host_cache_clear"):
+                     "lilac_host_cache_clear", "lilac_spmm"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -308,6 +311,11 @@ def spmv_host(A, x, y, version=0, naive=False):
                     A.vals.ctypes.data, _dtype_code(A.vals.dtype), x.ctypes.data, y.ctypes.data,
                     version, LILAC_HOST_NAIVE if naive else LILAC_HOST_CACHED)
     return y
+
+
+def lilac_spmm(A, X, Y, k, layout, where, stream=None):
+    _check(_lib().lilac_spmm(A, X, Y, k, layout, where,
+                             stream if stream is not None else current_stream()), "lilac_spmm")
 
 
 def lilac_bfs(A, source, level, where, stream=None):
@@ -522,6 +530,15 @@ class CsrMatrix:
 
     def set_variant(self, variant: int, width: int = 0):
         lilac_csr_set_variant(self.handle, variant, width)
+
+    def spmm(self, X, Y, k, layout=LILAC_LAYOUT_ROWS, stream=None):
+        """Y = A X for k vectors (numpy host or torch arrays, flat or 2D)."""
+        px, wx = _ptr_where(X)
+        py, wy = _ptr_where(Y)
+        if wx != wy:
+            raise ValueError("X and Y must both be host or both device")
+        lilac_spmm(self.handle, px, py, int(k), layout, wx, stream)
+        return Y
 
     def bfs(self, source, level, stream=None):
         """Levels from `source` into `level` (int32, host numpy or device torch); returns depth."""
