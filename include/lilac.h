@@ -477,6 +477,21 @@ double lilac_server_now(void);
 /* Clear a sticky device error of the handle and re-zero its scratch memory. */
 lilac_status lilac_csr_reset_error(lilac_csr A);
 
+/*
+ * Test hooks for the failure paths (no counterpart in the paper; for tests of
+ * error handling, which must not fault a shared GPU):
+ *   LILAC_INJECT_ALLOC_FAIL, arg n >= 1: the n-th device allocation from now
+ *       (process-wide; A may be NULL) fails with LILAC_ERR_OOM; arg 0 cancels.
+ *   LILAC_INJECT_SKIP_COPY (arg unused): the next STAGED SpMV launch of A
+ *       leaves the first bulk copy of its first CTA unissued, so that CTA's
+ *       bounded wait expires after about 2 s; the CTA records a device
+ *       timeout and returns, and A reports LILAC_ERR_TIMEOUT from its next
+ *       synchronizing call until lilac_csr_reset_error.  Every wait in the
+ *       kernels is bounded, so nothing hangs or faults.
+ */
+typedef enum { LILAC_INJECT_ALLOC_FAIL = 1, LILAC_INJECT_SKIP_COPY = 2 } lilac_inject;
+lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg);
+
 /* Static text for a status code. */
 const char* lilac_status_string(lilac_status s);
 

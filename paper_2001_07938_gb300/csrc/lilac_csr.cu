@@ -3,6 +3,7 @@
 // the status plumbing.  This is the explicit-handle form of the paper's
 // persistent harness state and marshaling (Section 3.3, Section 4.2).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -17,9 +18,16 @@ static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 
+// Test hook: the n-th device allocation from now fails as out of memory.
+static std::atomic<int64_t> g_fail_alloc_in{0};
+
 lilac_status DevBuf::alloc(size_t n) {
     release();
     if (n == 0) return LILAC_OK;
+    if (g_fail_alloc_in.load() > 0 && g_fail_alloc_in.fetch_sub(1) == 1) {
+        set_last_error("device allocation failed (injected by lilac_debug_inject)");
+        return LILAC_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -610,6 +618,29 @@ lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms,
     }
     A->profiling = enable != 0;
     return LILAC_OK;
+}
+
+lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg) {
+    if (what == LILAC_INJECT_ALLOC_FAIL) {
+        if (arg < 0) {
+            set_last_error("lilac_debug_inject: allocation count must be >= 0");
+            return LILAC_ERR_INVALID_ARG;
+        }
+        g_fail_alloc_in.store(arg);
+        return LILAC_OK;
+    }
+    if (what == LILAC_INJECT_SKIP_COPY) {
+        if (!A) {
+            set_last_error("NULL handle");
+            return LILAC_ERR_INVALID_ARG;
+        }
+        DeviceGuard g(A->device);
+        const int v = DEV_INJECT_SKIP_COPY;
+        LILAC_CUDA_TRY(cudaMemcpy(A->status.as<int>() + 1, &v, sizeof(int), cudaMemcpyHostToDevice));
+        return LILAC_OK;
+    }
+    set_last_error("lilac_debug_inject: unknown hook");
+    return LILAC_ERR_INVALID_ARG;
 }
 
 lilac_status lilac_csr_reset_error(lilac_csr A) {

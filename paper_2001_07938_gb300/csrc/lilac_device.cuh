@@ -11,6 +11,9 @@ namespace lilac {
 
 // Device error word values (written to Scratch::status, read by the host).
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+// Test hook word (Scratch::status[1]): the next STAGED launch leaves the first
+// tile copy of CTA 0 unissued, so its bounded wait expires.
+enum : int { DEV_INJECT_NONE = 0, DEV_INJECT_SKIP_COPY = 2 };
 
 // A bounded wait gives up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
@@ -173,7 +176,7 @@ struct Scratch {
     double* long_red;         // [num_long_rows * kMaxRed] epilogue sums of split rows
     unsigned int* long_cnt;   // [num_long_rows] arrival counters of split rows
     unsigned int* ticket;     // [1] arrival counter of the grid reduction
-    int* status;              // [1] device error word (DEV_*)
+    int* status;              // [2] device error word (DEV_*), test hook word (DEV_INJECT_*)
 };
 
 constexpr int kMaxRed = 2;

@@ -36,9 +36,16 @@ extern "C" lilac_status lilac_spmv(lilac_csr A, const void* x, void* y, lilac_me
         LILAC_TRY(launch_spmv(A, A->val.as<float>(), static_cast<const float*>(xd),
                               OpStore<float, float>{static_cast<float*>(yd)}, s));
     if (where == LILAC_MEM_HOST) {
+        // y and the device error word come back in one synchronization
+        int dev_status = DEV_OK;
         LILAC_CUDA_TRY(cudaMemcpyAsync(y, yd, vsz * (size_t)A->rows, cudaMemcpyDeviceToHost, s));
+        LILAC_CUDA_TRY(cudaMemcpyAsync(&dev_status, A->status.p, sizeof(int), cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
-        if (A->nlong > 0) LILAC_TRY(check_device_status(A, s));
+        if (dev_status != DEV_OK) {
+            A->sticky_error = true;
+            set_last_error("a device-side bounded wait timed out");
+            return LILAC_ERR_TIMEOUT;
+        }
     }
     return LILAC_OK;
 }

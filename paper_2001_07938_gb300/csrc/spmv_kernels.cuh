@@ -212,7 +212,10 @@ __global__ void __launch_bounds__(THREADS)
                      &bar[st], policy);
     };
 
-    if (cnt > 0 && tid == 0) issue(0, 0);
+    // test hook: CTA 0 leaves its first copy unissued (the waits below time out)
+    const bool skip_first = tid == 0 && blockIdx.x == 0 &&
+                            atomicExch(s.status + 1, DEV_INJECT_NONE) == DEV_INJECT_SKIP_COPY;
+    if (cnt > 0 && tid == 0 && !skip_first) issue(0, 0);
     bool failed = false;
     for (int i = 0; i < cnt; ++i) {
         const int st = i & 1;

@@ -46,8 +46,10 @@ EXPORTS = (
     "lilac_server_create", "lilac_server_destroy", "lilac_server_add_matrix",
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
     "lilac_server_now", "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host",
-    "lilac_host_cache_stats", "lilac_host_cache_clear", "lilac_spmm",
+    "lilac_host_cache_stats", "lilac_host_cache_clear", "lilac_spmm", "lilac_debug_inject",
 )
+
+LILAC_INJECT_ALLOC_FAIL, LILAC_INJECT_SKIP_COPY = 1, 2
 
 LILAC_LAYOUT_ROWS, LILAC_LAYOUT_VECTORS = 0, 1
 
@@ -154,6 +156,7 @@ def _lib():
         lib.lilac_host_cache_stats.argtypes = [c.POINTER(lilac_host_stats_t)]
         lib.lilac_host_cache_clear.argtypes = []
         lib.lilac_spmm.argtypes = [vp, vp, vp, i32, i32, c.c_int, vp]
+        lib.lilac_debug_inject.argtypes = [vp, i32, i64]
         lib.lilac_spmv.argtypes = [vp, vp, vp, c.c_int, vp]
         lib.lilac_cg_opts_default.argtypes = [c.POINTER(lilac_cg_opts)]
         lib.lilac_cg_opts_default.restype = None
@@ -193,7 +196,7 @@ def _lib():
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
                      "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
                      "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host", "lilac_host_cache_stats",
-                     "lilac_host_cache_clear", "lilac_spmm"):
+                     "lilac_host_cache_clear", "lilac_spmm", "lilac_debug_inject"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -311,6 +314,10 @@ def spmv_host(A, x, y, version=0, naive=False):
                     A.vals.ctypes.data, _dtype_code(A.vals.dtype), x.ctypes.data, y.ctypes.data,
                     version, LILAC_HOST_NAIVE if naive else LILAC_HOST_CACHED)
     return y
+
+
+def lilac_debug_inject(A, what, arg=0):
+    _check(_lib().lilac_debug_inject(A, what, arg), "lilac_debug_inject")
 
 
 def lilac_spmm(A, X, Y, k, layout, where, stream=None):

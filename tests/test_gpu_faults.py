@@ -1,0 +1,56 @@
+"""Failure paths, exercised without faulting the GPU: an injected allocation
+failure, and a bounded device wait made to expire by a host-set test hook
+(the STAGED kernel's first bulk copy left unissued); the handle reports the
+timeout, stays sticky, and works again after lilac_csr_reset_error."""
+import numpy as np
+import pytest
+
+from paper_2001_07938_gb300 import inputs
+from paper_2001_07938_gb300 import lilac as L
+from lilac_testutil import assert_spmv_close, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def test_injected_allocation_failure_is_oom_and_leaves_no_state():
+    torch_cuda()
+    A = inputs.laplacian2d(32)
+    L.lilac_debug_inject(None, L.LILAC_INJECT_ALLOC_FAIL, 1)
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    assert e.value.status == L.LILAC_ERR_OOM
+    # a later allocation in the middle of create
+    L.lilac_debug_inject(None, L.LILAC_INJECT_ALLOC_FAIL, 3)
+    with pytest.raises(L.LilacError) as e:
+        L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    assert e.value.status == L.LILAC_ERR_OOM
+    L.lilac_debug_inject(None, L.LILAC_INJECT_ALLOC_FAIL, 0)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    x = inputs.uniform(1, A.ncols)
+    y = np.zeros(A.n)
+    M.spmv(x, y)
+    assert_spmv_close(A, x, y, False, "after injected OOM")
+    M.close()
+
+
+def test_bounded_wait_timeout_is_reported_sticky_and_reset():
+    torch_cuda()
+    A = inputs.laplacian2d(200)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_STAGED, 1)
+    x = inputs.uniform(2, A.ncols)
+    y = np.zeros(A.n)
+    M.spmv(x, y)
+    assert_spmv_close(A, x, y, False, "before")
+    L.lilac_debug_inject(M.handle, L.LILAC_INJECT_SKIP_COPY)
+    with pytest.raises(L.LilacError) as e:
+        M.spmv(x, y)  # CTA 0 waits ~2 s for a copy that was never issued
+    assert e.value.status == L.LILAC_ERR_TIMEOUT
+    with pytest.raises(L.LilacError) as e:
+        M.spmv(x, y)  # sticky until reset
+    assert e.value.status == L.LILAC_ERR_TIMEOUT
+    L.lilac_csr_reset_error(M.handle)
+    y[:] = 0.0
+    M.spmv(x, y)
+    assert_spmv_close(A, x, y, False, "after reset")
+    M.close()
