@@ -200,14 +200,61 @@ struct FinCgUpdate {
     }
 };
 
+// 16-byte vector of T: the CG vector kernels move four FP32 or two FP64
+// elements per access when every array is 16-byte aligned.
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int N = 4;
+    __device__ static float get(const float4& v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
+    __device__ static void set(float4& v, int i, float a) {
+        if (i == 0) v.x = a; else if (i == 1) v.y = a; else if (i == 2) v.z = a; else v.w = a;
+    }
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int N = 2;
+    __device__ static double get(const double2& v, int i) { return i == 0 ? v.x : v.y; }
+    __device__ static void set(double2& v, int i, double a) {
+        if (i == 0) v.x = a; else v.y = a;
+    }
+};
+
+__device__ __forceinline__ bool aligned16(const void* a, const void* b, const void* c = nullptr,
+                                          const void* d = nullptr) {
+    return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) |
+             reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
+}
+
 template <class T, class Fin>
 static __global__ void __launch_bounds__(kVecThreads)
     cg_update_kernel(int n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
                      const T* __restrict__ q, Fin fin, Scratch s) {
     if (cg_done(fin.st)) return;
+    using VT = Vec16<T>;
+    using V = typename VT::type;
+    constexpr int N = VT::N;
     const T alpha = T(fin.st->alpha);
     double red[1] = {0.0};
-    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
+    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
+    const int nv = aligned16(x, r, p, q) ? n / N : 0;
+    for (int i = g0; i < nv; i += gs) {
+        V xv = reinterpret_cast<const V*>(x)[i], rv = reinterpret_cast<const V*>(r)[i];
+        const V pv = reinterpret_cast<const V*>(p)[i], qv = reinterpret_cast<const V*>(q)[i];
+#pragma unroll
+        for (int e = 0; e < N; ++e) {
+            VT::set(xv, e, VT::get(xv, e) + alpha * VT::get(pv, e));
+            const T ri = VT::get(rv, e) - alpha * VT::get(qv, e);
+            VT::set(rv, e, ri);
+            red[0] += double(ri) * double(ri);
+        }
+        reinterpret_cast<V*>(x)[i] = xv;
+        reinterpret_cast<V*>(r)[i] = rv;
+    }
+    for (int i = nv * N + g0; i < n; i += gs) {
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * q[i];
         r[i] = ri;
@@ -221,9 +268,20 @@ template <class T>
 static __global__ void __launch_bounds__(kVecThreads)
     cg_direction_kernel(int n, const T* __restrict__ r, T* __restrict__ p, const CgState* st) {
     if (cg_done(st)) return;
+    using VT = Vec16<T>;
+    using V = typename VT::type;
+    constexpr int N = VT::N;
     const T beta = T(st->beta);
-    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
-        p[i] = r[i] + beta * p[i];
+    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
+    const int nv = aligned16(r, p) ? n / N : 0;
+    for (int i = g0; i < nv; i += gs) {
+        const V rv = reinterpret_cast<const V*>(r)[i];
+        V pv = reinterpret_cast<const V*>(p)[i];
+#pragma unroll
+        for (int e = 0; e < N; ++e) VT::set(pv, e, VT::get(rv, e) + beta * VT::get(pv, e));
+        reinterpret_cast<V*>(p)[i] = pv;
+    }
+    for (int i = nv * N + g0; i < n; i += gs) p[i] = r[i] + beta * p[i];
 }
 
 // ---------------------------------------------------------------------------

@@ -217,6 +217,10 @@ __global__ void __launch_bounds__(THREADS)
                             atomicExch(s.status + 1, DEV_INJECT_NONE) == DEV_INJECT_SKIP_COPY;
     if (cnt > 0 && tid == 0 && !skip_first) issue(0, 0);
     bool failed = false;
+    // epilogues with reductions: rows are stored in phase B and reduced one
+    // row per thread in the next tile, after its gathers are issued
+    constexpr bool kDeferred = Op::kTwoPhase && NR > 0;
+    int prev_r0 = 0, prev_n = 0;
     for (int i = 0; i < cnt; ++i) {
         const int st = i & 1;
         if (i + 1 < cnt && tid == 0) {
@@ -254,6 +258,10 @@ __global__ void __launch_bounds__(THREADS)
             const int k = kb0 + j * THREADS + tid;
             xj[j] = k < ke0 ? __ldg(x + cj[j]) : typename Op::VecT(0);
         }
+        if constexpr (kDeferred) {
+            for (int q = tid; q < prev_n; q += THREADS) op.reduce(prev_r0 + q, red);
+            prev_n = 0;
+        }
         if (t.r1 >= 0) {
 #pragma unroll
             for (int j = 0; j < IPT; ++j) {
@@ -270,7 +278,16 @@ __global__ void __launch_bounds__(THREADS)
                 AccT sum = AccT(0);
                 for (int k = kb + lane; k < ke; k += V) sum += prod[k];
                 if constexpr (V > 1) sum = group_sum<V>(sum, mask);
-                if (lane == 0) op.row(t.r0 + rr, sum, red);
+                if (lane == 0) {
+                    if constexpr (kDeferred)
+                        op.store(t.r0 + rr, sum);
+                    else
+                        op.row(t.r0 + rr, sum, red);
+                }
+            }
+            if constexpr (kDeferred) {
+                prev_r0 = t.r0;
+                prev_n = nrows;
             }
         } else {
             // chunk of a split row: the whole block sums it
@@ -308,6 +325,9 @@ __global__ void __launch_bounds__(THREADS)
     if (failed) {
         if (tid == 0) atomicExch(s.status, DEV_TIMEOUT);
         return;
+    }
+    if constexpr (kDeferred) {
+        for (int q = tid; q < prev_n; q += THREADS) op.reduce(prev_r0 + q, red);
     }
     (void)sh_ok;
     if constexpr (NR > 0) {
