@@ -692,7 +692,8 @@ def served_stream(n_req=2000, n_mats=32, n_lo=1e3, n_hi=2e5, kmax=8, seed=0):
     """Seeded request stream: a pool of 2D/3D Laplacians and banded SPD matrices
     (half-bandwidth 8..64) with n log-uniform in [n_lo, n_hi]; requests pick a
     matrix with Zipf(1.1) popularity; half are SpMV batches of k in [1, kmax]
-    vectors, half CG solves to 1e-10 (b uniform in [-1, 1])."""
+    vectors, half CG solves to 1e-10 (b uniform in [-1, 1]), of which half ask
+    for FP32 values with FP64 refinement (precision 2)."""
     from paper_2001_07938_gb300 import inputs
     rng = np.random.default_rng(seed)
     pool = []
@@ -713,9 +714,10 @@ def served_stream(n_req=2000, n_mats=32, n_lo=1e3, n_hi=2e5, kmax=8, seed=0):
         A = pool[mi]
         if rng.random() < 0.5:
             k = int(rng.integers(1, kmax + 1))
-            reqs.append(("spmv", mi, inputs.uniform(10_000 + t, k * A.ncols), k))
+            reqs.append(("spmv", mi, inputs.uniform(10_000 + t, k * A.ncols), k, 0))
         else:
-            reqs.append(("cg", mi, inputs.uniform(20_000 + t, A.n), 1))
+            prec = 2 if rng.random() < 0.5 else 0
+            reqs.append(("cg", mi, inputs.uniform(20_000 + t, A.n), 1, prec))
     return pool, reqs
 
 
@@ -784,12 +786,13 @@ def run_served(args):
     pool, reqs = served_stream(n_req=args.served_requests)
     N = len(reqs)
     n_cg = sum(1 for r in reqs if r[0] == "cg")
+    n_mixed = sum(1 for r in reqs if r[0] == "cg" and r[4] == 2)
     # plain: one request at a time through lilac_spmv / lilac_cg (FP64), matrices resident
     Ms = [L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE) for A in pool]
     outs_plain = []
 
     def plain_one(r):
-        kind, mi, inp, k = r
+        kind, mi, inp, k, _ = r  # plain: every solve in FP64
         A, M = pool[mi], Ms[mi]
         if kind == "spmv":
             out = np.empty(k * A.n)
@@ -831,14 +834,15 @@ def run_served(args):
         while got < N:
             now = L.Server.now() - t0
             while i < N and (timed_arrivals is None or timed_arrivals[i] <= now):
-                kind, mi, inp, k = reqs[i]
+                kind, mi, inp, k, prec = reqs[i]
                 A = pool[mi]
                 out = np.empty(k * A.n) if kind == "spmv" else np.zeros(A.n)
                 outs[i] = out
                 if kind == "spmv":
                     S.submit(L.LILAC_REQ_SPMV, ids[mi], inp, out, i, nvec=k)
                 else:
-                    S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, i, max_iter=20000, rtol=1e-10)
+                    S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, i, max_iter=20000, rtol=1e-10,
+                             precision=prec)
                 i += 1
             pending = S.step()
             for c in S.poll():
@@ -865,6 +869,8 @@ def run_served(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "served_stream", "requests": N, "cg_requests": n_cg,
+                       "cg_mixed_precision_requests": n_mixed,
+                       "plain": "one request at a time, lilac_spmv / FP64 lilac_cg",
                        "matrices": len(pool), "n_range": [1e3, 2e5], "zipf": 1.1,
                        "spmv_vectors": "1..8", "rtol": 1e-10,
                        "arrivals": f"Poisson at {args.served_load} x plain capacity",

@@ -392,14 +392,18 @@ lilac_status lilac_batch_destroy(lilac_batch B); /* NULL is a no-op */
 lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
                               const double* const* x, double* const* y, void* stream);
 
-/* FP64 CG on count systems A[i] x[i] = b[i] at once (x0 = 0), each stopping
- * at ||r|| <= rtol ||b|| (rtol <= 0: exactly max_iter iterations); iterations
+/* CG on count systems A[i] x[i] = b[i] at once (x0 = 0), each stopping at
+ * ||r|| <= rtol ||b|| (rtol <= 0: exactly max_iter iterations); iterations
  * of all systems run together in captured rounds of 16, with one host check
- * per round.  infos (nullable) receives per-system iterations, status and
- * recursive relative residual.  Returns OK or the first non-OK status. */
+ * per round.  precision 0: FP64; 2: FP32 values and vectors with FP64
+ * reliable updates (as lilac_cg precision 2, residual replaced when it fell
+ * by 0.1; FP32 values derived once per handle).  infos (nullable) receives
+ * per-system iterations, status, residual replacements and relative residual
+ * (recursive for FP64, the last FP64 b - A x for precision 2).  Returns OK or
+ * the first non-OK status. */
 lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
                             const double* const* b, double* const* x, int32_t max_iter,
-                            double rtol, lilac_cg_info* infos, void* stream);
+                            double rtol, int32_t precision, lilac_cg_info* infos, void* stream);
 
 /*
  * Request server: continuous batching of SpMV and FP64 CG requests over a
@@ -435,6 +439,9 @@ typedef struct {
     const double* in;  /* host: SpMV x, nvec x ncols (vector-major); CG b, rows */
     double* out;       /* host: SpMV y, nvec x rows; CG x, rows; written before completion */
     int64_t tag;       /* caller's id, returned in the completion */
+    int32_t precision; /* CG: 0 FP64; 2 FP32 values and vectors with FP64 reliable
+                          updates (as lilac_cg precision 2; FP32 values derived once) */
+    int32_t pad;
 } lilac_request;
 
 typedef struct {

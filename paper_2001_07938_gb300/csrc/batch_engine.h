@@ -12,10 +12,13 @@ namespace lilac {
 
 // Bytes of workspace one problem needs (state, counters, per-item partials,
 // split-row scratch, and r, p, q for CG).
-size_t batch_workspace_bytes(const lilac_csr_s* A, int kind);
+size_t batch_workspace_bytes(const lilac_csr_s* A, int kind, int prec);
 
+// prec: BP_F64 or BP_F32_RU (then the handle's FP32 values must exist:
+// make_val32); delta: the reliable-update threshold of BP_F32_RU.
 BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* y_out,
-                          const double* b, double* x, double rtol, int max_iter, void* ws);
+                          const double* b, double* x, double rtol, int max_iter, void* ws,
+                          int prec, double delta);
 
 struct BatchEngine {
     int device = 0;
@@ -25,6 +28,7 @@ struct BatchEngine {
     std::vector<BatchProb> host_probs;
     std::vector<BatchItem> host_items_spmv, host_items_vec;
     int host_counts[4] = {0, 0, 0, 0};
+    bool mixed = false;  // an active CG problem runs in BP_F32_RU
     cudaStream_t capture_stream = nullptr;
     std::map<uint64_t, cudaGraphExec_t> graphs;
 

@@ -1,12 +1,18 @@
 // Batched kernels: many CSR problems of uneven size in one persistent launch.
 //
-// The work list holds (problem, tile) items for the SpMV phase and
+// The work list holds (problem, tile) items for the SpMV phases and
 // (problem, chunk) items for the vector phases of CG; persistent CTAs take
 // items blockIdx.x, blockIdx.x + grid, ...  Every reduction of a problem is
-// kept per item (one partial sum per tile or chunk) and added, in item order,
+// kept per item (partial sums per tile or chunk) and added, in item order,
 // by the CTA that completes the problem's last item (arrival counter), so a
 // problem's result depends only on its own tiling -- the same alone and in
-// any mix.  FP64 values and vectors.
+// any mix.
+//
+// CG problems run in one of two precisions: FP64 (values, vectors and sums),
+// or FP32 CG with FP64 reliable updates (FP32 values, vectors and row sums,
+// FP64 dot products, solution accumulated in FP64 and the residual replaced
+// by the FP64 b - A x whenever the FP32 residual fell by delta; the same
+// method as lilac_cg precision 2).
 #pragma once
 
 #include "ops.cuh"
@@ -14,6 +20,7 @@
 namespace lilac {
 
 enum BatchKind : int { BK_SPMV = 0, BK_CG = 1 };
+enum BatchPrec : int { BP_F64 = 0, BP_F32_RU = 2 };
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchItems = 2048;   // nonzeros per tile: matches the STAGED tile list
@@ -25,6 +32,7 @@ struct BatchProb {
     const int* row_ptr;
     const int* col_ind;
     const double* val;
+    const float* val32;  // FP32 values (BP_F32_RU)
     const TileDesc* tiles;
     const LongRow* longs;
     double* long_part;
@@ -35,22 +43,27 @@ struct BatchProb {
     int nlong;
     int kind;
     int nchunks;
-    int pad;
+    int prec;
     // SpMV: y = A x
     const double* x_in;
     double* y_out;
-    // CG state and vectors
+    // CG: b, x (FP64); r, p, q (FP64) or r32, p32, q32 and the FP32 correction d32
     const double* b;
     double* x;
     double* r;
     double* p;
     double* q;
+    float* r32;
+    float* p32;
+    float* q32;
+    float* d32;
     CgState* st;
     double rtol;
+    double delta2;  // BP_F32_RU: replace when r.r <= delta2 * r.r at the last replacement
     int max_iter;
-    int pad2;
-    // per-item partial sums ([0, ntiles): SpMV phase; then nchunks) and the
-    // arrival counters of the two reduction phases
+    int pad;
+    // per-item partial sums: [0, 2 ntiles) SpMV phases (two per tile), then
+    // one per vector chunk; arrival counters of the SpMV and vector phases
     double* part;
     unsigned* cnt;
 };
@@ -60,117 +73,194 @@ struct BatchItem {
     int idx;
 };
 
-// Item-order sum of a problem's partials (+ split-row sums), by one thread.
-__device__ __forceinline__ double batch_sum_parts(const double* part, int n, const double* extra,
-                                                  int nextra) {
+// Item-order sum of a problem's partials (stride apart) + split-row sums.
+__device__ __forceinline__ double batch_sum_parts(const double* part, int n, int stride,
+                                                  const double* extra, int nextra) {
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += __ldcg(part + i);
+    for (int i = 0; i < n; ++i) s += __ldcg(part + (size_t)i * stride);
     for (int i = 0; i < nextra; ++i) s += __ldcg(extra + (size_t)i * kMaxRed);
     return s;
 }
 
-// SpMV phase: y = A x (BK_SPMV) or q = A p with p.q -> alpha (BK_CG).
-static __global__ void __launch_bounds__(kBatchThreads)
-    batch_spmv_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
-                      const int* __restrict__ nitems_dev) {
+__device__ __forceinline__ bool batch_ru_due(const CgState* st) {
+    return *reinterpret_cast<const volatile int*>(&st->update) != 0 && !cg_done(st);
+}
+
+// Epilogues of the batched SpMV phases (row r's sum s; up to two FP64 sums).
+struct BEpiStore {  // y = A x
+    double* y;
+    __device__ void row(int r, double s, double*) const { y[r] = s; }
+};
+template <class T>
+struct BEpiPq {  // q = A p, p.q
+    T* q;
+    const T* p;
+    __device__ void row(int r, T s, double* red) const {
+        q[r] = s;
+        red[0] += double(p[r]) * double(s);
+    }
+};
+struct BEpiResid {  // r32 = float(b - A x), ||b - A x||^2, float(r).float(r)
+    float* r32;
+    const double* b;
+    __device__ void row(int r, double s, double* red) const {
+        const double ri = b[r] - s;
+        const float rf = float(ri);
+        r32[r] = rf;
+        red[0] += ri * ri;
+        red[1] += double(rf) * double(rf);
+    }
+};
+
+// One tile of one problem: products to shared memory, rows by groups of V
+// lanes; a chunk of a split row is summed by the block and finished by the
+// chunk that arrives last.  Returns the tile's FP64 sums in red[0..1].
+template <class ValT, class VecT, class AccT, class Epi>
+__device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t,
+                                           const ValT* __restrict__ val,
+                                           const VecT* __restrict__ xin, const Epi& epi,
+                                           double* red, unsigned char* smem, int* rp_s,
+                                           AccT* sh) {
     constexpr int THREADS = kBatchThreads;
     constexpr int IPT = kBatchItems / THREADS;
     constexpr int V = 4;
     constexpr int NGROUPS = THREADS / V;
-    __shared__ double prod[kBatchItems];
-    __shared__ int rp_s[kBatchRows + 2];
-    __shared__ double sh[32];
-    __shared__ double shr[kMaxRed * 32];
+    AccT* prod = reinterpret_cast<AccT*>(smem);
     const int tid = threadIdx.x;
     const int lane = tid & (V - 1), group = tid / V;
     const unsigned mask = group_mask<V>(tid);
+    int cj[IPT];
+    ValT vj[IPT];
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int k = t.k0 + j * THREADS + tid;
+        cj[j] = k < t.k1 ? ld_stream(P.col_ind + k) : 0;
+        vj[j] = k < t.k1 ? ld_stream(val + k) : ValT(0);
+    }
+#pragma unroll
+    for (int j = 0; j < IPT; ++j) {
+        const int k = t.k0 + j * THREADS + tid;
+        if (k < t.k1) prod[j * THREADS + tid] = AccT(vj[j]) * AccT(__ldg(xin + cj[j]));
+    }
+    if (t.r1 >= 0) {
+        const int nrows = t.r1 - t.r0;
+        for (int q = tid; q <= nrows; q += THREADS) rp_s[q] = __ldg(P.row_ptr + t.r0 + q);
+        __syncthreads();
+        for (int rr = group; rr < nrows; rr += NGROUPS) {
+            const int kb = rp_s[rr] - t.k0, ke = rp_s[rr + 1] - t.k0;
+            AccT sum = AccT(0);
+            for (int k = kb + lane; k < ke; k += V) sum += prod[k];
+            sum = group_sum<V>(sum, mask);
+            if (lane == 0) epi.row(t.r0 + rr, sum, red);
+        }
+    } else {
+        __syncthreads();
+        AccT sum = AccT(0);
+        for (int k = tid; k < t.k1 - t.k0; k += THREADS) sum += prod[k];
+        sum = block_sum_all<THREADS, AccT>(sum, sh);
+        if (tid == 0) {
+            const int lid = t.r0, slot = -t.r1 - 1;
+            P.long_part[slot] = double(sum);
+            __threadfence();
+            const LongRow lr = P.longs[lid];
+            if (atomicAdd(&P.long_cnt[lid], 1u) == (unsigned)lr.nchunks - 1u) {
+                __threadfence();
+                AccT rs = AccT(0);
+                for (int j = 0; j < lr.nchunks; ++j) rs += AccT(__ldcg(&P.long_part[lr.first_slot + j]));
+                double lred[2] = {0.0, 0.0};
+                epi.row(lr.row, rs, lred);
+                P.long_red[lid * kMaxRed] = lred[0];
+                P.long_red[lid * kMaxRed + 1] = lred[1];
+                P.long_cnt[lid] = 0u;
+            }
+        }
+    }
+}
+
+// Problem-level ends of the SpMV phases (last tile of the problem, thread 0).
+__device__ __forceinline__ void batch_finish_pq(const BatchProb& P) {
+    const double pq = batch_sum_parts(P.part, P.ntiles, 2, P.long_red, P.nlong);
+    CgState* st = P.st;
+    st->pq = pq;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+        st->status = LILAC_ERR_BREAKDOWN;
+        st->done = 1;
+    } else {
+        st->alpha = st->rr / pq;
+    }
+}
+
+__device__ __forceinline__ void batch_finish_resid(const BatchProb& P) {
+    const double rr_true = batch_sum_parts(P.part, P.ntiles, 2, P.long_red, P.nlong);
+    const double rr32 = batch_sum_parts(P.part + 1, P.ntiles, 2, P.long_red + 1, P.nlong);
+    CgState* st = P.st;
+    st->true_rr = rr_true;
+    st->updates += 1;
+    st->update = 0;
+    if (rr_true == 0.0 || (st->tol2 >= 0.0 && rr_true <= st->tol2)) {
+        st->done = 1;
+        st->status = LILAC_OK;
+    } else if (st->iters >= st->max_iter) {
+        st->done = 1;
+        st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+    } else {
+        st->beta = rr32 / st->rr;  // r.r before this iteration
+        st->rr = rr32;
+        st->rr_anchor = rr32;
+    }
+}
+
+// SpMV phases.  MODE 0: y = A x (BK_SPMV) or q = A p with p.q -> alpha (BK_CG,
+// in the problem's precision).  MODE 1: the FP64 residual of BP_F32_RU
+// problems whose replacement is due (other items return at once).
+template <int MODE>
+static __global__ void __launch_bounds__(kBatchThreads)
+    batch_spmv_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
+                      const int* __restrict__ nitems_dev) {
+    constexpr int THREADS = kBatchThreads;
+    __shared__ __align__(16) unsigned char smem[kBatchItems * sizeof(double)];
+    __shared__ int rp_s[kBatchRows + 2];
+    __shared__ double sh[32];
+    __shared__ float shf[32];
+    __shared__ double shr[kMaxRed * 32];
+    const int tid = threadIdx.x;
     const int nitems = *nitems_dev;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const BatchItem item = items[it];
         const BatchProb& P = probs[item.prob];
         const int kind = P.kind;
-        if (kind == BK_CG && cg_done(P.st)) continue;  // uniform over the block
+        // uniform over the block: flags change only in earlier launches
+        if (MODE == 0 && kind == BK_CG && cg_done(P.st)) continue;
+        if (MODE == 1 && !(kind == BK_CG && P.prec == BP_F32_RU && batch_ru_due(P.st))) continue;
         const TileDesc t = P.tiles[item.idx];
-        const double* __restrict__ xin = kind == BK_CG ? P.p : P.x_in;
-        double red = 0.0;
-        // phase A: products of the tile's nonzeros
-        int cj[IPT];
-        double vj[IPT];
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int k = t.k0 + j * THREADS + tid;
-            cj[j] = k < t.k1 ? ld_stream(P.col_ind + k) : 0;
-            vj[j] = k < t.k1 ? ld_stream(P.val + k) : 0.0;
-        }
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int k = t.k0 + j * THREADS + tid;
-            if (k < t.k1) prod[j * THREADS + tid] = vj[j] * __ldg(xin + cj[j]);
-        }
-        if (t.r1 >= 0) {
-            const int nrows = t.r1 - t.r0;
-            for (int q = tid; q <= nrows; q += THREADS) rp_s[q] = __ldg(P.row_ptr + t.r0 + q);
-            __syncthreads();
-            // phase B: rows of the tile
-            for (int rr = group; rr < nrows; rr += NGROUPS) {
-                const int kb = rp_s[rr] - t.k0, ke = rp_s[rr + 1] - t.k0;
-                double sum = 0.0;
-                for (int k = kb + lane; k < ke; k += V) sum += prod[k];
-                sum = group_sum<V>(sum, mask);
-                if (lane == 0) {
-                    const int r = t.r0 + rr;
-                    if (kind == BK_CG) {
-                        P.q[r] = sum;
-                        red += P.p[r] * sum;
-                    } else {
-                        P.y_out[r] = sum;
-                    }
-                }
-            }
+        double red[2] = {0.0, 0.0};
+        if (MODE == 1) {
+            batch_tile<double, double, double>(P, t, P.val, P.x, BEpiResid{P.r32, P.b}, red, smem,
+                                               rp_s, sh);
+        } else if (kind == BK_SPMV) {
+            batch_tile<double, double, double>(P, t, P.val, P.x_in, BEpiStore{P.y_out}, red, smem,
+                                               rp_s, sh);
+        } else if (P.prec == BP_F32_RU) {
+            batch_tile<float, float, float>(P, t, P.val32, P.p32, BEpiPq<float>{P.q32, P.p32}, red,
+                                            smem, rp_s, shf);
         } else {
-            // chunk of a split row
-            __syncthreads();
-            double sum = 0.0;
-            for (int k = tid; k < t.k1 - t.k0; k += THREADS) sum += prod[k];
-            sum = block_sum_all<THREADS, double>(sum, sh);
-            if (tid == 0) {
-                const int lid = t.r0, slot = -t.r1 - 1;
-                P.long_part[slot] = sum;
-                __threadfence();
-                const LongRow lr = P.longs[lid];
-                if (atomicAdd(&P.long_cnt[lid], 1u) == (unsigned)lr.nchunks - 1u) {
-                    __threadfence();
-                    double rs = 0.0;
-                    for (int j = 0; j < lr.nchunks; ++j) rs += __ldcg(&P.long_part[lr.first_slot + j]);
-                    double lred = 0.0;
-                    if (kind == BK_CG) {
-                        P.q[lr.row] = rs;
-                        lred = P.p[lr.row] * rs;
-                    } else {
-                        P.y_out[lr.row] = rs;
-                    }
-                    P.long_red[lid * kMaxRed] = lred;
-                    P.long_cnt[lid] = 0u;
-                }
-            }
+            batch_tile<double, double, double>(P, t, P.val, P.p, BEpiPq<double>{P.q, P.p}, red,
+                                               smem, rp_s, sh);
         }
         if (kind == BK_CG) {
-            // this tile's share of p.q; the problem's last tile finishes alpha
-            double r1[1] = {red}, tot[1];
-            block_sum<1, THREADS>(r1, tot, shr);
+            // this tile's share of the sums; the problem's last tile finishes
+            double tot[2];
+            block_sum<2, THREADS>(red, tot, shr);
             if (tid == 0) {
-                P.part[item.idx] = tot[0];
+                P.part[2 * item.idx] = tot[0];
+                P.part[2 * item.idx + 1] = tot[1];
                 __threadfence();
                 if (atomicAdd(&P.cnt[0], 1u) == (unsigned)P.ntiles - 1u) {
                     __threadfence();
-                    const double pq = batch_sum_parts(P.part, P.ntiles, P.long_red, P.nlong);
-                    P.st->pq = pq;
-                    if (!(pq > 0.0) || !isfinite(pq)) {
-                        P.st->status = LILAC_ERR_BREAKDOWN;
-                        P.st->done = 1;
-                    } else {
-                        P.st->alpha = P.st->rr / pq;
-                    }
+                    if (MODE == 0)
+                        batch_finish_pq(P);
+                    else
+                        batch_finish_resid(P);
                     P.cnt[0] = 0u;
                 }
             }
@@ -180,9 +270,11 @@ static __global__ void __launch_bounds__(kBatchThreads)
 }
 
 // Vector phases of CG over (problem, chunk) items.
-//   PHASE 0: start   x = 0, r = p = b, rr = b.b
-//   PHASE 1: update  x += alpha p, r -= alpha q, rr' = r.r -> beta, convergence
-//   PHASE 2: direction p = r + beta p
+//   PHASE 0: start      x = 0, r = p = b (d = 0), r.r
+//   PHASE 1: update     x (or d) += alpha p, r -= alpha q, r.r -> beta, convergence
+//                       (BP_F32_RU: or flag a residual replacement)
+//   PHASE 2: direction  p = r + beta p
+//   PHASE 3: BP_F32_RU problems with a replacement due: x += d (FP64), d = 0
 template <int PHASE>
 static __global__ void __launch_bounds__(kBatchThreads)
     batch_vec_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
@@ -195,7 +287,9 @@ static __global__ void __launch_bounds__(kBatchThreads)
         const BatchItem item = items[it];
         const BatchProb& P = probs[item.prob];
         CgState* st = P.st;
+        const bool ru = P.prec == BP_F32_RU;
         if (PHASE != 0 && cg_done(st)) continue;  // uniform over the block
+        if (PHASE == 3 && !(ru && batch_ru_due(st))) continue;
         const int i0 = item.idx * kBatchChunk;
         const int i1 = min(P.rows, i0 + kBatchChunk);
         double red = 0.0;
@@ -203,31 +297,61 @@ static __global__ void __launch_bounds__(kBatchThreads)
             for (int i = i0 + tid; i < i1; i += THREADS) {
                 const double bi = P.b[i];
                 P.x[i] = 0.0;
-                P.r[i] = bi;
-                P.p[i] = bi;
-                red += bi * bi;
+                if (ru) {
+                    const float bf = float(bi);
+                    P.r32[i] = bf;
+                    P.p32[i] = bf;
+                    P.d32[i] = 0.0f;
+                    red += double(bf) * double(bf);
+                } else {
+                    P.r[i] = bi;
+                    P.p[i] = bi;
+                    red += bi * bi;
+                }
             }
         } else if (PHASE == 1) {
-            const double alpha = st->alpha;
-            for (int i = i0 + tid; i < i1; i += THREADS) {
-                P.x[i] += alpha * P.p[i];
-                const double ri = P.r[i] - alpha * P.q[i];
-                P.r[i] = ri;
-                red += ri * ri;
+            if (ru) {
+                const float alpha = float(st->alpha);
+                for (int i = i0 + tid; i < i1; i += THREADS) {
+                    P.d32[i] += alpha * P.p32[i];
+                    const float ri = P.r32[i] - alpha * P.q32[i];
+                    P.r32[i] = ri;
+                    red += double(ri) * double(ri);
+                }
+            } else {
+                const double alpha = st->alpha;
+                for (int i = i0 + tid; i < i1; i += THREADS) {
+                    P.x[i] += alpha * P.p[i];
+                    const double ri = P.r[i] - alpha * P.q[i];
+                    P.r[i] = ri;
+                    red += ri * ri;
+                }
             }
+        } else if (PHASE == 2) {
+            if (ru) {
+                const float beta = float(st->beta);
+                for (int i = i0 + tid; i < i1; i += THREADS) P.p32[i] = P.r32[i] + beta * P.p32[i];
+            } else {
+                const double beta = st->beta;
+                for (int i = i0 + tid; i < i1; i += THREADS) P.p[i] = P.r[i] + beta * P.p[i];
+            }
+            continue;  // no reduction
         } else {
-            const double beta = st->beta;
-            for (int i = i0 + tid; i < i1; i += THREADS) P.p[i] = P.r[i] + beta * P.p[i];
+            for (int i = i0 + tid; i < i1; i += THREADS) {
+                P.x[i] += double(P.d32[i]);
+                P.d32[i] = 0.0f;
+            }
             continue;  // no reduction
         }
         double r1[1] = {red}, tot[1];
         block_sum<1, THREADS>(r1, tot, shr);
         if (tid == 0) {
-            P.part[P.ntiles + item.idx] = tot[0];
+            double* vpart = P.part + 2 * (size_t)P.ntiles;
+            vpart[item.idx] = tot[0];
             __threadfence();
             if (atomicAdd(&P.cnt[1], 1u) == (unsigned)P.nchunks - 1u) {
                 __threadfence();
-                const double s = batch_sum_parts(P.part + P.ntiles, P.nchunks, nullptr, 0);
+                const double s = batch_sum_parts(vpart, P.nchunks, 1, nullptr, 0);
                 if (PHASE == 0) {
                     st->rr = s;
                     st->bb = s;
@@ -236,17 +360,32 @@ static __global__ void __launch_bounds__(kBatchThreads)
                     st->max_iter = P.max_iter;
                     st->done = s == 0.0 ? 1 : 0;
                     st->status = s == 0.0 ? LILAC_OK : LILAC_ERR_NOT_CONVERGED;
+                    st->rr_anchor = s;
+                    st->delta2 = P.delta2;
+                    st->update = 0;
+                    st->updates = 0;
+                    st->true_rr = -1.0;
                 } else {
                     const int iters = st->iters + 1;
                     st->iters = iters;
-                    st->beta = s / st->rr;
-                    st->rr = s;
-                    if (s == 0.0 || (st->tol2 >= 0.0 && s <= st->tol2)) {
-                        st->done = 1;
-                        st->status = LILAC_OK;
-                    } else if (iters >= st->max_iter) {
-                        st->done = 1;
-                        st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+                    if (ru) {
+                        if (s <= st->delta2 * st->rr_anchor || s == 0.0 ||
+                            (st->tol2 >= 0.0 && s <= st->tol2) || iters >= st->max_iter) {
+                            st->update = 1;  // st->rr keeps the previous r.r for beta
+                        } else {
+                            st->beta = s / st->rr;
+                            st->rr = s;
+                        }
+                    } else {
+                        st->beta = s / st->rr;
+                        st->rr = s;
+                        if (s == 0.0 || (st->tol2 >= 0.0 && s <= st->tol2)) {
+                            st->done = 1;
+                            st->status = LILAC_OK;
+                        } else if (iters >= st->max_iter) {
+                            st->done = 1;
+                            st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+                        }
                     }
                 }
                 P.cnt[1] = 0u;

@@ -1,11 +1,13 @@
-// Batched execution of many CSR problems (SpMV and FP64 CG) in persistent
-// launches: the engine behind lilac_batch_* and the request server.
+// Batched execution of many CSR problems (SpMV, and CG in FP64 or in FP32
+// with FP64 reliable updates) in persistent launches: the engine behind
+// lilac_batch_* and the request server.
 //
 // A round of CG is three batched launches (SpMV + p.q; update + r.r;
-// direction) over all active problems; R rounds are captured once as a CUDA
-// graph whose kernels read the problem table and work lists from device
-// buffers, so the set of problems can change between replays without a new
-// capture.
+// direction) over all active problems, five when a mixed-precision problem
+// is active (x += d and the FP64 residual, for the problems whose residual
+// replacement is due); R rounds are captured once as a CUDA graph whose
+// kernels read the problem table and work lists from device buffers, so the
+// set of problems can change between replays without a new capture.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -18,23 +20,24 @@ namespace lilac {
 static_assert(kBatchItems == kTileNnz && kBatchRows == kTileRows,
               "batched tiles are the handles' STAGED tiles");
 
-size_t batch_workspace_bytes(const lilac_csr_s* A, int kind) {
+size_t batch_workspace_bytes(const lilac_csr_s* A, int kind, int prec) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n = (size_t)std::max(1, A->rows);
     const size_t nchunks = (n + kBatchChunk - 1) / kBatchChunk;
     size_t bytes = al(sizeof(CgState)) + al(4 * sizeof(unsigned));
-    bytes += al(sizeof(double) * ((size_t)A->ntiles + nchunks + 1));
+    bytes += al(sizeof(double) * (2 * (size_t)A->ntiles + nchunks + 1));
     bytes += al(sizeof(double) * (size_t)std::max(1, A->nlong_chunks));
     bytes += al(sizeof(double) * kMaxRed * (size_t)std::max(1, A->nlong));
     bytes += al(sizeof(unsigned) * (size_t)std::max(1, A->nlong));
-    if (kind == BK_CG) bytes += 3 * al(sizeof(double) * n);
+    if (kind == BK_CG) bytes += prec == BP_F32_RU ? 4 * al(sizeof(float) * n) : 3 * al(sizeof(double) * n);
     return bytes;
 }
 
 // Fill a problem descriptor from a handle and a workspace block (which must
 // hold batch_workspace_bytes and have been zeroed).
 BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* y_out,
-                          const double* b, double* x, double rtol, int max_iter, void* ws) {
+                          const double* b, double* x, double rtol, int max_iter, void* ws,
+                          int prec, double delta) {
     auto al = [](size_t b_) { return (b_ + 255) & ~size_t(255); };
     unsigned char* w = static_cast<unsigned char*>(ws);
     const size_t n = (size_t)std::max(1, A->rows);
@@ -43,6 +46,9 @@ BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* 
     P.row_ptr = A->row_ptr.as<int>();
     P.col_ind = A->col_ind.as<int>();
     P.val = A->val.as<double>();
+    P.val32 = A->val32.as<float>();
+    P.prec = kind == BK_CG ? prec : BP_F64;
+    P.delta2 = delta * delta;
     P.tiles = A->tiles.as<TileDesc>();
     P.longs = A->longs.as<LongRow>();
     P.rows = A->rows;
@@ -61,14 +67,20 @@ BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* 
     P.cnt = reinterpret_cast<unsigned*>(w);
     w += al(4 * sizeof(unsigned));
     P.part = reinterpret_cast<double*>(w);
-    w += al(sizeof(double) * ((size_t)A->ntiles + nchunks + 1));
+    w += al(sizeof(double) * (2 * (size_t)A->ntiles + nchunks + 1));
     P.long_part = reinterpret_cast<double*>(w);
     w += al(sizeof(double) * (size_t)std::max(1, A->nlong_chunks));
     P.long_red = reinterpret_cast<double*>(w);
     w += al(sizeof(double) * kMaxRed * (size_t)std::max(1, A->nlong));
     P.long_cnt = reinterpret_cast<unsigned*>(w);
     w += al(sizeof(unsigned) * (size_t)std::max(1, A->nlong));
-    if (kind == BK_CG) {
+    if (kind == BK_CG && P.prec == BP_F32_RU) {
+        float** v[4] = {&P.r32, &P.p32, &P.q32, &P.d32};
+        for (float** f : v) {
+            *f = reinterpret_cast<float*>(w);
+            w += al(sizeof(float) * n);
+        }
+    } else if (kind == BK_CG) {
         P.r = reinterpret_cast<double*>(w);
         w += al(sizeof(double) * n);
         P.p = reinterpret_cast<double*>(w);
@@ -93,8 +105,10 @@ lilac_status BatchEngine::ensure(int nprobs, int64_t nspmv, int64_t nvec) {
 
 lilac_status BatchEngine::upload(const std::vector<BatchProb>& probs, cudaStream_t s) {
     std::vector<BatchItem> ispmv, ivec;
+    mixed = false;
     for (int i = 0; i < (int)probs.size(); ++i) {
         const BatchProb& P = probs[i];
+        mixed = mixed || (P.kind == BK_CG && P.prec == BP_F32_RU);
         for (int t = 0; t < P.ntiles; ++t) ispmv.push_back({i, t});
         if (P.kind == BK_CG)
             for (int c = 0; c < P.nchunks; ++c) ivec.push_back({i, c});
@@ -129,7 +143,7 @@ int BatchEngine::grid_for(int64_t items) const {
 
 lilac_status BatchEngine::spmv_phase(cudaStream_t s) {
     if (host_counts[0] == 0) return LILAC_OK;
-    batch_spmv_kernel<<<grid_for(host_counts[0]), kBatchThreads, 0, s>>>(
+    batch_spmv_kernel<0><<<grid_for(host_counts[0]), kBatchThreads, 0, s>>>(
         probs_d.as<BatchProb>(), items_spmv_d.as<BatchItem>(), counts_d.as<int>());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -148,11 +162,18 @@ lilac_status BatchEngine::cg_start(cudaStream_t s) {
 // counts are not touched: the kernels read the counts from the device).
 lilac_status BatchEngine::enqueue_rounds(int R, cudaStream_t s, int g1, int g2) {
     for (int r = 0; r < R; ++r) {
-        batch_spmv_kernel<<<g1, kBatchThreads, 0, s>>>(probs_d.as<BatchProb>(),
-                                                       items_spmv_d.as<BatchItem>(), counts_d.as<int>());
+        batch_spmv_kernel<0><<<g1, kBatchThreads, 0, s>>>(
+            probs_d.as<BatchProb>(), items_spmv_d.as<BatchItem>(), counts_d.as<int>());
         batch_vec_kernel<1><<<g2, kBatchThreads, 0, s>>>(probs_d.as<BatchProb>(),
                                                          items_vec_d.as<BatchItem>(),
                                                          counts_d.as<int>() + 1);
+        if (mixed) {
+            batch_vec_kernel<3><<<g2, kBatchThreads, 0, s>>>(probs_d.as<BatchProb>(),
+                                                             items_vec_d.as<BatchItem>(),
+                                                             counts_d.as<int>() + 1);
+            batch_spmv_kernel<1><<<g1, kBatchThreads, 0, s>>>(
+                probs_d.as<BatchProb>(), items_spmv_d.as<BatchItem>(), counts_d.as<int>());
+        }
         batch_vec_kernel<2><<<g2, kBatchThreads, 0, s>>>(probs_d.as<BatchProb>(),
                                                          items_vec_d.as<BatchItem>(),
                                                          counts_d.as<int>() + 1);
@@ -165,7 +186,7 @@ lilac_status BatchEngine::cg_rounds(int R, cudaStream_t s) {
     if (host_counts[1] == 0) return LILAC_OK;
     // persistent grids: the full machine, independent of the current counts
     const int g = sm_count * 8;
-    const uint64_t key = ((uint64_t)R << 32) ^ gen;
+    const uint64_t key = ((uint64_t)R << 33) ^ ((uint64_t)mixed << 32) ^ gen;
     auto it = graphs.find(key);
     if (it == graphs.end()) {
         if (!capture_stream)
@@ -239,7 +260,7 @@ static lilac_status batch_check(lilac_batch B, int32_t count, const lilac_csr* A
     for (int i = 0; i < count; ++i) {
         LILAC_TRY(check_handle(A[i]));
         if (A[i]->dtype != LILAC_F64) {
-            set_last_error("batched calls take FP64 matrices");
+            set_last_error("batched calls take FP64 matrices (mixed precision derives FP32 values)");
             return LILAC_ERR_DTYPE;
         }
         if (A[i]->device != B->eng.device) {
@@ -252,11 +273,11 @@ static lilac_status batch_check(lilac_batch B, int32_t count, const lilac_csr* A
 
 // Carve zeroed workspaces for the problems out of the batch's arena.
 static lilac_status batch_workspaces(lilac_batch B, int32_t count, const lilac_csr* A, int kind,
-                                     std::vector<void*>& ws, cudaStream_t s) {
+                                     int prec, std::vector<void*>& ws, cudaStream_t s) {
     std::vector<size_t> sz((size_t)count);
     size_t total = 0;
     for (int i = 0; i < count; ++i) {
-        sz[i] = batch_workspace_bytes(A[i], kind);
+        sz[i] = batch_workspace_bytes(A[i], kind, prec);
         total += sz[i];
     }
     if (B->arena.bytes < total) {
@@ -284,19 +305,21 @@ extern "C" lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lil
     DeviceGuard g(B->eng.device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<void*> ws;
-    LILAC_TRY(batch_workspaces(B, count, A, BK_SPMV, ws, s));
+    LILAC_TRY(batch_workspaces(B, count, A, BK_SPMV, BP_F64, ws, s));
     std::vector<BatchProb> probs;
     for (int i = 0; i < count; ++i)
-        probs.push_back(make_batch_prob(A[i], BK_SPMV, x[i], y[i], nullptr, nullptr, 0.0, 0, ws[i]));
+        probs.push_back(make_batch_prob(A[i], BK_SPMV, x[i], y[i], nullptr, nullptr, 0.0, 0, ws[i],
+                                        BP_F64, 0.0));
     LILAC_TRY(B->eng.upload(probs, s));
     return B->eng.spmv_phase(s);
 }
 
 extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
                                        const double* const* b, double* const* x, int32_t max_iter,
-                                       double rtol, lilac_cg_info* infos, void* stream) {
+                                       double rtol, int32_t precision, lilac_cg_info* infos,
+                                       void* stream) {
     LILAC_TRY(batch_check(B, count, A));
-    if ((count > 0 && (!b || !x)) || max_iter < 0) {
+    if ((count > 0 && (!b || !x)) || max_iter < 0 || (precision != 0 && precision != 2)) {
         set_last_error("invalid argument to lilac_batch_cg");
         return LILAC_ERR_INVALID_ARG;
     }
@@ -309,10 +332,14 @@ extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac
     DeviceGuard g(B->eng.device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<void*> ws;
-    LILAC_TRY(batch_workspaces(B, count, A, BK_CG, ws, s));
+    const int prec = precision == 2 ? BP_F32_RU : BP_F64;
+    if (prec == BP_F32_RU)
+        for (int i = 0; i < count; ++i) LILAC_TRY(make_val32(A[i], s));
+    LILAC_TRY(batch_workspaces(B, count, A, BK_CG, prec, ws, s));
     std::vector<BatchProb> probs;
     for (int i = 0; i < count; ++i)
-        probs.push_back(make_batch_prob(A[i], BK_CG, nullptr, nullptr, b[i], x[i], rtol, max_iter, ws[i]));
+        probs.push_back(make_batch_prob(A[i], BK_CG, nullptr, nullptr, b[i], x[i], rtol, max_iter, ws[i],
+                                        prec, 0.1));
     LILAC_TRY(B->eng.upload(probs, s));
     LILAC_TRY(B->eng.cg_start(s));
     // rounds of R iterations until every problem is done
@@ -343,9 +370,12 @@ extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac
         if (infos) {
             infos[i] = lilac_cg_info{};
             infos[i].iters = hs[i].iters;
+            infos[i].refinements = prec == BP_F32_RU ? hs[i].updates : 0;
             infos[i].status = hs[i].status;
-            infos[i].rel_res = hs[i].bb > 0.0 ? std::sqrt(hs[i].rr / hs[i].bb) : 0.0;
-            infos[i].true_rel_res = -1.0;
+            const double rr = prec == BP_F32_RU && hs[i].true_rr >= 0.0 ? hs[i].true_rr : hs[i].rr;
+            infos[i].rel_res = hs[i].bb > 0.0 ? std::sqrt(rr / hs[i].bb) : 0.0;
+            // mixed precision: the last FP64 residual b - A x
+            infos[i].true_rel_res = prec == BP_F32_RU ? infos[i].rel_res : -1.0;
         }
         if (hs[i].status != LILAC_OK && worst == LILAC_OK) worst = (lilac_status)hs[i].status;
     }

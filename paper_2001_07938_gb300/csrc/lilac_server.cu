@@ -176,16 +176,21 @@ static lilac_status make_resident(lilac_server_s* S, int id, bool* ok) {
     return LILAC_OK;
 }
 
+static int req_prec(const SrvRequest* q) {
+    return q->r.kind == LILAC_REQ_CG && q->r.precision == 2 ? BP_F32_RU : BP_F64;
+}
+
 // Workspace of a request: per-vector problem workspaces + device in/out vectors.
 static size_t request_bytes(const lilac_server_s* S, const SrvRequest* q) {
     const SrvMatrix& m = S->mats[q->r.matrix];
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     if (q->r.kind == LILAC_REQ_SPMV) {
         const size_t k = (size_t)q->r.nvec;
-        return k * (al(batch_workspace_bytes(m.h, BK_SPMV)) + al(sizeof(double) * (size_t)std::max(1, m.ncols)) +
+        return k * (al(batch_workspace_bytes(m.h, BK_SPMV, BP_F64)) +
+                    al(sizeof(double) * (size_t)std::max(1, m.ncols)) +
                     al(sizeof(double) * (size_t)std::max(1, m.rows)));
     }
-    return al(batch_workspace_bytes(m.h, BK_CG)) + 2 * al(sizeof(double) * (size_t)m.rows);
+    return al(batch_workspace_bytes(m.h, BK_CG, req_prec(q))) + 2 * al(sizeof(double) * (size_t)m.rows);
 }
 
 static lilac_status admit(lilac_server_s* S) {
@@ -196,9 +201,18 @@ static lilac_status admit(lilac_server_s* S) {
         LILAC_TRY(make_resident(S, q->r.matrix, &ok));
         if (!ok) break;  // wait for memory to be released
         const size_t need = request_bytes(S, q);
-        if (used_bytes(S) + (int64_t)DevicePool::cls(need) > S->o.hbm_budget_bytes) {
+        // a mixed-precision solve derives the matrix's FP32 values on first use
+        const bool needs_val32 = req_prec(q) == BP_F32_RU && !m.h->val32_valid;
+        const int64_t extra = needs_val32 ? (int64_t)m.nnz * 4 + 256 : 0;
+        if (used_bytes(S) + (int64_t)DevicePool::cls(need) + extra > S->o.hbm_budget_bytes) {
             S->stats.budget_waits++;
             break;
+        }
+        if (needs_val32) {
+            LILAC_TRY(make_val32(m.h, S->stream));
+            lilac_csr_info_t info;
+            lilac_csr_info(m.h, &info);
+            m.bytes = info.device_bytes;
         }
         LILAC_TRY(S->pool.get(need, &q->ws));
         q->ws_bytes = need;
@@ -207,7 +221,7 @@ static lilac_status admit(lilac_server_s* S) {
         unsigned char* w = static_cast<unsigned char*>(q->ws);
         q->probs.clear();
         if (q->r.kind == LILAC_REQ_SPMV) {
-            const size_t wsb = al(batch_workspace_bytes(m.h, BK_SPMV));
+            const size_t wsb = al(batch_workspace_bytes(m.h, BK_SPMV, BP_F64));
             const size_t xb = al(sizeof(double) * (size_t)std::max(1, m.ncols));
             const size_t yb = al(sizeof(double) * (size_t)std::max(1, m.rows));
             for (int j = 0; j < q->r.nvec; ++j) {
@@ -216,17 +230,18 @@ static lilac_status admit(lilac_server_s* S) {
                 LILAC_CUDA_TRY(cudaMemcpyAsync(xd, q->r.in + (size_t)j * m.ncols,
                                                sizeof(double) * (size_t)m.ncols, cudaMemcpyHostToDevice,
                                                S->stream));
-                q->probs.push_back(make_batch_prob(m.h, BK_SPMV, xd, yd, nullptr, nullptr, 0.0, 0, w));
+                q->probs.push_back(
+                    make_batch_prob(m.h, BK_SPMV, xd, yd, nullptr, nullptr, 0.0, 0, w, BP_F64, 0.0));
                 w += wsb + xb + yb;
             }
         } else {
-            const size_t wsb = al(batch_workspace_bytes(m.h, BK_CG));
+            const size_t wsb = al(batch_workspace_bytes(m.h, BK_CG, req_prec(q)));
             double* bd = reinterpret_cast<double*>(w + wsb);
             double* xd = reinterpret_cast<double*>(w + wsb + al(sizeof(double) * (size_t)m.rows));
             LILAC_CUDA_TRY(cudaMemcpyAsync(bd, q->r.in, sizeof(double) * (size_t)m.rows,
                                            cudaMemcpyHostToDevice, S->stream));
             q->probs.push_back(make_batch_prob(m.h, BK_CG, nullptr, nullptr, bd, xd, q->r.rtol,
-                                               q->r.max_iter, w));
+                                               q->r.max_iter, w, req_prec(q), 0.1));
             S->cg_set_changed = true;
         }
         m.users++;
@@ -328,7 +343,9 @@ static lilac_status run_round(lilac_server_s* S) {
         if (it != finished_cg.end()) {
             const size_t i = (size_t)(std::find(cg_reqs.begin(), cg_reqs.end(), q) - cg_reqs.begin());
             const CgState& st = S->states_h[i];
-            retire(S, q, st.status, st.iters, st.bb > 0.0 ? std::sqrt(st.rr / st.bb) : 0.0);
+            // mixed precision reports its last FP64 residual b - A x
+            const double rr = req_prec(q) == BP_F32_RU && st.true_rr >= 0.0 ? st.true_rr : st.rr;
+            retire(S, q, st.status, st.iters, st.bb > 0.0 ? std::sqrt(rr / st.bb) : 0.0);
             S->cg_set_changed = true;
         } else {
             still.push_back(q);
@@ -416,7 +433,8 @@ lilac_status lilac_server_add_matrix(lilac_server S, int32_t rows, int32_t ncols
 lilac_status lilac_server_submit(lilac_server S, const lilac_request* r) {
     if (!S || !r || r->matrix < 0 || r->matrix >= (int32_t)S->mats.size() || !r->in || !r->out ||
         (r->kind != LILAC_REQ_SPMV && r->kind != LILAC_REQ_CG) ||
-        (r->kind == LILAC_REQ_SPMV && r->nvec < 1) || (r->kind == LILAC_REQ_CG && r->max_iter < 1)) {
+        (r->kind == LILAC_REQ_SPMV && r->nvec < 1) || (r->kind == LILAC_REQ_CG && r->max_iter < 1) ||
+        (r->kind == LILAC_REQ_CG && r->precision != 0 && r->precision != 2)) {
         set_last_error("invalid request");
         return LILAC_ERR_INVALID_ARG;
     }

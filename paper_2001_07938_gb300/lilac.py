@@ -93,7 +93,8 @@ class lilac_server_opts(ctypes.Structure):
 class lilac_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("matrix", ctypes.c_int32), ("nvec", ctypes.c_int32),
                 ("max_iter", ctypes.c_int32), ("rtol", ctypes.c_double),
-                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("tag", ctypes.c_int64)]
+                ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p), ("tag", ctypes.c_int64),
+                ("precision", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class lilac_completion(ctypes.Structure):
@@ -170,7 +171,7 @@ def _lib():
         lib.lilac_batch_destroy.argtypes = [vp]
         lib.lilac_batch_spmv.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), vp]
         lib.lilac_batch_cg.argtypes = [vp, i32, c.POINTER(vp), c.POINTER(vp), c.POINTER(vp), i32,
-                                       dbl, c.POINTER(lilac_cg_info), vp]
+                                       dbl, i32, c.POINTER(lilac_cg_info), vp]
         lib.lilac_server_opts_default.argtypes = [c.POINTER(lilac_server_opts)]
         lib.lilac_server_opts_default.restype = None
         lib.lilac_server_create.argtypes = [c.POINTER(lilac_server_opts), vp, c.POINTER(vp)]
@@ -382,11 +383,11 @@ class Batch:
                                        stream if stream is not None else current_stream()),
                "lilac_batch_spmv")
 
-    def cg(self, mats, bs, xs, max_iter=1000, rtol=1e-10, stream=None):
+    def cg(self, mats, bs, xs, max_iter=1000, rtol=1e-10, precision=0, stream=None):
         n = len(mats)
         infos = (lilac_cg_info * max(1, n))()
         st = _lib().lilac_batch_cg(self.handle, n, self._ptrs([m.handle.value for m in mats]),
-                                   self._ptrs(bs), self._ptrs(xs), max_iter, rtol, infos,
+                                   self._ptrs(bs), self._ptrs(xs), max_iter, rtol, precision, infos,
                                    stream if stream is not None else current_stream())
         _check(st, "lilac_batch_cg", (LILAC_OK, LILAC_ERR_NOT_CONVERGED, LILAC_ERR_BREAKDOWN))
         return st, [infos[i] for i in range(n)]
@@ -433,8 +434,9 @@ class Server:
         self._keep[("m", mid.value)] = (rp, ci, v)
         return mid.value
 
-    def submit(self, kind, matrix, inp, out, tag, nvec=1, max_iter=1000, rtol=1e-10):
-        r = lilac_request(kind, matrix, nvec, max_iter, rtol, inp.ctypes.data, out.ctypes.data, tag)
+    def submit(self, kind, matrix, inp, out, tag, nvec=1, max_iter=1000, rtol=1e-10, precision=0):
+        r = lilac_request(kind, matrix, nvec, max_iter, rtol, inp.ctypes.data, out.ctypes.data, tag,
+                          precision, 0)
         _check(_lib().lilac_server_submit(self.handle, ctypes.byref(r)), "lilac_server_submit")
         self._keep[("r", tag)] = (inp, out)
 

@@ -102,3 +102,30 @@ def test_batch_rejects_fp32_handles():
     assert e.value.status == L.LILAC_ERR_DTYPE
     B.close()
     M.close()
+
+
+def test_batched_mixed_precision_cg_reaches_fp64_tolerance_alone_and_in_a_mix():
+    """Precision 2 (FP32 values and vectors, FP64 reliable updates) in the
+    batched engine: each system's FP64 true residual <= 1e-10 (values FP32-exact
+    or not), and a system's result is bitwise the same alone and in a mix."""
+    torch = torch_cuda()
+    As = [inputs.laplacian3d(20), inputs.banded_spd(5000, 12, 1.0, seed=3, fp32_exact=False),
+          inputs.spd_random(6000, 15, 20.0, 3)]
+    Ms = [L.CsrMatrix.from_csr(A) for A in As]
+    bs = [dev(inputs.uniform(60 + i, A.n)) for i, A in enumerate(As)]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device="cuda") for A in As]
+    B = L.Batch()
+    st, infos = B.cg(Ms, bs, xs, max_iter=5000, rtol=1e-10, precision=2)
+    torch.cuda.synchronize()
+    assert st == L.LILAC_OK
+    for A, b, x, info in zip(As, bs, xs, infos):
+        assert info.status == L.LILAC_OK and info.refinements >= 1
+        assert true_rel_residual(A, host(b), host(x)) <= 1e-10
+        assert info.rel_res <= 1e-10
+    x_alone = torch.zeros(As[1].n, dtype=torch.float64, device="cuda")
+    B.cg([Ms[1]], [bs[1]], [x_alone], max_iter=5000, rtol=1e-10, precision=2)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host(x_alone), host(xs[1]))
+    B.close()
+    for M in Ms:
+        M.close()

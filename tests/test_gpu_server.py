@@ -1,5 +1,6 @@
-"""The request server: every request of a mixed SpMV / CG stream completes
-with the oracle's result (SpMV tolerance; CG true residual <= 1e-10), a
+"""The request server: every request of a mixed SpMV / CG stream (CG in FP64
+or in FP32 with FP64 reliable updates) completes with the oracle's result
+(SpMV tolerance; CG true residual <= 1e-10), a
 request's result is bitwise the same alone and in the mix, and a small
 device-memory budget forces evictions and waiting without changing results."""
 import numpy as np
@@ -20,7 +21,8 @@ def _pool():
 
 
 def _requests(pool, n, seed):
-    """(kind, matrix index, input, tag) for a seeded mix of SpMV and CG requests."""
+    """(kind, matrix index, input, vectors, tag, precision) for a seeded mix of
+    SpMV and CG requests; half of the CG requests run in mixed precision."""
     rng = np.random.default_rng(seed)
     out = []
     for t in range(n):
@@ -29,10 +31,10 @@ def _requests(pool, n, seed):
         if rng.random() < 0.5:
             k = int(rng.integers(1, 4))
             x = inputs.uniform(1000 + t, k * A.ncols)
-            out.append(("spmv", mi, x, k, t))
+            out.append(("spmv", mi, x, k, t, 0))
         else:
             b = inputs.uniform(2000 + t, A.n)
-            out.append(("cg", mi, b, 1, t))
+            out.append(("cg", mi, b, 1, t, 2 if rng.random() < 0.5 else 0))
     return out
 
 
@@ -43,14 +45,15 @@ def _serve(pool, reqs, budget=None, burst=7):
     outs, results = {}, {}
     i = 0
     while i < len(reqs) or len(results) < len(reqs):
-        for kind, mi, inp, k, tag in reqs[i:i + burst]:
+        for kind, mi, inp, k, tag, prec in reqs[i:i + burst]:
             A = pool[mi]
             if kind == "spmv":
                 out = np.full(k * A.n, np.nan)
                 S.submit(L.LILAC_REQ_SPMV, ids[mi], inp, out, tag, nvec=k)
             else:
                 out = np.full(A.n, np.nan)
-                S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, tag, max_iter=5000, rtol=1e-10)
+                S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, tag, max_iter=5000, rtol=1e-10,
+                         precision=prec)
             outs[tag] = out
         i += burst
         S.step()
@@ -62,7 +65,7 @@ def _serve(pool, reqs, budget=None, burst=7):
 
 
 def _check(pool, reqs, outs, results):
-    for kind, mi, inp, k, tag in reqs:
+    for kind, mi, inp, k, tag, prec in reqs:
         A, out, c = pool[mi], outs[tag], results[tag]
         assert c["status"] == L.LILAC_OK, (tag, c)
         assert c["finish"] >= c["arrival"]
@@ -73,7 +76,9 @@ def _check(pool, reqs, outs, results):
                 ref = oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
                 assert np.all(np.abs(y - ref) <= spmv_tolerance(A, x, False)), tag
         else:
-            assert true_rel_residual(A, inp, out) <= 1e-10, tag
+            assert true_rel_residual(A, inp, out) <= 1e-10, (tag, prec)
+            if prec == 2:  # reported: the last FP64 residual b - A x
+                assert c["rel_res"] <= 1e-10
 
 
 def test_mixed_stream_matches_oracle():
@@ -88,7 +93,11 @@ def test_same_result_alone_and_in_the_mix():
     pool = _pool()
     reqs = _requests(pool, 40, seed=1)
     outs_mix, _, _ = _serve(pool, reqs)
-    for probe in [r for r in reqs if r[0] == "cg"][:3] + [r for r in reqs if r[0] == "spmv"][:3]:
+    cgs = [r for r in reqs if r[0] == "cg"]
+    probes = ([r for r in cgs if r[5] == 0][:2] + [r for r in cgs if r[5] == 2][:2] +
+              [r for r in reqs if r[0] == "spmv"][:3])
+    assert len(probes) == 7
+    for probe in probes:
         outs_alone, _, _ = _serve(pool, [probe])
         np.testing.assert_array_equal(outs_alone[probe[4]], outs_mix[probe[4]])
 
@@ -112,6 +121,8 @@ def test_invalid_requests_are_rejected():
         S.submit(L.LILAC_REQ_SPMV, mid + 5, x, x, 0)
     with pytest.raises(L.LilacError):
         S.submit(L.LILAC_REQ_SPMV, mid, x, x, 0, nvec=0)
+    with pytest.raises(L.LilacError):
+        S.submit(L.LILAC_REQ_CG, mid, x, x, 0, precision=1)
     big = L.Server(hbm_budget_bytes=1 << 10)
     bid = big.add_matrix(A)
     with pytest.raises(L.LilacError) as e:
