@@ -80,9 +80,10 @@ typedef enum {
     LILAC_VARIANT_MERGE = 4,  /* merge-path partition of (rows + nonzeros) over CTAs; each thread
                                  walks 8 consecutive path items, rows split between threads or
                                  CTAs are finished from carries; no lanes-per-row setting */
-    LILAC_VARIANT_SLAB = 5,   /* row blocks x column slabs, built once per matrix: x is read
-                                 from shared memory, one slab of columns at a time; x must be
-                                 16-byte aligned (else STAGED runs) */
+    LILAC_VARIANT_SLAB = 5,   /* column slabs, built once per matrix: one CTA per SM holds a
+                                 slab of x (up to 192 KB) in shared memory and streams that
+                                 slab's nonzeros of a run of rows; partial sums combined per
+                                 row.  Matrices with more than 64 slabs run STAGED */
     LILAC_VARIANT_JDS = 6     /* jagged diagonal storage (Section 3.2), built once per matrix:
                                  rows sorted by length, one thread per row, nonzero d of all
                                  rows stored together; on another value array (an FP32 copy)
@@ -151,8 +152,8 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
 
 /* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR,
  * STAGED and SLAB, lanes per row (power of two 1..32; 0 keeps the current
- * one; SCALAR and MERGE use 1 whatever is passed).  Affects later calls.
- * Choosing SLAB builds its regrouped copy of the matrix on first use
+ * one; SCALAR, MERGE and JDS use 1 whatever is passed).  Affects later calls.
+ * Choosing SLAB or JDS builds the regrouped copy of the matrix on first use
  * (synchronous; errors OOM, CUDA). */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
 

@@ -150,20 +150,18 @@ lilac_status launch_jds(lilac_csr_s* A, const typename Op::ValT* val, const type
     return LILAC_OK;
 }
 
-template <int V, class Op>
-using SlabLayoutOf = SlabLayout<typename Op::ValT, typename Op::VecT, typename Op::AccT, kSlabTileNnz,
-                                kSlabTileRows, kSlabWidth, kSlabBlockRows, kSlabStages>;
-
+// SLAB: one CTA per SM holding a slab of x in shared memory (lilac_slab.cu
+// builds the regrouped copy).  The copy holds the handle's own values; another
+// value array (an FP32 copy) goes to STAGED, as does a handle without a copy.
 template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
-    using L = SlabLayoutOf<V, Op>;
     int& bps = bps_slot<V + 64, Op, true>(A->device);
     if (bps == 0) {
-        auto kern = spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth,
-                                     kSlabBlockRows, kSlabStages, Op>;
+        auto kern = spmv_slab_kernel<V, kSlabThreads, typename Op::ValT, typename Op::VecT,
+                                     typename Op::AccT>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (int)L::kSmemBytes));
-        bps = occupancy_per_sm(kern, kSlabThreads, L::kSmemBytes);
+                                            kSlabMaxBytes));
+        bps = 1;
     }
     return LILAC_OK;
 }
@@ -171,21 +169,18 @@ lilac_status prepare_slab(lilac_csr_s* A) {
 template <int V, class Op>
 lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    using L = SlabLayoutOf<V, Op>;
-    // the regrouped copy holds the handle's own values; another value array
-    // (e.g. an FP32 copy) or an x that bulk copies cannot read go to STAGED
-    const bool own_vals = (const void*)val == A->val.p;
-    if (!A->slab_built || !own_vals || (reinterpret_cast<uintptr_t>(x) & 15u) != 0)
-        return launch_staged<V, Op>(A, val, x, op, stream);
+    if (!A->slab_built || (const void*)val != A->val.p) return launch_staged<V, Op>(A, val, x, op, stream);
     LILAC_TRY(prepare_slab<V, Op>(A));
-    spmv_slab_kernel<V, kSlabThreads, kSlabTileNnz, kSlabTileRows, kSlabWidth, kSlabBlockRows,
-                     kSlabStages, Op>
-        <<<(unsigned)A->slab_grid, kSlabThreads, L::kSmemBytes, stream>>>(
-            A->slab_val.as<typename Op::ValT>(), A->slab_col.as<int>(), A->slab_lrp.as<int>(),
-            A->slab_tiles.as<SlabTile>(), A->slab_cta_tiles.as<int2>(), A->slab_cta_slabs.as<int2>(),
-            A->slab_blocks.as<SlabBlock>(), A->slab_nblocks, A->slab_nslabs, A->rows, A->ncols,
-            A->slab_P.as<typename Op::AccT>(), A->slab_cnt.as<unsigned>(),
-            A->slab_block_red.as<double>(), x, op, A->scratch());
+    using AccT = typename Op::AccT;
+    const size_t smem = sizeof(typename Op::VecT) * (size_t)A->slab_W;
+    spmv_slab_kernel<V, kSlabThreads, typename Op::ValT, typename Op::VecT, AccT>
+        <<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
+            A->slab_rp.as<int>(), A->slab_rp_stride, A->slab_col.as<uint16_t>(),
+            A->slab_val.as<typename Op::ValT>(), A->slab_ctas.as<int4>(), A->rows, A->ncols,
+            A->slab_W, x, A->slab_P.as<AccT>());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    slab_combine_kernel<kVecThreads, Op><<<vec_grid(A, A->rows), kVecThreads, 0, stream>>>(
+        A->rows, A->slab_S, A->slab_P.as<AccT>(), op, A->scratch());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
 }
@@ -198,8 +193,8 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
             return FN_JDS<1, Op>(__VA_ARGS__);                              \
         case LILAC_VARIANT_SLAB:                                            \
             switch (A->vwidth) {                                            \
-                case 1:                                                     \
-                case 2:                                                     \
+                case 1: return FN_SLAB<1, Op>(__VA_ARGS__);                 \
+                case 2: return FN_SLAB<2, Op>(__VA_ARGS__);                 \
                 case 4: return FN_SLAB<4, Op>(__VA_ARGS__);                 \
                 case 8: return FN_SLAB<8, Op>(__VA_ARGS__);                 \
                 default: return FN_SLAB<16, Op>(__VA_ARGS__);               \

@@ -242,9 +242,8 @@ lilac::Scratch lilac_csr_s::scratch() const {
 
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
-                                  &slab_val, &slab_col, &slab_lrp, &slab_tiles, &slab_blocks,
-                                  &slab_perm, &merge_coords, &merge_carries, &slab_cta_tiles,
-                                  &slab_cta_slabs, &slab_P, &slab_cnt, &slab_block_red,
+                                  &slab_rp, &slab_col, &slab_val, &slab_perm, &slab_ctas,
+                                  &slab_P, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
@@ -407,16 +406,23 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     cands.push_back({A->variant, A->vwidth});  // the heuristic's choice first
     for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_STAGED, w});
     cands.push_back({LILAC_VARIANT_MERGE, 1});
-    // SLAB is selectable (lilac_csr_set_variant) but not a tuning candidate:
-    // on the matrices it targets it measured slower than VECTOR.
     // row-per-group kernels serialise a long row in one group: only for
     // rows no longer than a few tiles
     if (A->max_row_len <= 4 * kTileNnz) {
         for (int w : {4, 8, 16, 32}) cands.push_back({LILAC_VARIANT_VECTOR, w});
         cands.push_back({LILAC_VARIANT_SCALAR, 1});
     }
-    // JDS (one thread per row, rows sorted by length): its copy is built for
-    // the trial and kept only if it wins
+    // SLAB (x slabs in shared memory) and JDS (one thread per row, rows sorted
+    // by length): their copies are built for the trial and kept only if they win
+    bool slab_trial = false;
+    if (!A->slab_built && slab_worthwhile(A)) {
+        if (ensure_slab(A, stream) == LILAC_OK && A->slab_built) {
+            slab_trial = true;
+            for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_SLAB, w});
+        } else {
+            slab_release(A);
+        }
+    }
     bool jds_trial = false;
     if (A->max_row_len <= 1024 && !A->jds_built) {
         if (ensure_jds(A, stream) == LILAC_OK) {
@@ -458,10 +464,11 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     cudaEventDestroy(e1);
     A->variant = bestc.variant;
     A->vwidth = bestc.width;
-    if (jds_trial && bestc.variant != LILAC_VARIANT_JDS) {
+    if ((jds_trial && bestc.variant != LILAC_VARIANT_JDS) ||
+        (slab_trial && bestc.variant != LILAC_VARIANT_SLAB))
         LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
-        jds_release(A);
-    }
+    if (jds_trial && bestc.variant != LILAC_VARIANT_JDS) jds_release(A);
+    if (slab_trial && bestc.variant != LILAC_VARIANT_SLAB) slab_release(A);
     return LILAC_OK;
 }
 
@@ -472,10 +479,7 @@ static void free_handle(lilac_csr A) {
     A->prof_events.clear();
     if (A->capture_stream) cudaStreamDestroy(A->capture_stream);
     lilac::DevBuf* all[] = {&A->row_ptr, &A->col_ind, &A->val, &A->val32, &A->tiles, &A->longs,
-                            &A->slab_val, &A->slab_col, &A->slab_lrp, &A->slab_tiles,
-                            &A->slab_blocks, &A->slab_perm, &A->merge_coords, &A->merge_carries,
-                            &A->slab_cta_tiles, &A->slab_cta_slabs, &A->slab_P, &A->slab_cnt,
-                            &A->slab_block_red,
+                            &A->merge_coords, &A->merge_carries,
                             &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
                             &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
                             &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
@@ -484,6 +488,7 @@ static void free_handle(lilac_csr A) {
                             &A->bfs_state, &A->bfs_level, &A->spmm_buf};
     for (auto* b : all) b->release();
     jds_release(A);
+    slab_release(A);
     delete A;
 }
 

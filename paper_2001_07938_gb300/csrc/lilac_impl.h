@@ -31,14 +31,10 @@ constexpr int kStagedThreads = LILAC_STAGED_THREADS;
 constexpr int kTileNnz = LILAC_TILE_NNZ;
 constexpr int kTileRows = LILAC_TILE_ROWS;
 constexpr int kRowsThreads = 256;
-// SLAB kernel shape: 512 threads, tiles of 2048 nonzeros touching at most
-// 256 rows, column slabs of 8192, row blocks of 512 rows, 3 pipeline stages.
-constexpr int kSlabThreads = 512;
-constexpr int kSlabTileNnz = 2048;
-constexpr int kSlabTileRows = 256;
-constexpr int kSlabWidth = 8192;
-constexpr int kSlabBlockRows = 512;
-constexpr int kSlabStages = 3;
+// SLAB kernel shape: one CTA of 1024 threads per SM with a slab of x of at
+// most kSlabMaxBytes (x elements counted as 8 bytes) in shared memory.
+constexpr int kSlabThreads = 1024;
+constexpr int kSlabMaxBytes = 192 * 1024;
 // MERGE kernel shape: 256 threads, sub-tiles of 2048 path items (8 per
 // thread); overridable at build time.
 #ifndef LILAC_MERGE_THREADS
@@ -120,10 +116,12 @@ struct lilac_csr_s {
     // STAGED schedule
     lilac::DevBuf tiles, longs;
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
-    // SLAB regrouped copy (built on first use)
-    lilac::DevBuf slab_val, slab_col, slab_lrp, slab_tiles, slab_blocks, slab_perm;
-    lilac::DevBuf slab_cta_tiles, slab_cta_slabs, slab_P, slab_cnt, slab_block_red;
-    int slab_nblocks = 0, slab_ntiles = 0, slab_nslabs = 0, slab_grid = 0;
+    // SLAB regrouped copy (built on first use): per-slab row pointers (S rows
+    // of rp_stride ints), 16-bit local columns, values, the CSR index of each
+    // regrouped nonzero (value updates), CTA runs {slab, first row, end row, -},
+    // and the partial sums P (S x rows)
+    lilac::DevBuf slab_rp, slab_col, slab_val, slab_perm, slab_ctas, slab_P;
+    int slab_S = 0, slab_W = 0, slab_grid = 0, slab_rp_stride = 0;
     bool slab_built = false;
     // JDS copy (built on first use): slot -> row, row -> slot, slot lengths,
     // jagged diagonal offsets, columns and values in JDS order
@@ -186,6 +184,7 @@ lilac_status ensure_jds(lilac_csr A, cudaStream_t stream);
 lilac_status jds_refresh_values(lilac_csr A, cudaStream_t stream);
 void jds_release(lilac_csr A);
 lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
+void slab_release(lilac_csr A);
 bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status check_device_status(lilac_csr A, cudaStream_t stream);
 // Event pairs for timing SpMV launches (pair i = events 2i, 2i+1).

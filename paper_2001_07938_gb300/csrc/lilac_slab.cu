@@ -1,16 +1,15 @@
-// Regrouped copy of a matrix for the SLAB kernel (row blocks x column
-// slabs), built once per handle on first use and kept with it, like the
-// other invariants cached at create.
+// Regrouped copy of a matrix for the SLAB kernels, built once per handle on
+// first use (or for the tuner's trial) and kept with it, like the other
+// invariants cached at create.
 //
-// Rows are cut into blocks of kSlabBlockRows; columns into slabs of
-// kSlabWidth.  Unit (b, s) = the nonzeros of block b whose columns lie in
-// slab s.  Storage is slab-major (slab, then block, then row; CSR order
-// inside a row) with local columns c - s*W and one row-pointer array per
-// unit (block rows + 1 absolute offsets).  Tiles of at most kSlabTileNnz
-// nonzeros and kSlabTileRows rows never cross a unit.  Non-empty units are
-// dealt, in storage order, to CTAs in contiguous runs of about equal
-// nonzero count; a run never touches more than two slabs (the kernel holds
-// two slabs of x), so runs are split where needed.
+// The columns are cut into S slabs of W columns, W * 8 bytes at most
+// kSlabMaxBytes, S as small as that allows.  Sub-matrix A_s holds, for every
+// row, the nonzeros whose column lies in [s W, (s+1) W), in CSR order, with
+// 16-bit local columns c - s W; the sub-matrices are stored one after the
+// other, each with its own row pointers (absolute offsets).  The rows of each
+// A_s are cut into G = SMs / S runs of about equal nonzero count, one per
+// CTA.  A permutation (regrouped position -> CSR position) re-gathers the
+// values after lilac_csr_update_values.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -19,153 +18,28 @@
 
 namespace lilac {
 
-bool slab_worthwhile(const lilac_csr_s* A) {
-    if (A->nnz == 0 || A->ncols == 0) return false;
-    const int64_t S = (A->ncols + kSlabWidth - 1) / kSlabWidth;
-    // each CTA's share of the nonzeros should cover whole slabs' worth of
-    // gathers: at least ~16 nonzeros per column on average, few slabs
-    return (double)A->nnz / (double)A->ncols >= 16.0 && S <= 64;
+namespace {
+
+int slab_count(const lilac_csr_s* A, int* W) {
+    const int64_t per = kSlabMaxBytes / 8;
+    const int64_t S = A->ncols > 0 ? (A->ncols + per - 1) / per : 0;
+    int64_t w = S > 0 ? (A->ncols + S - 1) / S : 0;
+    w = (w + 7) & ~int64_t(7);
+    *W = (int)w;
+    return (int)S;
 }
 
-template <class T>
-static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
-    const int n = A->rows;
-    const int64_t nnz = A->nnz;
-    const int W = kSlabWidth, RB = kSlabBlockRows;
-    const int S = A->ncols > 0 ? (A->ncols + W - 1) / W : 0;
-    const int NB = (n + RB - 1) / RB;
-    std::vector<int32_t> col((size_t)nnz);
-    std::vector<T> val((size_t)nnz);
-    if (nnz > 0) {
-        LILAC_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col_ind.p, sizeof(int32_t) * (size_t)nnz,
-                                       cudaMemcpyDeviceToHost, s));
-        LILAC_CUDA_TRY(cudaMemcpyAsync(val.data(), A->val.p, sizeof(T) * (size_t)nnz,
-                                       cudaMemcpyDeviceToHost, s));
-        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
-    }
-    const auto& rp = A->h_row_ptr;
-    // entries per (row, slab)
-    std::vector<int32_t> rs_cnt((size_t)n * std::max(1, S), 0);
-    for (int r = 0; r < n; ++r)
-        for (int j = rp[r]; j < rp[r + 1]; ++j) rs_cnt[(size_t)r * S + col[j] / W]++;
-    // units in storage order, their row pointers and tiles
-    std::vector<SlabBlock> blocks((size_t)NB);
-    for (int b = 0; b < NB; ++b) blocks[b] = {b * RB, std::min(RB, n - b * RB), 0, 0};
-    struct Unit { int b, s; int64_t k0, k1; int tile_begin, tile_end; int64_t lrp_base; };
-    std::vector<Unit> units;
-    std::vector<int32_t> lrp;
-    std::vector<int64_t> next((size_t)n * std::max(1, S));
-    int64_t pos = 0;
-    for (int sl = 0; sl < S; ++sl)
-        for (int b = 0; b < NB; ++b) {
-            const SlabBlock& B = blocks[b];
-            const int64_t base = (int64_t)lrp.size();
-            const int64_t k0 = pos;
-            for (int r = B.r0; r < B.r0 + B.nrows; ++r) {
-                lrp.push_back((int32_t)pos);
-                next[(size_t)r * S + sl] = pos;
-                pos += rs_cnt[(size_t)r * S + sl];
-            }
-            lrp.push_back((int32_t)pos);
-            if (pos > k0) {
-                units.push_back({b, sl, k0, pos, 0, 0, base});
-                blocks[b].need++;
-            }
-        }
-    std::vector<T> sval((size_t)((nnz + 11) & ~3ll));
-    std::vector<int32_t> scol((size_t)((nnz + 11) & ~3ll), 0);
-    std::vector<int32_t> perm((size_t)std::max<int64_t>(1, nnz));
-    for (int r = 0; r < n; ++r)
-        for (int j = rp[r]; j < rp[r + 1]; ++j) {
-            const int sl = col[j] / W;
-            const int64_t q = next[(size_t)r * S + sl]++;
-            sval[(size_t)q] = val[(size_t)j];
-            scol[(size_t)q] = col[j] - sl * W;
-            perm[(size_t)q] = j;
-        }
-    // tiles per unit
-    std::vector<SlabTile> tiles;
-    for (Unit& u : units) {
-        const int nr = blocks[u.b].nrows;
-        const int32_t* Lp = &lrp[(size_t)u.lrp_base];
-        u.tile_begin = (int)tiles.size();
-        int64_t k = u.k0;
-        int rl = 0;
-        while (k < u.k1) {
-            while (Lp[rl + 1] <= k) ++rl;  // first row that ends after k
-            int64_t k1 = std::min<int64_t>(u.k1, k + kSlabTileNnz);
-            int re = rl;
-            while (re < nr && Lp[re] < k1) ++re;  // rows [rl, re) start before k1
-            if (re - rl > kSlabTileRows) {
-                re = rl + kSlabTileRows;
-                k1 = Lp[re];
-            }
-            tiles.push_back({(int)k, (int)k1, (int)(u.lrp_base + rl), rl, re - rl, u.s, u.b, 0});
-            k = k1;
-        }
-        tiles.back().last = 1;
-        u.tile_end = (int)tiles.size();
-    }
-    // CTA runs: contiguous units, about nnz / sm_count each, at most two slabs
-    std::vector<int2> cta_tiles, cta_slabs;
-    const int64_t target = std::max<int64_t>(1, (nnz + A->sm_count - 1) / A->sm_count);
-    size_t u = 0;
-    while (u < units.size()) {
-        const size_t u0 = u;
-        int64_t acc = 0;
-        int s_a = units[u].s, s_b = -1;
-        while (u < units.size() && (acc < target || u == u0)) {
-            const int su = units[u].s;
-            if (su != s_a) {
-                if (s_b < 0)
-                    s_b = su;
-                else if (su != s_b)
-                    break;
-            }
-            acc += units[u].k1 - units[u].k0;
-            ++u;
-        }
-        cta_tiles.push_back(make_int2(units[u0].tile_begin, units[u - 1].tile_end));
-        cta_slabs.push_back(make_int2(s_a, s_b));
-    }
-    if (cta_tiles.empty()) {  // no nonzero at all: one CTA writes the zero rows
-        cta_tiles.push_back(make_int2(0, 0));
-        cta_slabs.push_back(make_int2(-1, -1));
-    }
-    lrp.resize(lrp.size() + 8, lrp.empty() ? 0 : lrp.back());  // padding for rounded-up copies
-    LILAC_TRY(A->ws_alloc(A->slab_val, sizeof(T) * sval.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_col, sizeof(int32_t) * scol.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_lrp, sizeof(int32_t) * lrp.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_blocks, sizeof(SlabBlock) * std::max<size_t>(1, blocks.size())));
-    LILAC_TRY(A->ws_alloc(A->slab_tiles, sizeof(SlabTile) * std::max<size_t>(1, tiles.size())));
-    LILAC_TRY(A->ws_alloc(A->slab_perm, sizeof(int32_t) * perm.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_cta_tiles, sizeof(int2) * cta_tiles.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_cta_slabs, sizeof(int2) * cta_slabs.size()));
-    LILAC_TRY(A->ws_alloc(A->slab_P, sizeof(double) * (size_t)std::max(1, S) * (size_t)std::max(1, n)));
-    LILAC_TRY(A->ws_alloc(A->slab_cnt, sizeof(unsigned) * std::max<size_t>(1, blocks.size())));
-    LILAC_TRY(A->ws_alloc(A->slab_block_red, sizeof(double) * kMaxRed * std::max<size_t>(1, blocks.size())));
-    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_P.p, 0, A->slab_P.bytes, s));  // empty units stay 0
-    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_cnt.p, 0, A->slab_cnt.bytes, s));
-    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_block_red.p, 0, A->slab_block_red.bytes, s));
-    auto up = [&](lilac::DevBuf& d, const void* h, size_t bytes) -> lilac_status {
-        if (bytes) LILAC_CUDA_TRY(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
-        return LILAC_OK;
-    };
-    LILAC_TRY(up(A->slab_val, sval.data(), sizeof(T) * sval.size()));
-    LILAC_TRY(up(A->slab_col, scol.data(), sizeof(int32_t) * scol.size()));
-    LILAC_TRY(up(A->slab_lrp, lrp.data(), sizeof(int32_t) * lrp.size()));
-    LILAC_TRY(up(A->slab_blocks, blocks.data(), sizeof(SlabBlock) * blocks.size()));
-    LILAC_TRY(up(A->slab_tiles, tiles.data(), sizeof(SlabTile) * tiles.size()));
-    LILAC_TRY(up(A->slab_perm, perm.data(), sizeof(int32_t) * perm.size()));
-    LILAC_TRY(up(A->slab_cta_tiles, cta_tiles.data(), sizeof(int2) * cta_tiles.size()));
-    LILAC_TRY(up(A->slab_cta_slabs, cta_slabs.data(), sizeof(int2) * cta_slabs.size()));
-    LILAC_CUDA_TRY(cudaStreamSynchronize(s));
-    A->slab_nblocks = (int)blocks.size();
-    A->slab_ntiles = (int)tiles.size();
-    A->slab_nslabs = S;
-    A->slab_grid = (int)cta_tiles.size();
-    A->slab_built = true;
-    return LILAC_OK;
+}  // namespace
+
+// Worth building when x is too large for L1 yet a handful of slabs holds it,
+// each CTA's share of the nonzeros is large, and rows are long enough per
+// slab to amortise the per-row work.
+bool slab_worthwhile(const lilac_csr_s* A) {
+    if (A->nnz == 0 || A->rows == 0 || A->ncols == 0) return false;
+    int W = 0;
+    const int S = slab_count(A, &W);
+    return (int64_t)A->ncols * 8 > (128 << 10) && S <= 8 && S <= A->sm_count &&
+           A->mean_row_len >= 8.0 * S && A->nnz >= (int64_t)A->sm_count * 4096;
 }
 
 template <class T>
@@ -176,28 +50,128 @@ __global__ void slab_regather_kernel(int64_t nnz, const int* __restrict__ perm,
         sval[q] = val[perm[q]];
 }
 
-// After new values were uploaded: rebuild the regrouped values on the device.
-lilac_status slab_refresh_values(lilac_csr A, cudaStream_t s) {
-    if (!A->slab_built || A->nnz == 0) return LILAC_OK;
-    if (A->dtype == LILAC_F64)
-        slab_regather_kernel<double><<<A->sm_count * 8, 256, 0, s>>>(
-            A->nnz, A->slab_perm.as<int>(), A->val.as<double>(), A->slab_val.as<double>());
-    else
-        slab_regather_kernel<float><<<A->sm_count * 8, 256, 0, s>>>(
-            A->nnz, A->slab_perm.as<int>(), A->val.as<float>(), A->slab_val.as<float>());
+template <class T>
+static lilac_status regather(lilac_csr A, cudaStream_t s) {
+    if (A->nnz == 0) return LILAC_OK;
+    slab_regather_kernel<T><<<A->sm_count * 8, 256, 0, s>>>(A->nnz, A->slab_perm.as<int>(),
+                                                             A->val.as<T>(), A->slab_val.as<T>());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
 }
 
+static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
+    const int n = A->rows;
+    const int64_t nnz = A->nnz;
+    int W = 0;
+    const int S = slab_count(A, &W);
+    const auto& rp = A->h_row_ptr;
+    std::vector<int32_t> col((size_t)nnz);
+    LILAC_CUDA_TRY(cudaMemcpyAsync(col.data(), A->col_ind.p, sizeof(int32_t) * (size_t)nnz,
+                                   cudaMemcpyDeviceToHost, s));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    // per-slab row pointers, rows padded to a multiple of 4 ints (16 bytes)
+    const int stride = ((n + 1) + 3) & ~3;
+    std::vector<int32_t> srp((size_t)S * (size_t)stride, 0);
+    {
+        std::vector<int32_t> cnt((size_t)S * (size_t)std::max(1, n), 0);
+        for (int r = 0; r < n; ++r)
+            for (int k = rp[r]; k < rp[r + 1]; ++k) cnt[(size_t)(col[(size_t)k] / W) * n + r]++;
+        int64_t base = 0;
+        for (int sl = 0; sl < S; ++sl) {
+            int32_t* p = srp.data() + (size_t)sl * stride;
+            p[0] = (int32_t)base;
+            for (int r = 0; r < n; ++r) {
+                p[r + 1] = p[r] + cnt[(size_t)sl * n + r];
+            }
+            for (int r = n + 1; r < stride; ++r) p[r] = p[n];
+            base = p[n];
+        }
+    }
+    // regrouped local columns and the permutation
+    std::vector<int32_t> perm((size_t)nnz);
+    std::vector<uint16_t> c16((size_t)nnz);
+    {
+        std::vector<int32_t> pos((size_t)S);
+        for (int r = 0; r < n; ++r) {
+            for (int sl = 0; sl < S; ++sl) pos[(size_t)sl] = srp[(size_t)sl * stride + r];
+            for (int k = rp[r]; k < rp[r + 1]; ++k) {
+                const int c = col[(size_t)k];
+                const int sl = c / W;
+                const int32_t q = pos[(size_t)sl]++;
+                perm[(size_t)q] = k;
+                c16[(size_t)q] = (uint16_t)(c - sl * W);
+            }
+        }
+    }
+    // runs of rows of about equal nonzero count per slab, one per CTA
+    const int G = std::max(1, A->sm_count / std::max(1, S));
+    std::vector<int4> ctas;
+    for (int sl = 0; sl < S; ++sl) {
+        const int32_t* p = srp.data() + (size_t)sl * stride;
+        const int64_t k0 = p[0], tot = (int64_t)p[n] - k0;
+        int r = 0;
+        for (int g = 0; g < G && r < n; ++g) {
+            const int r0 = r;
+            const int64_t target = k0 + tot * (g + 1) / G;
+            if (g == G - 1)
+                r = n;
+            else
+                while (r < n && p[r + 1] <= target) ++r;
+            if (r > r0) ctas.push_back(make_int4(sl, r0, r, 0));
+        }
+        if (r < n) ctas.push_back(make_int4(sl, r, n, 0));
+    }
+    const size_t vsz = A->dtype == LILAC_F64 ? 8 : 4;
+    const size_t npad = (size_t)nnz + 16;
+    LILAC_TRY(A->ws_alloc(A->slab_rp, sizeof(int32_t) * srp.size()));
+    LILAC_TRY(A->ws_alloc(A->slab_col, sizeof(uint16_t) * npad));
+    LILAC_TRY(A->ws_alloc(A->slab_val, vsz * npad));
+    LILAC_TRY(A->ws_alloc(A->slab_perm, sizeof(int32_t) * (size_t)std::max<int64_t>(1, nnz)));
+    LILAC_TRY(A->ws_alloc(A->slab_ctas, sizeof(int4) * std::max<size_t>(1, ctas.size())));
+    LILAC_TRY(A->ws_alloc(A->slab_P, sizeof(double) * (size_t)S * (size_t)std::max(1, n)));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_col.p, 0, A->slab_col.bytes, s));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_val.p, 0, A->slab_val.bytes, s));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_P.p, 0, A->slab_P.bytes, s));
+    auto up = [&](lilac::DevBuf& d, const void* h, size_t bytes) -> lilac_status {
+        if (bytes) LILAC_CUDA_TRY(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
+        return LILAC_OK;
+    };
+    LILAC_TRY(up(A->slab_rp, srp.data(), sizeof(int32_t) * srp.size()));
+    LILAC_TRY(up(A->slab_col, c16.data(), sizeof(uint16_t) * c16.size()));
+    LILAC_TRY(up(A->slab_perm, perm.data(), sizeof(int32_t) * perm.size()));
+    LILAC_TRY(up(A->slab_ctas, ctas.data(), sizeof(int4) * ctas.size()));
+    LILAC_TRY(A->dtype == LILAC_F64 ? regather<double>(A, s) : regather<float>(A, s));
+    LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    A->slab_S = S;
+    A->slab_W = W;
+    A->slab_grid = (int)ctas.size();
+    A->slab_rp_stride = stride;
+    A->slab_built = !ctas.empty();
+    return LILAC_OK;
+}
+
+// After new values were uploaded: rebuild the regrouped values on the device.
+lilac_status slab_refresh_values(lilac_csr A, cudaStream_t s) {
+    if (!A->slab_built) return LILAC_OK;
+    return A->dtype == LILAC_F64 ? regather<double>(A, s) : regather<float>(A, s);
+}
+
+void slab_release(lilac_csr A) {
+    lilac::DevBuf* b[] = {&A->slab_rp, &A->slab_col, &A->slab_val, &A->slab_perm, &A->slab_ctas,
+                          &A->slab_P};
+    for (auto* d : b) d->release();
+    A->slab_S = A->slab_W = A->slab_grid = A->slab_rp_stride = 0;
+    A->slab_built = false;
+}
+
 lilac_status ensure_slab(lilac_csr A, cudaStream_t s) {
     if (A->slab_built) return LILAC_OK;
-    const int64_t S = A->ncols > 0 ? (A->ncols + kSlabWidth - 1) / kSlabWidth : 0;
-    // per (row, slab) counters and row pointers: (slabs) x (rows + blocks) entries
-    if (S > 256 || S * (2 * (int64_t)A->rows + 2) >= (int64_t(1) << 31) - 64) {
-        set_last_error("matrix has too many column slabs for the SLAB layout");
-        return LILAC_ERR_UNSUPPORTED;
-    }
-    return A->dtype == LILAC_F64 ? build_slab<double>(A, s) : build_slab<float>(A, s);
+    int W = 0;
+    const int S = slab_count(A, &W);
+    if (A->nnz == 0 || S == 0) return LILAC_OK;  // nothing to regroup: STAGED runs
+    // too many slabs for the layout: not built, STAGED runs
+    if (S > 64 || (int64_t)S * ((int64_t)A->rows + 4) >= (int64_t(1) << 31) - 64) return LILAC_OK;
+    return build_slab(A, s);
 }
 
 }  // namespace lilac

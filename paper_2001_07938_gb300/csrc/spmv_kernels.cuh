@@ -343,275 +343,96 @@ __global__ void __launch_bounds__(THREADS)
 namespace lilac {
 
 // ---------------------------------------------------------------------------
-// SLAB kernel: x read from shared memory instead of L2.
+// SLAB kernels: x gathered from shared memory instead of through L1/L2.
 //
-// The matrix is regrouped once (lilac_slab.cu) into row blocks x column
-// slabs: the nonzeros of row block b whose columns lie in slab s (columns
-// [s*W, (s+1)*W)) form unit (b, s), stored contiguously, row by row, with
-// local column indices col - s*W and a row-pointer array per unit.  Units are
-// ordered slab by slab and dealt to CTAs in nnz-balanced contiguous runs, so a
-// CTA touches at most two slabs: it loads those slabs of x into shared memory
-// once (bulk copies), then streams its units' nonzeros in tiles through an
-// NST-stage bulk-copy pipeline, gathering x from shared memory and adding each
-// row's pieces into a per-row accumulator in shared memory.  At the end of a
-// unit the accumulators go to the partial array P[s][row]; the CTA that
-// completes the last unit of a row block (arrival counter) adds P over the
-// slabs in slab order and runs the epilogue for the block's rows.  Gathers
-// never leave the SM; the extra traffic is P (written and read once).
-struct SlabTile {
-    int k0, k1;    // nonzeros [k0, k1) of the regrouped arrays
-    int lrp_idx;   // index in the row-pointer array of the tile's first row
-    int rl0;       // block-local index of that row
-    int nrows;     // rows [rl0, rl0 + nrows) overlap the tile
-    int slab;      // column slab
-    int block;     // row block
-    int last;      // 1: last tile of its unit
-};
-
-struct SlabBlock {
-    int r0, nrows;  // rows [r0, r0 + nrows)
-    int need;       // number of non-empty units of the block
-    int pad;
-};
-
-template <class ValT, class VecT, class AccT, int TN, int TRS, int W, int RB, int NST>
-struct SlabLayout {
-    static constexpr size_t kXBytes = sizeof(VecT) * W;
-    static constexpr size_t kYBytes = (sizeof(AccT) * RB + 15) / 16 * 16;
-    static constexpr int kValElems = TN + 8;
-    static constexpr int kRpElems = TRS + 8;
-    static constexpr size_t kValBytes = sizeof(ValT) * kValElems;
-    static constexpr size_t kColBytes = sizeof(int) * kValElems;
-    static constexpr size_t kRpBytes = sizeof(int) * kRpElems;
-    static constexpr size_t kStageBytes = kValBytes + kColBytes + kRpBytes;
-    static constexpr size_t kProdBytes = sizeof(AccT) * kValElems;  // products: own buffer
-    static constexpr size_t kStageOff = 2 * kXBytes + kYBytes;
-    static constexpr size_t kSmemBytes = kStageOff + NST * kStageBytes + kProdBytes;
-};
-
-template <int V, int THREADS, int TN, int TRS, int W, int RB, int NST, class Op>
+// Random 8-byte gathers through L1 cost one tag lookup per distinct line
+// (about one per cycle per SM); gathers from shared memory cost one bank
+// access each, many per cycle.  The columns are cut into S slabs of W
+// columns (W * 8 bytes at most kSlabMaxBytes) and the matrix is regrouped
+// once (lilac_slab.cu) into S sub-matrices A_s (the nonzeros of each row
+// whose column lies in slab s, in CSR order, 16-bit local columns c - s W),
+// stored one after the other with their own row pointers.  CTA (s, g), one
+// per SM, loads slab s of x into shared memory and computes the row sums of
+// A_s x_s for its run of rows (runs of about equal nonzero count) into
+// P[s][row], V lanes per row with four nonzeros in flight per lane; the
+// combine kernel adds P over the slabs in slab order and runs the epilogue.
+template <int V, int THREADS, class ValT, class VecT, class AccT>
 __global__ void __launch_bounds__(THREADS, 1)
-    spmv_slab_kernel(const typename Op::ValT* __restrict__ sval, const int* __restrict__ scol,
-                     const int* __restrict__ lrp, const SlabTile* __restrict__ tiles,
-                     const int2* __restrict__ cta_tiles, const int2* __restrict__ cta_slabs,
-                     const SlabBlock* __restrict__ blocks, int nblocks, int nslabs, int rows,
-                     int ncols, typename Op::AccT* __restrict__ P, unsigned* __restrict__ cnt,
-                     double* __restrict__ block_red, const typename Op::VecT* __restrict__ x,
-                     Op op, Scratch s) {
+    spmv_slab_kernel(const int* __restrict__ srp, int rp_stride, const uint16_t* __restrict__ scol,
+                     const ValT* __restrict__ sval, const int4* __restrict__ ctas, int rows,
+                     int ncols, int W, const VecT* __restrict__ x, AccT* __restrict__ P) {
+    extern __shared__ __align__(16) unsigned char slab_smem[];
+    VecT* xs = reinterpret_cast<VecT*>(slab_smem);
+    const int4 c = ctas[blockIdx.x];  // {slab, first row, end row, -}
+    const int sl = c.x, r0 = c.y, r1 = c.z;
+    const int c0 = sl * W;
+    const int w = min(W, ncols - c0);
+    {
+        // the slab of x into shared memory: 16-byte loads when x is aligned
+        // (c0 is a multiple of 8), eight in flight per thread
+        constexpr int E = 16 / sizeof(VecT);
+        const bool al = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
+        const int nv = al ? w / E : 0;
+        const uint4* __restrict__ xv = reinterpret_cast<const uint4*>(x + c0);
+        uint4* xsv = reinterpret_cast<uint4*>(xs);
+        int i = threadIdx.x;
+        for (; i + 7 * THREADS < nv; i += 8 * THREADS) {
+            uint4 t[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) t[u] = __ldg(xv + i + u * THREADS);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xsv[i + u * THREADS] = t[u];
+        }
+        for (; i < nv; i += THREADS) xsv[i] = __ldg(xv + i);
+        for (int j = nv * E + threadIdx.x; j < w; j += THREADS) xs[j] = __ldg(x + c0 + j);
+    }
+    __syncthreads();
+    const int* __restrict__ rp = srp + (size_t)sl * rp_stride;
+    const int lane = threadIdx.x & (V - 1);
+    const int group = threadIdx.x / V;
+    constexpr int NG = THREADS / V;
+    const unsigned mask = group_mask<V>(threadIdx.x);
+    AccT* __restrict__ Ps = P + (size_t)sl * rows;
+    for (int r = r0 + group; r < r1; r += NG) {
+        const int kb = __ldg(rp + r), ke = __ldg(rp + r + 1);
+        AccT s0 = AccT(0), s1 = AccT(0), s2 = AccT(0), s3 = AccT(0);
+        int k = kb + lane;
+        for (; k + 3 * V < ke; k += 4 * V) {
+            const int a0 = ld_stream(scol + k), a1 = ld_stream(scol + k + V);
+            const int a2 = ld_stream(scol + k + 2 * V), a3 = ld_stream(scol + k + 3 * V);
+            const ValT v0 = ld_stream(sval + k), v1 = ld_stream(sval + k + V);
+            const ValT v2 = ld_stream(sval + k + 2 * V), v3 = ld_stream(sval + k + 3 * V);
+            s0 += AccT(v0) * AccT(xs[a0]);
+            s1 += AccT(v1) * AccT(xs[a1]);
+            s2 += AccT(v2) * AccT(xs[a2]);
+            s3 += AccT(v3) * AccT(xs[a3]);
+        }
+        for (; k < ke; k += V) s0 += AccT(ld_stream(sval + k)) * AccT(xs[(int)ld_stream(scol + k)]);
+        AccT sum = (s0 + s1) + (s2 + s3);
+        if constexpr (V > 1) sum = group_sum<V>(sum, mask);
+        if (lane == 0) Ps[r] = sum;
+    }
+}
+
+// y_r = sum over slabs s (in order) of P[s][r], then the epilogue.
+template <int THREADS, class Op>
+__global__ void __launch_bounds__(THREADS)
+    slab_combine_kernel(int rows, int S, const typename Op::AccT* __restrict__ P, Op op, Scratch s) {
     if (op.skip()) return;
     op.begin();
-    using ValT = typename Op::ValT;
-    using VecT = typename Op::VecT;
     using AccT = typename Op::AccT;
-    using L = SlabLayout<ValT, VecT, AccT, TN, TRS, W, RB, NST>;
     constexpr int NR = Op::NR;
-    constexpr int NGROUPS = THREADS / V;
-    constexpr int IPT = TN / THREADS;
-    static_assert(TN % THREADS == 0, "tile nonzeros must be a multiple of the block size");
-
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar[NST];
-    __shared__ __align__(8) uint64_t xbar[2];
-    __shared__ SlabTile sdesc[NST];
-    __shared__ double sh_red[kMaxRed * 32];
-    __shared__ int s_last;
-
-    VecT* xs[2] = {reinterpret_cast<VecT*>(smem), reinterpret_cast<VecT*>(smem + L::kXBytes)};
-    AccT* yacc = reinterpret_cast<AccT*>(smem + 2 * L::kXBytes);
-    auto stage_ptr = [&](int st) { return smem + L::kStageOff + st * L::kStageBytes; };
-    AccT* prod_extra = reinterpret_cast<AccT*>(smem + L::kStageOff + NST * L::kStageBytes);
-
-    const int tid = threadIdx.x;
-    const int lane = tid & (V - 1);
-    const int group = tid / V;
-    const unsigned mask = group_mask<V>(tid);
-    const int2 ct = cta_tiles[blockIdx.x];   // tiles [ct.x, ct.y)
-    const int2 cs2 = cta_slabs[blockIdx.x];  // slabs held in buffers 0 and 1 (-1: none)
-
-    uint64_t policy = 0;
-    if (tid == 0) {
-        for (int q = 0; q < NST; ++q) mbar_init(&bar[q], 1);
-        mbar_init(&xbar[0], 1);
-        mbar_init(&xbar[1], 1);
-        fence_mbar_init();
-        policy = l2_policy_evict_first();
-    }
-    for (int r = tid; r < RB; r += THREADS) yacc[r] = AccT(0);
-    __syncthreads();
-
-    // Thread 0: x slab `sl` into buffer b (16-byte-aligned bulk part by the
-    // copy engine, the last < 16 bytes by plain loads before the arrive).
-    auto issue_x = [&](int sl, int b) {
-        const int c0 = sl * W;
-        const int ne = min(W, ncols - c0);
-        const uint32_t bytes = (uint32_t)ne * (uint32_t)sizeof(VecT);
-        const uint32_t bulk = bytes & ~15u;
-        for (uint32_t e = bulk / sizeof(VecT); e < (uint32_t)ne; ++e) xs[b][e] = x[c0 + e];
-        mbar_arrive_expect_tx(&xbar[b], bulk);
-        if (bulk) bulk_g2s(xs[b], x + c0, bulk, &xbar[b], l2_policy_evict_normal());
-    };
-    auto issue_tile = [&](int ti, int st) {
-        const SlabTile t = tiles[ti];
-        sdesc[st] = t;
-        unsigned char* base = stage_ptr(st);
-        const int ka = t.k0 & ~3;
-        const int kz = (t.k1 + 3) & ~3;
-        const uint32_t nk = (uint32_t)(kz - ka);
-        const int ra = t.lrp_idx & ~3;
-        const int rz = (t.lrp_idx + t.nrows + 1 + 3) & ~3;
-        const uint32_t nr = (uint32_t)(rz - ra);
-        mbar_arrive_expect_tx(&bar[st], nk * (uint32_t)(sizeof(ValT) + sizeof(int)) + nr * 4u);
-        if (nk) {
-            bulk_g2s(base, sval + ka, nk * (uint32_t)sizeof(ValT), &bar[st], policy);
-            bulk_g2s(base + L::kValBytes, scol + ka, nk * 4u, &bar[st], policy);
-        }
-        bulk_g2s(base + L::kValBytes + L::kColBytes, lrp + ra, nr * 4u, &bar[st], policy);
-    };
-
-    const int ntile = ct.y - ct.x;
-    if (tid == 0) {
-        if (cs2.x >= 0) issue_x(cs2.x, 0);
-        if (cs2.y >= 0) issue_x(cs2.y, 1);
-        for (int q = 0; q < NST - 1 && q < ntile; ++q) issue_tile(ct.x + q, q);
-    }
-    bool failed = false;
-    bool xready[2] = {false, false};
-    uint32_t uses[NST];
-#pragma unroll
-    for (int q = 0; q < NST; ++q) uses[q] = 0u;
-    for (int i = 0; i < ntile; ++i) {
-        const int st = i % NST;
-        if (tid == 0 && i + NST - 1 < ntile) {
-            fence_proxy_async_smem();
-            issue_tile(ct.x + i + NST - 1, (i + NST - 1) % NST);
-        }
-        ++uses[st];
-        bool ok = mbar_wait_bounded(&bar[st], (uses[st] - 1u) & 1u);
-        const SlabTile t = sdesc[st];
-        const int xb = t.slab == cs2.x ? 0 : 1;
-        if (!xready[xb]) {
-            ok = ok && mbar_wait_bounded(&xbar[xb], 0u);
-            xready[xb] = true;
-        }
-        if (!__syncthreads_and(ok ? 1 : 0)) {
-            failed = true;
-            break;
-        }
-        unsigned char* base = stage_ptr(st);
-        const ValT* vs = reinterpret_cast<const ValT*>(base);
-        const int* cs = reinterpret_cast<const int*>(base + L::kValBytes);
-        const int* rps = reinterpret_cast<const int*>(base + L::kValBytes + L::kColBytes);
-        AccT* prod = prod_extra;
-        const VecT* xv = xs[xb];
-        const int ka = t.k0 & ~3;
-        const int kb0 = t.k0 - ka, ke0 = t.k1 - ka;
-        // Phase A: products, x from shared memory
-#pragma unroll
-        for (int j = 0; j < IPT; ++j) {
-            const int k = kb0 + j * THREADS + tid;
-            if (k < ke0) prod[k] = AccT(vs[k]) * AccT(xv[cs[k]]);
-        }
-        __syncthreads();
-        // Phase B: each row's part of the tile, into its accumulator
-        const int ra = t.lrp_idx & ~3;
-        for (int rr = group; rr < t.nrows; rr += NGROUPS) {
-            const int a = max(rps[t.lrp_idx - ra + rr], t.k0) - ka;
-            const int b = min(rps[t.lrp_idx - ra + rr + 1], t.k1) - ka;
-            AccT sum = AccT(0);
-            for (int k = a + lane; k < b; k += V) sum += prod[k];
-            if constexpr (V > 1) sum = group_sum<V>(sum, mask);
-            if (lane == 0 && b > a) yacc[t.rl0 + rr] += sum;
-        }
-        __syncthreads();
-        if (t.last) {
-            // end of unit (t.block, t.slab): accumulators -> P, then arrival
-            const SlabBlock B = blocks[t.block];
-            AccT* Pp = P + (size_t)t.slab * rows + B.r0;
-            for (int r = tid; r < B.nrows; r += THREADS) {
-                Pp[r] = yacc[r];
-                yacc[r] = AccT(0);
-            }
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();  // cumulative: publishes the block's P writes
-                const unsigned c = atomicAdd(&cnt[t.block], 1u);
-                s_last = (c == (unsigned)B.need - 1u) ? 1 : 0;
-            }
-            __syncthreads();
-            if (s_last) {
-                // this CTA finished the block: sum the slabs in order, epilogue
-                __threadfence();
-                double red[NR > 0 ? NR : 1] = {};
-                for (int r = tid; r < B.nrows; r += THREADS) {
-                    AccT v = AccT(0);
-                    for (int sl = 0; sl < nslabs; ++sl) v += __ldcg(&P[(size_t)sl * rows + B.r0 + r]);
-                    op.row(B.r0 + r, v, red);
-                }
-                if constexpr (NR > 0) {
-                    double tot[NR];
-                    double r2[NR];
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) r2[q] = red[q];
-                    block_sum<NR, THREADS>(r2, tot, sh_red);
-                    if (tid == 0) {
-#pragma unroll
-                        for (int q = 0; q < NR; ++q) block_red[t.block * kMaxRed + q] = tot[q];
-                    }
-                }
-                if (tid == 0) cnt[t.block] = 0u;
-                __syncthreads();
-            }
-        }
-    }
-    if (failed) {
-        if (tid == 0) atomicExch(s.status, DEV_TIMEOUT);
-        return;
-    }
-    // blocks without any nonzero: their rows are 0 (done by CTA 0's range)
-    if (blockIdx.x == 0) {
-        double red[NR > 0 ? NR : 1] = {};
-        for (int b = 0; b < nblocks; ++b) {
-            const SlabBlock B = blocks[b];
-            if (B.need != 0) continue;
-            for (int r = tid; r < B.nrows; r += THREADS) op.row(B.r0 + r, AccT(0), red);
-            if constexpr (NR > 0) {
-                double tot[NR];
-                double r2[NR];
-#pragma unroll
-                for (int q = 0; q < NR; ++q) r2[q] = red[q];
-                block_sum<NR, THREADS>(r2, tot, sh_red);
-                if (tid == 0) {
-#pragma unroll
-                    for (int q = 0; q < NR; ++q) block_red[b * kMaxRed + q] = tot[q];
-                }
-#pragma unroll
-                for (int q = 0; q < NR; ++q) red[q] = 0.0;
-            }
-        }
+    double red[NR > 0 ? NR : 1] = {};
+    for (int r = blockIdx.x * THREADS + threadIdx.x; r < rows; r += gridDim.x * THREADS) {
+        AccT sum = P[r];
+        for (int q = 1; q < S; ++q) sum += P[(size_t)q * rows + r];
+        op.row(r, sum, red);
     }
     if constexpr (NR > 0) {
-        // grid sum over the per-block sums, in block order
-        if (tid == 0) {
-            __threadfence();
-            const unsigned t = atomicAdd(s.ticket, 1u);
-            s_last = (t == gridDim.x - 1) ? 1 : 0;
-        }
-        __syncthreads();
-        if (!s_last) return;
-        __threadfence();
-        double acc[NR];
+        double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] = 0.0;
-        for (int b = tid; b < nblocks; b += THREADS) {
-#pragma unroll
-            for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&block_red[b * kMaxRed + q]);
-        }
-        double tot[NR];
-        block_sum<NR, THREADS>(acc, tot, sh_red);
-        if (tid == 0) {
-            op.finish(tot);
-            *s.ticket = 0u;
-        }
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
     }
 }
 

@@ -59,4 +59,4 @@ def true_rel_residual(A, b, x):
 
 
 ALL_VARIANTS = ([(1, 1)] + [(2, w) for w in (2, 4, 8, 16, 32)] + [(3, w) for w in (1, 2, 4, 8, 16, 32)]
-                + [(4, 1)] + [(5, w) for w in (4, 8, 16)] + [(6, 1)])
+                + [(4, 1)] + [(5, w) for w in (1, 2, 4, 8, 16)] + [(6, 1)])
