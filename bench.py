@@ -191,7 +191,10 @@ class CG75k(Workload):
         self.xd = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
         self.opts = L.lilac_cg_opts_default()
         self.opts.max_iter, self.opts.rtol, self.opts.true_residual = self.iters, 0.0, 0
-        self.launches_per_step = 2 + 3 * self.iters
+        # kernels per solve, as the library counts them for the chosen variant
+        _, info = L.lilac_cg(self.M.handle, self.bd.data_ptr(), self.xd.data_ptr(),
+                             L.LILAC_MEM_DEVICE, self.opts, want_info=True)
+        self.launches_per_step = info.kernel_launches
 
     def step(self):
         L = self.L

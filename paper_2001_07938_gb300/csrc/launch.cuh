@@ -228,6 +228,12 @@ lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
     return prepare_staged<V, Op>(A);
 }
 
+// Kernel launches one SpMV of the handle's variant makes with value array
+// `val` (SLAB: the slab kernel and the combine kernel).
+inline int spmv_launch_count(const lilac_csr_s* A, const void* val) {
+    return A->variant == LILAC_VARIANT_SLAB && A->slab_built && val == A->val.p ? 2 : 1;
+}
+
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
     LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge,

@@ -99,7 +99,19 @@ __global__ void __launch_bounds__(THREADS)
             s3 += AccT(w3) * AccT(x3);
             k = kn;
         }
-        for (; k < ke; k += V) s0 += AccT(ld_stream(A.val + k)) * AccT(__ldg(x + ld_stream(A.col_ind + k)));
+        {
+            // the last (at most three) nonzeros of this lane: loads issued together
+            const bool q0 = k < ke, q1 = k + V < ke, q2 = k + 2 * V < ke;
+            const int a0 = q0 ? ld_stream(A.col_ind + k) : 0;
+            const int a1 = q1 ? ld_stream(A.col_ind + k + V) : 0;
+            const int a2 = q2 ? ld_stream(A.col_ind + k + 2 * V) : 0;
+            const typename Op::ValT w0 = q0 ? ld_stream(A.val + k) : typename Op::ValT(0);
+            const typename Op::ValT w1 = q1 ? ld_stream(A.val + k + V) : typename Op::ValT(0);
+            const typename Op::ValT w2 = q2 ? ld_stream(A.val + k + 2 * V) : typename Op::ValT(0);
+            if (q0) s0 += AccT(w0) * AccT(__ldg(x + a0));
+            if (q1) s1 += AccT(w1) * AccT(__ldg(x + a1));
+            if (q2) s2 += AccT(w2) * AccT(__ldg(x + a2));
+        }
         AccT sum = (s0 + s1) + (s2 + s3);
         if constexpr (V > 1) sum = group_sum<V>(sum, mask);
         if (lane == 0) op.row(r, sum, red);
@@ -407,7 +419,19 @@ __global__ void __launch_bounds__(THREADS, 1)
             s2 += AccT(v2) * AccT(xs[a2]);
             s3 += AccT(v3) * AccT(xs[a3]);
         }
-        for (; k < ke; k += V) s0 += AccT(ld_stream(sval + k)) * AccT(xs[(int)ld_stream(scol + k)]);
+        {
+            // the last (at most three) nonzeros of this lane: loads issued together
+            const bool q0 = k < ke, q1 = k + V < ke, q2 = k + 2 * V < ke;
+            const int a0 = q0 ? ld_stream(scol + k) : 0;
+            const int a1 = q1 ? ld_stream(scol + k + V) : 0;
+            const int a2 = q2 ? ld_stream(scol + k + 2 * V) : 0;
+            const ValT w0 = q0 ? ld_stream(sval + k) : ValT(0);
+            const ValT w1 = q1 ? ld_stream(sval + k + V) : ValT(0);
+            const ValT w2 = q2 ? ld_stream(sval + k + 2 * V) : ValT(0);
+            s0 += AccT(w0) * AccT(xs[a0]);
+            s1 += AccT(w1) * AccT(xs[a1]);
+            s2 += AccT(w2) * AccT(xs[a2]);
+        }
         AccT sum = (s0 + s1) + (s2 + s3);
         if constexpr (V > 1) sum = group_sum<V>(sum, mask);
         if (lane == 0) Ps[r] = sum;
