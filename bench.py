@@ -904,6 +904,35 @@ def _dist():
     return ws, rank, local
 
 
+def collectives(ws, device):
+    """(barrier, max_over_ranks) for N replicas: with ws > 1 through the
+    initialised process group (NCCL on the GPU, gloo on the CPU in tests)."""
+    import torch
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        if device == "cuda":
+            torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            return float(t.item())
+        return v
+
+    return barrier, max_over_ranks
+
+
+def replica_value(ws, steps, work_per_step, total_ms):
+    """Whole-job throughput of ws replicas: the units all ranks processed over
+    the slowest rank's time."""
+    return ws * steps * work_per_step / (total_ms / 1000.0)
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -912,7 +941,7 @@ def run_reference(args):
     oracle.build()
     wl = WORKLOADS[args.workload](None, None)
     steps, warm = args.steps, args.warmup
-    budget = max(0.5, 120.0 / max(1, steps + warm))
+    budget = max(0.05, args.ref_seconds / max(1, steps + warm))
     vals, sample = [], ""
     for i in range(warm + steps):
         v, sample = wl.cpu_sample(budget)
@@ -950,17 +979,7 @@ def run_lilac(args):
         dist.barrier()
     L.load()
 
-    def barrier():
-        if ws > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(v):
-        if ws > 1:
-            t = torch.tensor([v], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return v
+    barrier, max_over_ranks = collectives(ws, "cuda")
 
     wl = WORKLOADS[args.workload](L, torch)
     wl.setup()
@@ -994,7 +1013,7 @@ def run_lilac(args):
     clk = clocks.stop() if clocks else None
     step_ms = [ev0[k].elapsed_time(ev1[k]) for k in range(K)]
     total_ms = max_over_ranks(sum(step_ms))
-    value = ws * K * wl.work_per_step / (total_ms / 1000.0)
+    value = replica_value(ws, K, wl.work_per_step, total_ms)
 
     # dominant kernel: CUDA events on its own stream
     kern_ms, n_kern, kern_bytes, kname = wl.roofline_sample(min(K, 5))
@@ -1053,6 +1072,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served", "marshal"],
                     default="cg75k")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=120.0,
+                    help="reference arm: total seconds of oracle work over all steps")
     ap.add_argument("--rmat-scale", type=int, default=22,
                     help="R-MAT scale of the pagerank22 workload (22 is the benchmark size)")
     ap.add_argument("--ir-precision", type=int, choices=[1, 2], default=2,
