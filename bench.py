@@ -137,8 +137,10 @@ def _kernel_name(M):
     info = M.info()
     w = info["vector_width"]
     return {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {w} lanes/row)",
-            3: f"spmv_staged_kernel ({w} lanes/row)", 4: f"spmv_merge_kernel ({w} lanes/row)",
-            5: f"spmv_slab_kernel ({w} lanes/row)"}.get(info["variant"], "spmv")
+            3: f"spmv_staged_kernel ({w} lanes/row)", 4: "spmv_merge_kernel",
+            5: "spmv_slab_kernel + slab_combine_kernel (sliced ELL over x slabs in shared memory)",
+            6: "spmv_jds_kernel", 7: "spmv_sell_kernel (sliced ELL, one lane per row)"
+            }.get(info["variant"], "spmv")
 
 
 # --- workloads ------------------------------------------------------------------
@@ -358,7 +360,7 @@ class PageRank22(Workload):
         torch, L = self.torch, self.L
         self.M = L.CsrMatrix.from_csr(self.A)
         self.xd = torch.empty(self.A.n, dtype=torch.float32, device="cuda")
-        self.launches_per_step = 1 + self.iters
+        self.launches_per_step = 1 + self.iters * self.M.info()["spmv_kernels"]
 
     def step(self):
         L = self.L
@@ -985,7 +987,8 @@ def run_lilac(args):
     wl.setup()
     if args.variant:
         name, _, width = args.variant.partition(":")
-        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6}
+        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6,
+                 "sell": 7}
         wl.M.set_variant(codes[name], int(width or 0))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None

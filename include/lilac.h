@@ -81,13 +81,22 @@ typedef enum {
                                  walks 8 consecutive path items, rows split between threads or
                                  CTAs are finished from carries; no lanes-per-row setting */
     LILAC_VARIANT_SLAB = 5,   /* column slabs, built once per matrix: one CTA per SM holds a
-                                 slab of x (up to 192 KB) in shared memory and streams that
-                                 slab's nonzeros of a run of rows; partial sums combined per
-                                 row.  Matrices with more than 64 slabs run STAGED */
-    LILAC_VARIANT_JDS = 6     /* jagged diagonal storage (Section 3.2), built once per matrix:
+                                 slab of x (up to 192 KB) in shared memory and runs a range of
+                                 that slab's sliced ELL chunks (each row's piece in the slab
+                                 summed by one lane); partial sums combined per row in slab
+                                 order.  Matrices with more than 64 slabs, or whose pieces pad
+                                 by more than a quarter, run STAGED */
+    LILAC_VARIANT_JDS = 6,    /* jagged diagonal storage (Section 3.2), built once per matrix:
                                  rows sorted by length, one thread per row, nonzero d of all
                                  rows stored together; on another value array (an FP32 copy)
                                  STAGED runs */
+    LILAC_VARIANT_SELL = 7    /* sliced ELL (chunks of 32 rows, element k of the chunk's 32
+                                 rows stored together), built once per matrix: one lane per row
+                                 with one fused multiply-add per nonzero; rows longer than a
+                                 piece cap are cut into pieces finished in piece order; rows
+                                 sorted by length when row order would pad much.  On another
+                                 value array (an FP32 copy), or where the copy would pad by more
+                                 than half, STAGED runs */
 } lilac_variant;
 
 /* lilac_csr_create flags.  By default create times the candidate SpMV
@@ -135,7 +144,8 @@ typedef struct {
     int64_t nnz;
     int32_t dtype;          /* lilac_dtype */
     int32_t variant;        /* lilac_variant in use */
-    int32_t vector_width;   /* lanes per row for VECTOR / STAGED */
+    int32_t vector_width;   /* lanes per row for VECTOR / STAGED; for SLAB / SELL, the
+                               STAGED width used on another value array */
     int32_t max_row_len;
     int32_t empty_rows;
     int32_t num_tiles;      /* STAGED: row tiles incl. long-row chunks */
@@ -145,16 +155,25 @@ typedef struct {
     double std_row_len;
     int64_t device_bytes;   /* device memory held by the handle right now */
     int64_t h2d_bytes;      /* bytes uploaded to the matrix so far (create + updates) */
+    int32_t active_variant; /* the kernel that runs on the handle's own values: `variant`, or
+                               STAGED where a SLAB / SELL / JDS copy does not suit the matrix */
+    int32_t sell_split_rows; /* SELL copy: rows cut into pieces (0 without a copy) */
+    int64_t sell_padded_nnz; /* SELL copy: stored elements including padding (0 without one) */
+    int32_t spmv_kernels;    /* kernels one SpMV with a reducing epilogue (CG, PageRank) launches
+                                on the handle's own values: 2 for SLAB (slab + combine) and for
+                                SELL on many sorted short rows (SpMV + row-order reduction) */
 } lilac_csr_info_t;
 
 /* Describe the handle.  Synchronous only on host state. */
 lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
 
-/* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR,
- * STAGED and SLAB, lanes per row (power of two 1..32; 0 keeps the current
- * one; SCALAR, MERGE and JDS use 1 whatever is passed).  Affects later calls.
- * Choosing SLAB or JDS builds the regrouped copy of the matrix on first use
- * (synchronous; errors OOM, CUDA). */
+/* Override the autotuner: variant (lilac_variant, not AUTO) and, for VECTOR
+ * and STAGED, lanes per row (power of two 1..32; 0 keeps the current one;
+ * SCALAR, MERGE and JDS use 1 whatever is passed; for SLAB and SELL it is the
+ * STAGED width used where they fall back to STAGED).  Affects later calls.
+ * Choosing SLAB, SELL or JDS builds that copy of the matrix on first use
+ * (synchronous; errors OOM, CUDA); a matrix the copy does not suit runs
+ * STAGED. */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
 
 /*

@@ -150,17 +150,48 @@ lilac_status launch_jds(lilac_csr_s* A, const typename Op::ValT* val, const type
     return LILAC_OK;
 }
 
-// SLAB: one CTA per SM holding a slab of x in shared memory (lilac_slab.cu
-// builds the regrouped copy).  The copy holds the handle's own values; another
-// value array (an FP32 copy) goes to STAGED, as does a handle without a copy.
+// STAGED at the handle's lanes per row: where a copy-based variant (SLAB,
+// SELL) falls back, vector_width keeps the STAGED width to use.
+template <class Op>
+lilac_status prepare_staged_any(lilac_csr_s* A) {
+    switch (A->vwidth) {
+        case 1: return prepare_staged<1, Op>(A);
+        case 2: return prepare_staged<2, Op>(A);
+        case 4: return prepare_staged<4, Op>(A);
+        case 8: return prepare_staged<8, Op>(A);
+        case 16: return prepare_staged<16, Op>(A);
+        default: return prepare_staged<32, Op>(A);
+    }
+}
+
+template <class Op>
+lilac_status launch_staged_any(lilac_csr_s* A, const typename Op::ValT* val,
+                               const typename Op::VecT* x, const Op& op, cudaStream_t stream) {
+    switch (A->vwidth) {
+        case 1: return launch_staged<1, Op>(A, val, x, op, stream);
+        case 2: return launch_staged<2, Op>(A, val, x, op, stream);
+        case 4: return launch_staged<4, Op>(A, val, x, op, stream);
+        case 8: return launch_staged<8, Op>(A, val, x, op, stream);
+        case 16: return launch_staged<16, Op>(A, val, x, op, stream);
+        default: return launch_staged<32, Op>(A, val, x, op, stream);
+    }
+}
+
+// Elements in flight per lane in the sliced ELL kernels.
+constexpr int kSellUnroll = 8;
+
+// SLAB: one CTA per SM holding a slab of x in shared memory (lilac_sell.cu
+// builds the sliced ELL copy of every slab).  The copy holds the handle's own
+// values; another value array (an FP32 copy) goes to STAGED, as does a handle
+// without a copy.
 template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
     int& bps = bps_slot<V + 64, Op, true>(A->device);
     if (bps == 0) {
-        auto kern = spmv_slab_kernel<V, kSlabThreads, typename Op::ValT, typename Op::VecT,
+        auto kern = spmv_slab_kernel<kSlabThreads, kSellUnroll, typename Op::ValT, typename Op::VecT,
                                      typename Op::AccT>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            kSlabMaxBytes));
+                                            kSlabMaxBytes + 64));
         bps = 1;
     }
     return LILAC_OK;
@@ -169,13 +200,14 @@ lilac_status prepare_slab(lilac_csr_s* A) {
 template <int V, class Op>
 lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    if (!A->slab_built || (const void*)val != A->val.p) return launch_staged<V, Op>(A, val, x, op, stream);
+    if (!A->slab_built || (const void*)val != A->val.p) return launch_staged_any<Op>(A, val, x, op, stream);
     LILAC_TRY(prepare_slab<V, Op>(A));
     using AccT = typename Op::AccT;
-    const size_t smem = sizeof(typename Op::VecT) * (size_t)A->slab_W;
-    spmv_slab_kernel<V, kSlabThreads, typename Op::ValT, typename Op::VecT, AccT>
+    // the slab and the zero after it, in 16-byte units
+    const size_t smem = (sizeof(typename Op::VecT) * ((size_t)A->slab_W + 1) + 15) & ~size_t(15);
+    spmv_slab_kernel<kSlabThreads, kSellUnroll, typename Op::ValT, typename Op::VecT, AccT>
         <<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
-            A->slab_rp.as<int>(), A->slab_rp_stride, A->slab_col.as<uint16_t>(),
+            A->slab_cptr.as<int>(), A->slab_crow.as<int>(), A->slab_col.as<uint16_t>(),
             A->slab_val.as<typename Op::ValT>(), A->slab_ctas.as<int4>(), A->rows, A->ncols,
             A->slab_W, x, A->slab_P.as<AccT>());
     LILAC_CUDA_TRY(cudaGetLastError());
@@ -185,20 +217,86 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
     return LILAC_OK;
 }
 
-#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, FN_JDS, ...) \
+// SELL: the sliced ELL copy (lilac_sell.cu) with x gathered through L1/L2;
+// split rows finish through the copy's own piece sums and counters.  Another
+// value array (an FP32 copy) goes to STAGED, as does a handle without a copy.
+constexpr int kSellThreads = 256;
+
+// A two-phase epilogue with reductions runs as store + rows_reduce_kernel on
+// a copy whose rows are sorted and many (sell_two_pass): reading x[row] and
+// friends in sorted row order would scatter.
+template <class Op>
+bool sell_split_epilogue(const lilac_csr_s* A) {
+    return Op::kTwoPhase && Op::NR > 0 && A->sell_two_pass;
+}
+
+template <int V, class Op>
+lilac_status prepare_sell(lilac_csr_s* A) {
+    int& bps = bps_slot<V + 256, Op, false>(A->device);
+    if (bps == 0) {
+        auto k1 = spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op>;
+        // no shared memory: the unified array goes to L1, which caches x
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        int b = occupancy_per_sm(k1, kSellThreads, 0);
+        if constexpr (Op::kTwoPhase && Op::NR > 0) {
+            auto k2 = spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op>;
+            LILAC_CUDA_TRY(cudaFuncSetAttribute(k2, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+            b = std::min(b, occupancy_per_sm(k2, kSellThreads, 0));
+        }
+        bps = b;
+    }
+    return prepare_staged_any<Op>(A);
+}
+
+template <int V, class Op>
+lilac_status launch_sell(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                         const Op& op, cudaStream_t stream) {
+    if (!A->sell_built || (const void*)val != A->val.p) return launch_staged_any<Op>(A, val, x, op, stream);
+    LILAC_TRY(prepare_sell<V, Op>(A));
+    const int bps = bps_slot<V + 256, Op, false>(A->device);
+    constexpr int kWarps = kSellThreads / 32;
+    int64_t grid = (int64_t)A->sm_count * bps;
+    const int64_t need = ((int64_t)A->sell_nchunks + kWarps - 1) / kWarps;
+    if (grid > need) grid = need;
+    if (grid > kMaxCtas) grid = kMaxCtas;
+    if (grid < 1) grid = 1;
+    SellView view{A->sell_cptr.as<int>(), A->sell_crow.as<int>(), A->sell_col.as<int>(),
+                  A->sell_splits.as<int4>(), A->sell_piece_split.as<int>(), A->sell_nchunks,
+                  A->sell_nsplit};
+    Scratch sc = A->scratch();
+    sc.long_part = A->sell_part.as<double>();
+    sc.long_red = A->sell_red.as<double>();
+    sc.long_cnt = A->sell_cnt.as<unsigned>();
+    if constexpr (Op::kTwoPhase && Op::NR > 0) {
+        if (sell_split_epilogue<Op>(A)) {
+            spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op>
+                <<<(unsigned)grid, kSellThreads, 0, stream>>>(view, A->sell_val.as<typename Op::ValT>(),
+                                                              x, op, sc);
+            LILAC_CUDA_TRY(cudaGetLastError());
+            rows_reduce_kernel<kVecThreads, Op><<<vec_grid(A, A->rows), kVecThreads, 0, stream>>>(
+                A->rows, op, A->scratch());
+            LILAC_CUDA_TRY(cudaGetLastError());
+            return LILAC_OK;
+        }
+    }
+    {
+        spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op><<<(unsigned)grid, kSellThreads, 0, stream>>>(
+            view, A->sell_val.as<typename Op::ValT>(), x, op, sc);
+    }
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, FN_JDS, FN_SELL, ...) \
     switch (A->variant) {                                                   \
+        case LILAC_VARIANT_SELL: /* one lane per row piece */               \
+            return FN_SELL<1, Op>(__VA_ARGS__);                             \
         case LILAC_VARIANT_MERGE: /* thread-sequential: no lanes per row */ \
             return FN_MERGE<1, Op>(__VA_ARGS__);                            \
         case LILAC_VARIANT_JDS: /* one thread per row */                    \
             return FN_JDS<1, Op>(__VA_ARGS__);                              \
-        case LILAC_VARIANT_SLAB:                                            \
-            switch (A->vwidth) {                                            \
-                case 1: return FN_SLAB<1, Op>(__VA_ARGS__);                 \
-                case 2: return FN_SLAB<2, Op>(__VA_ARGS__);                 \
-                case 4: return FN_SLAB<4, Op>(__VA_ARGS__);                 \
-                case 8: return FN_SLAB<8, Op>(__VA_ARGS__);                 \
-                default: return FN_SLAB<16, Op>(__VA_ARGS__);               \
-            }                                                               \
+        case LILAC_VARIANT_SLAB: /* one lane per row piece */               \
+            return FN_SLAB<1, Op>(__VA_ARGS__);                             \
         case LILAC_VARIANT_SCALAR:                                          \
             return FN_ROWS<1, Op>(__VA_ARGS__);                             \
         case LILAC_VARIANT_VECTOR:                                          \
@@ -225,26 +323,31 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
 template <int V, class Op>
 lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
     LILAC_TRY(prepare_slab<V, Op>(A));
-    return prepare_staged<V, Op>(A);
+    return prepare_staged_any<Op>(A);
 }
 
-// Kernel launches one SpMV of the handle's variant makes with value array
-// `val` (SLAB: the slab kernel and the combine kernel).
-inline int spmv_launch_count(const lilac_csr_s* A, const void* val) {
-    return A->variant == LILAC_VARIANT_SLAB && A->slab_built && val == A->val.p ? 2 : 1;
+// Kernel launches one SpMV with epilogue Op of the handle's variant makes
+// with value array `val` (SLAB: the slab kernel and the combine kernel; SELL
+// with a split epilogue: the SpMV and the row-order reduction).
+template <class Op>
+int spmv_launch_count(const lilac_csr_s* A, const void* val) {
+    if (val != A->val.p) return 1;
+    if (A->variant == LILAC_VARIANT_SLAB && A->slab_built) return 2;
+    if (A->variant == LILAC_VARIANT_SELL && A->sell_built && sell_split_epilogue<Op>(A)) return 2;
+    return 1;
 }
 
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
     LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge,
-                        prepare_jds, A)
+                        prepare_jds, prepare_sell, A)
 }
 
 template <class Op>
 lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
-    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, launch_jds, A, val,
-                        x, op, stream)
+    LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, launch_jds,
+                        launch_sell, A, val, x, op, stream)
 }
 
 // Replay `body` (which enqueues work on the stream it is given) as a CUDA

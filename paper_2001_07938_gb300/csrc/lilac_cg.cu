@@ -100,7 +100,7 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
             LILAC_TRY(start(cs));
             return enqueue_iters<V, T>(A, val, x, W, max_iter, cs, prof.on);
         }));
-        prof.kernels += 2 + (2 + spmv_launch_count(A, val)) * max_iter;
+        prof.kernels += 2 + (2 + spmv_launch_count<OpCgPq<V, T>>(A, val)) * max_iter;
         if (prof.on) {
             LILAC_CUDA_TRY(cudaStreamSynchronize(s));
             LILAC_TRY(collect_prof(A, max_iter, prof));
@@ -118,7 +118,7 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
             return enqueue_iters<V, T>(A, val, x, W, nit, cs, prof.on);
         }));
         done_iters += nit;
-        prof.kernels += (2 + spmv_launch_count(A, val)) * nit;
+        prof.kernels += (2 + spmv_launch_count<OpCgPq<V, T>>(A, val)) * nit;
         LILAC_CUDA_TRY(cudaMemcpyAsync(host_state, W.state.p, sizeof(CgState),
                                        cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -332,7 +332,8 @@ static lilac_status cg_mixed_ru_impl(lilac_csr A, const V* val, const double* b,
             return enqueue_iters_ru<V>(A, val32, val, b, x, d, W, nit, cs, prof.on);
         }));
         launched += nit;
-        prof.kernels += (3 + spmv_launch_count(A, val32) + spmv_launch_count(A, val)) * nit;
+        prof.kernels += (3 + spmv_launch_count<OpCgPq<float, float>>(A, val32) +
+                         spmv_launch_count<OpResidualRU<V>>(A, val)) * nit;
         LILAC_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
         if (prof.on) LILAC_TRY(collect_prof(A, nit, prof));

@@ -242,8 +242,10 @@ lilac::Scratch lilac_csr_s::scratch() const {
 
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
-                                  &slab_rp, &slab_col, &slab_val, &slab_perm, &slab_ctas,
-                                  &slab_P, &merge_coords, &merge_carries,
+                                  &slab_cptr, &slab_crow, &slab_col, &slab_val, &slab_perm,
+                                  &slab_ctas, &slab_P, &sell_cptr, &sell_crow, &sell_col,
+                                  &sell_val, &sell_splits, &sell_piece_split, &sell_part,
+                                  &sell_red, &sell_cnt, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
                                   &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
@@ -260,7 +262,7 @@ static lilac_status zero_scratch(lilac_csr A, cudaStream_t stream) {
                              &A->status};
     for (auto* b : bufs)
         if (b->p) LILAC_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, stream));
-    return LILAC_OK;
+    return sell_zero_counters(A, stream);
 }
 
 static lilac_status tune_timed(lilac_csr A, cudaStream_t stream);
@@ -412,15 +414,27 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
         for (int w : {4, 8, 16, 32}) cands.push_back({LILAC_VARIANT_VECTOR, w});
         cands.push_back({LILAC_VARIANT_SCALAR, 1});
     }
-    // SLAB (x slabs in shared memory) and JDS (one thread per row, rows sorted
-    // by length): their copies are built for the trial and kept only if they win
+    // SLAB (x slabs in shared memory), SELL (sliced ELL) and JDS (one thread
+    // per row, rows sorted by length): their copies are built for the trial
+    // and kept only if they win.  SLAB and SELL keep the heuristic's STAGED
+    // width for calls on another value array (an FP32 copy).
+    const int staged_w = std::min(pick_width(A->mean_row_len), 8);
     bool slab_trial = false;
     if (!A->slab_built && slab_worthwhile(A)) {
         if (ensure_slab(A, stream) == LILAC_OK && A->slab_built) {
             slab_trial = true;
-            for (int w : {1, 2, 4, 8}) cands.push_back({LILAC_VARIANT_SLAB, w});
+            cands.push_back({LILAC_VARIANT_SLAB, staged_w});
         } else {
             slab_release(A);
+        }
+    }
+    bool sell_trial = false;
+    if (!A->sell_built) {
+        if (ensure_sell(A, stream) == LILAC_OK && A->sell_built) {
+            sell_trial = true;
+            cands.push_back({LILAC_VARIANT_SELL, staged_w});
+        } else {
+            sell_release(A);
         }
     }
     bool jds_trial = false;
@@ -448,13 +462,19 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
                 st = launch_spmv(A, A->val.as<float>(), x.as<float>(), OpStore<float, float>{y.as<float>()}, stream);
         };
         run();  // warm-up
-        LILAC_CUDA_TRY(cudaEventRecord(e0, stream));
-        for (int it = 0; it < 3 && st == LILAC_OK; ++it) run();
-        LILAC_CUDA_TRY(cudaEventRecord(e1, stream));
-        LILAC_CUDA_TRY(cudaEventSynchronize(e1));
+        run();
+        // the faster of two rounds of three calls
+        float ms = 1e30f;
+        for (int round = 0; round < 2 && st == LILAC_OK; ++round) {
+            LILAC_CUDA_TRY(cudaEventRecord(e0, stream));
+            for (int it = 0; it < 3 && st == LILAC_OK; ++it) run();
+            LILAC_CUDA_TRY(cudaEventRecord(e1, stream));
+            LILAC_CUDA_TRY(cudaEventSynchronize(e1));
+            float t = 0.f;
+            LILAC_CUDA_TRY(cudaEventElapsedTime(&t, e0, e1));
+            ms = std::min(ms, t);
+        }
         if (st != LILAC_OK) continue;
-        float ms = 0.f;
-        LILAC_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
             best = ms;
             bestc = c;
@@ -465,10 +485,12 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     A->variant = bestc.variant;
     A->vwidth = bestc.width;
     if ((jds_trial && bestc.variant != LILAC_VARIANT_JDS) ||
-        (slab_trial && bestc.variant != LILAC_VARIANT_SLAB))
+        (slab_trial && bestc.variant != LILAC_VARIANT_SLAB) ||
+        (sell_trial && bestc.variant != LILAC_VARIANT_SELL))
         LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
     if (jds_trial && bestc.variant != LILAC_VARIANT_JDS) jds_release(A);
     if (slab_trial && bestc.variant != LILAC_VARIANT_SLAB) slab_release(A);
+    if (sell_trial && bestc.variant != LILAC_VARIANT_SELL) sell_release(A);
     return LILAC_OK;
 }
 
@@ -489,6 +511,7 @@ static void free_handle(lilac_csr A) {
     for (auto* b : all) b->release();
     jds_release(A);
     slab_release(A);
+    sell_release(A);
     delete A;
 }
 
@@ -546,6 +569,7 @@ lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem wh
     A->h2d_bytes += (int64_t)(vsz * (size_t)A->nnz);
     A->val32_valid = false;  // derived FP32 copy is stale
     LILAC_TRY(slab_refresh_values(A, s));
+    LILAC_TRY(sell_refresh_values(A, s));
     LILAC_TRY(jds_refresh_values(A, s));
     return LILAC_OK;
 }
@@ -578,6 +602,17 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) {
     info->std_row_len = A->std_row_len;
     info->device_bytes = A->device_bytes();
     info->h2d_bytes = A->h2d_bytes;
+    // the kernel that runs on the handle's own values: a copy-based variant
+    // whose copy is not built runs STAGED
+    int active = A->variant;
+    if ((active == LILAC_VARIANT_SLAB && !A->slab_built) ||
+        (active == LILAC_VARIANT_SELL && !A->sell_built) ||
+        (active == LILAC_VARIANT_JDS && !A->jds_built))
+        active = LILAC_VARIANT_STAGED;
+    info->active_variant = active;
+    info->sell_split_rows = A->sell_built ? A->sell_nsplit : 0;
+    info->sell_padded_nnz = A->sell_built ? A->sell_elems : 0;
+    info->spmv_kernels = active == LILAC_VARIANT_SLAB || (active == LILAC_VARIANT_SELL && A->sell_two_pass) ? 2 : 1;
     return LILAC_OK;
 }
 
@@ -586,7 +621,7 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
     }
-    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_JDS ||
+    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_SELL ||
         (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
                                (vector_width & (vector_width - 1)) != 0))) {
         set_last_error("unsupported variant / width");
@@ -599,6 +634,10 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
     if (variant == LILAC_VARIANT_JDS) {
         DeviceGuard g(A->device);
         LILAC_TRY(ensure_jds(A, nullptr));
+    }
+    if (variant == LILAC_VARIANT_SELL) {
+        DeviceGuard g(A->device);
+        LILAC_TRY(ensure_sell(A, nullptr));
     }
     A->variant = variant;
     if (vector_width) A->vwidth = vector_width;

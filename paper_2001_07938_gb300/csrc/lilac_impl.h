@@ -116,13 +116,24 @@ struct lilac_csr_s {
     // STAGED schedule
     lilac::DevBuf tiles, longs;
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
-    // SLAB regrouped copy (built on first use): per-slab row pointers (S rows
-    // of rp_stride ints), 16-bit local columns, values, the CSR index of each
-    // regrouped nonzero (value updates), CTA runs {slab, first row, end row, -},
-    // and the partial sums P (S x rows)
-    lilac::DevBuf slab_rp, slab_col, slab_val, slab_perm, slab_ctas, slab_P;
-    int slab_S = 0, slab_W = 0, slab_grid = 0, slab_rp_stride = 0;
+    // SLAB copy (built on first use): sliced ELL chunks of every slab's row
+    // pieces (chunk offsets, lane rows, 16-bit local columns, values), the CSR
+    // index of each element (-1: padding; value updates), CTA ranges
+    // {slab, first chunk, end chunk, -}, and the partial sums P (S x rows)
+    lilac::DevBuf slab_cptr, slab_crow, slab_col, slab_val, slab_perm, slab_ctas, slab_P;
+    int slab_S = 0, slab_W = 0, slab_grid = 0;
+    int64_t slab_elems = 0;
     bool slab_built = false;
+    // SELL copy (built on first use): chunk offsets, lane rows / pieces,
+    // columns (-1: padding), values, split rows {row, first piece, pieces, -},
+    // piece -> split row, and the split rows' piece sums, epilogue sums and
+    // arrival counters
+    lilac::DevBuf sell_cptr, sell_crow, sell_col, sell_val, sell_splits, sell_piece_split,
+        sell_part, sell_red, sell_cnt;
+    int sell_nchunks = 0, sell_nsplit = 0, sell_npieces = 0, sell_cap = 0, sell_sigma = 0;
+    int64_t sell_elems = 0;
+    bool sell_built = false;
+    bool sell_two_pass = false;  // sorted rows, many of them: reductions in a row-order pass
     // JDS copy (built on first use): slot -> row, row -> slot, slot lengths,
     // jagged diagonal offsets, columns and values in JDS order
     lilac::DevBuf jds_slot_row, jds_row_slot, jds_len, jds_ptr, jds_col, jds_val;
@@ -186,6 +197,10 @@ void jds_release(lilac_csr A);
 lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
 void slab_release(lilac_csr A);
 bool slab_worthwhile(const lilac_csr_s* A);
+lilac_status ensure_sell(lilac_csr A, cudaStream_t stream);
+lilac_status sell_refresh_values(lilac_csr A, cudaStream_t stream);
+void sell_release(lilac_csr A);
+lilac_status sell_zero_counters(lilac_csr A, cudaStream_t stream);
 lilac_status check_device_status(lilac_csr A, cudaStream_t stream);
 // Event pairs for timing SpMV launches (pair i = events 2i, 2i+1).
 lilac_status ensure_prof_events(lilac_csr A, int pairs);

@@ -355,28 +355,171 @@ __global__ void __launch_bounds__(THREADS)
 namespace lilac {
 
 // ---------------------------------------------------------------------------
-// SLAB kernels: x gathered from shared memory instead of through L1/L2.
-//
-// Random 8-byte gathers through L1 cost one tag lookup per distinct line
-// (about one per cycle per SM); gathers from shared memory cost one bank
-// access each, many per cycle.  The columns are cut into S slabs of W
-// columns (W * 8 bytes at most kSlabMaxBytes) and the matrix is regrouped
-// once (lilac_slab.cu) into S sub-matrices A_s (the nonzeros of each row
-// whose column lies in slab s, in CSR order, 16-bit local columns c - s W),
-// stored one after the other with their own row pointers.  CTA (s, g), one
-// per SM, loads slab s of x into shared memory and computes the row sums of
-// A_s x_s for its run of rows (runs of about equal nonzero count) into
-// P[s][row], V lanes per row with four nonzeros in flight per lane; the
-// combine kernel adds P over the slabs in slab order and runs the epilogue.
-template <int V, int THREADS, class ValT, class VecT, class AccT>
+// SELL kernels: a sliced ELLPACK copy of the matrix (SELL-C-sigma with C = 32,
+// built once per handle in lilac_sell.cu).  Chunk c holds 32 row pieces, one
+// per lane, padded to the longest; element k of lane l is at cptr[c] + 32 k + l,
+// so every load of a warp is one contiguous segment.  Each lane adds its piece
+// with one fused multiply-add per element in nonzero order and no shuffle
+// reductions: on GB300 a warp-wide FP64 FMA costs the same issue slot however
+// many lanes are active, so FP64 SpMV is bound by FMA issue as much as by HBM,
+// and the layout spends (almost) exactly one FMA per nonzero.
+
+// Global-x form.  crow[c * 32 + l] is the lane's row (>= 0), -1 (padding lane)
+// or -(2 + p) for piece p of a row longer than the piece cap: its sum goes to
+// part[p], and the last of the row's pieces to arrive (counter) adds them in
+// piece order and runs the epilogue.  Padding elements have column -1 (no
+// load; they add 0 * 0).
+struct SellView {
+    const int* __restrict__ cptr;         // [nchunks + 1]
+    const int* __restrict__ crow;         // [nchunks * 32]
+    const int* __restrict__ col;          // [cptr[nchunks]]
+    const int4* __restrict__ splits;      // per split row {row, first piece, pieces, -}
+    const int* __restrict__ piece_split;  // piece -> split row
+    int nchunks;
+    int nsplit;
+};
+
+template <bool kStoreOnly, class AccT, class Op>
+__device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& op, const Scratch& s,
+                                                  int p, AccT acc) {
+    constexpr int NR = kStoreOnly ? 0 : Op::NR;
+    s.long_part[p] = (double)acc;
+    __threadfence();
+    const int lid = S.piece_split[p];
+    const int4 sp = S.splits[lid];
+    const unsigned c = atomicAdd(&s.long_cnt[lid], 1u);
+    if (c == (unsigned)sp.z - 1u) {
+        __threadfence();
+        AccT rs = AccT(0);
+        for (int j = 0; j < sp.z; ++j) rs += AccT(__ldcg(&s.long_part[sp.y + j]));
+        if constexpr (kStoreOnly) {
+            op.store(sp.x, rs);
+        } else {
+            double lred[NR > 0 ? NR : 1] = {};
+            op.row(sp.x, rs, lred);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = lred[q];
+        }
+        s.long_cnt[lid] = 0u;
+        __threadfence();  // the epilogue sums before this CTA's grid-reduction ticket
+    }
+}
+
+// kStoreOnly (two-phase epilogues): rows are only stored; the reductions run
+// in row order in rows_reduce_kernel, which keeps their loads coalesced when
+// the rows are sorted by length.
+template <int THREADS, int UNR, bool kStoreOnly, class Op>
+__global__ void __launch_bounds__(THREADS)
+    spmv_sell_kernel(SellView S, const typename Op::ValT* __restrict__ val,
+                     const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
+    if (op.skip()) return;
+    op.begin();
+    using ValT = typename Op::ValT;
+    using VecT = typename Op::VecT;
+    using AccT = typename Op::AccT;
+    constexpr int NR = kStoreOnly ? 0 : Op::NR;
+    double red[NR > 0 ? NR : 1] = {};
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)(gridDim.x * (THREADS / 32));
+    for (int ch = (int)((blockIdx.x * THREADS + threadIdx.x) >> 5); ch < S.nchunks; ch += nwarps) {
+        const int base = __ldg(S.cptr + ch);
+        const int width = (__ldg(S.cptr + ch + 1) - base) >> 5;
+        const int who = __ldg(S.crow + (size_t)ch * 32 + lane);
+        const ValT* __restrict__ vp = val + base + lane;
+        const int* __restrict__ cp = S.col + base + lane;
+        AccT acc = AccT(0);
+        int k = 0;
+        for (; k + UNR <= width; k += UNR) {
+            ValT vv[UNR];
+            int cc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                vv[u] = ld_stream(vp + 32 * (k + u));
+                cc[u] = ld_stream(cp + 32 * (k + u));
+            }
+            VecT xx[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xx[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : VecT(0);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xx[u]);
+        }
+        if (k < width) {
+            // the last (fewer than UNR) elements, loads issued together; the
+            // bound is the same for the whole warp, so skipped FMAs cost nothing
+            ValT vv[UNR];
+            int cc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const bool q = k + u < width;
+                vv[u] = q ? ld_stream(vp + 32 * (k + u)) : ValT(0);
+                cc[u] = q ? ld_stream(cp + 32 * (k + u)) : -1;
+            }
+            VecT xx[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) xx[u] = cc[u] >= 0 ? __ldg(x + cc[u]) : VecT(0);
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (k + u < width) acc += AccT(vv[u]) * AccT(xx[u]);
+        }
+        if (who >= 0) {
+            if constexpr (kStoreOnly)
+                op.store(who, acc);
+            else
+                op.row(who, acc, red);
+        } else if (who < -1) {
+            sell_finish_piece<kStoreOnly, AccT>(S, op, s, -who - 2, acc);
+        }
+    }
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, S.nsplit);
+    }
+}
+
+// Second phase of a two-phase epilogue: op.reduce for every row, in row order,
+// then the grid sum.
+template <int THREADS, class Op>
+__global__ void __launch_bounds__(THREADS) rows_reduce_kernel(int rows, Op op, Scratch s) {
+    if (op.skip()) return;
+    op.begin();
+    constexpr int NR = Op::NR;
+    double red[NR > 0 ? NR : 1] = {};
+    for (int r = blockIdx.x * THREADS + threadIdx.x; r < rows; r += gridDim.x * THREADS)
+        op.reduce(r, red);
+    if constexpr (NR > 0) {
+        double r2[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SLAB kernel: the sliced ELL layout over column slabs, x read from shared
+// memory.  Random 8-byte gathers through L1 cost one tag lookup per distinct
+// line (about one per cycle per SM); from shared memory they cost one bank
+// access each.  The columns are cut into S slabs of W columns (x slab of at
+// most kSlabMaxBytes) and each slab's pieces of all rows (the nonzeros of the
+// row whose column lies in the slab, in CSR order, 16-bit local columns) form
+// their own sliced ELL chunks, rows sorted by piece length.  One CTA of
+// THREADS threads per SM loads slab s of x into shared memory (plus a zero at
+// index W that padding elements point to) and runs a range of that slab's
+// chunks, warps taking chunks from a shared counter; the lane's sum goes to
+// P[s][row].  The combine kernel adds P over the slabs in slab order and runs
+// the epilogue.
+template <int THREADS, int UNR, class ValT, class VecT, class AccT>
 __global__ void __launch_bounds__(THREADS, 1)
-    spmv_slab_kernel(const int* __restrict__ srp, int rp_stride, const uint16_t* __restrict__ scol,
-                     const ValT* __restrict__ sval, const int4* __restrict__ ctas, int rows,
-                     int ncols, int W, const VecT* __restrict__ x, AccT* __restrict__ P) {
+    spmv_slab_kernel(const int* __restrict__ cptr, const int* __restrict__ crow,
+                     const uint16_t* __restrict__ scol, const ValT* __restrict__ sval,
+                     const int4* __restrict__ ctas, int rows, int ncols, int W,
+                     const VecT* __restrict__ x, AccT* __restrict__ P) {
     extern __shared__ __align__(16) unsigned char slab_smem[];
+    __shared__ int next_chunk;
     VecT* xs = reinterpret_cast<VecT*>(slab_smem);
-    const int4 c = ctas[blockIdx.x];  // {slab, first row, end row, -}
-    const int sl = c.x, r0 = c.y, r1 = c.z;
+    const int4 c = ctas[blockIdx.x];  // {slab, first chunk, end chunk, -}
+    const int sl = c.x;
     const int c0 = sl * W;
     const int w = min(W, ncols - c0);
     {
@@ -397,44 +540,50 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (; i < nv; i += THREADS) xsv[i] = __ldg(xv + i);
         for (int j = nv * E + threadIdx.x; j < w; j += THREADS) xs[j] = __ldg(x + c0 + j);
+        for (int j = w + threadIdx.x; j <= W; j += THREADS) xs[j] = VecT(0);
     }
+    if (threadIdx.x == 0) next_chunk = c.y + THREADS / 32;
     __syncthreads();
-    const int* __restrict__ rp = srp + (size_t)sl * rp_stride;
-    const int lane = threadIdx.x & (V - 1);
-    const int group = threadIdx.x / V;
-    constexpr int NG = THREADS / V;
-    const unsigned mask = group_mask<V>(threadIdx.x);
+    const int lane = threadIdx.x & 31;
     AccT* __restrict__ Ps = P + (size_t)sl * rows;
-    for (int r = r0 + group; r < r1; r += NG) {
-        const int kb = __ldg(rp + r), ke = __ldg(rp + r + 1);
-        AccT s0 = AccT(0), s1 = AccT(0), s2 = AccT(0), s3 = AccT(0);
-        int k = kb + lane;
-        for (; k + 3 * V < ke; k += 4 * V) {
-            const int a0 = ld_stream(scol + k), a1 = ld_stream(scol + k + V);
-            const int a2 = ld_stream(scol + k + 2 * V), a3 = ld_stream(scol + k + 3 * V);
-            const ValT v0 = ld_stream(sval + k), v1 = ld_stream(sval + k + V);
-            const ValT v2 = ld_stream(sval + k + 2 * V), v3 = ld_stream(sval + k + 3 * V);
-            s0 += AccT(v0) * AccT(xs[a0]);
-            s1 += AccT(v1) * AccT(xs[a1]);
-            s2 += AccT(v2) * AccT(xs[a2]);
-            s3 += AccT(v3) * AccT(xs[a3]);
+    int ch = c.y + (int)(threadIdx.x >> 5);
+    while (ch < c.z) {
+        const int base = __ldg(cptr + ch);
+        const int width = (__ldg(cptr + ch + 1) - base) >> 5;
+        const int row = __ldg(crow + (size_t)ch * 32 + lane);
+        const ValT* __restrict__ vp = sval + base + lane;
+        const uint16_t* __restrict__ cp = scol + base + lane;
+        AccT acc = AccT(0);
+        int k = 0;
+        for (; k + UNR <= width; k += UNR) {
+            ValT vv[UNR];
+            int cc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                vv[u] = ld_stream(vp + 32 * (k + u));
+                cc[u] = ld_stream(cp + 32 * (k + u));
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
         }
-        {
-            // the last (at most three) nonzeros of this lane: loads issued together
-            const bool q0 = k < ke, q1 = k + V < ke, q2 = k + 2 * V < ke;
-            const int a0 = q0 ? ld_stream(scol + k) : 0;
-            const int a1 = q1 ? ld_stream(scol + k + V) : 0;
-            const int a2 = q2 ? ld_stream(scol + k + 2 * V) : 0;
-            const ValT w0 = q0 ? ld_stream(sval + k) : ValT(0);
-            const ValT w1 = q1 ? ld_stream(sval + k + V) : ValT(0);
-            const ValT w2 = q2 ? ld_stream(sval + k + 2 * V) : ValT(0);
-            s0 += AccT(w0) * AccT(xs[a0]);
-            s1 += AccT(w1) * AccT(xs[a1]);
-            s2 += AccT(w2) * AccT(xs[a2]);
+        if (k < width) {
+            // the last (fewer than UNR) elements, loads issued together
+            ValT vv[UNR];
+            int cc[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const bool q = k + u < width;
+                vv[u] = q ? ld_stream(vp + 32 * (k + u)) : ValT(0);
+                cc[u] = q ? (int)ld_stream(cp + 32 * (k + u)) : W;
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (k + u < width) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
         }
-        AccT sum = (s0 + s1) + (s2 + s3);
-        if constexpr (V > 1) sum = group_sum<V>(sum, mask);
-        if (lane == 0) Ps[r] = sum;
+        if (row >= 0) Ps[row] = acc;
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&next_chunk, 1);
+        ch = __shfl_sync(0xffffffffu, nx, 0);
     }
 }
 

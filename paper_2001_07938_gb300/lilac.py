@@ -31,10 +31,12 @@ LILAC_ERR_UNSUPPORTED = 10
 LILAC_F64, LILAC_F32 = 0, 1
 LILAC_MEM_HOST, LILAC_MEM_DEVICE = 0, 1
 LILAC_VARIANT_AUTO, LILAC_VARIANT_SCALAR, LILAC_VARIANT_VECTOR, LILAC_VARIANT_STAGED, \
-    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB, LILAC_VARIANT_JDS = 0, 1, 2, 3, 4, 5, 6
+    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB, LILAC_VARIANT_JDS, LILAC_VARIANT_SELL = \
+    0, 1, 2, 3, 4, 5, 6, 7
 LILAC_CREATE_NO_TUNE = 0x1
 
-VARIANT_NAMES = {1: "scalar", 2: "vector", 3: "staged", 4: "merge", 5: "slab"}
+VARIANT_NAMES = {1: "scalar", 2: "vector", 3: "staged", 4: "merge", 5: "slab", 6: "jds",
+                 7: "sell"}
 
 # every symbol include/lilac.h declares (checked by the tests)
 EXPORTS = (
@@ -65,7 +67,9 @@ class lilac_csr_info_t(ctypes.Structure):
                 ("empty_rows", ctypes.c_int32), ("num_tiles", ctypes.c_int32),
                 ("num_long_rows", ctypes.c_int32), ("sm_count", ctypes.c_int32),
                 ("mean_row_len", ctypes.c_double), ("std_row_len", ctypes.c_double),
-                ("device_bytes", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64)]
+                ("device_bytes", ctypes.c_int64), ("h2d_bytes", ctypes.c_int64),
+                ("active_variant", ctypes.c_int32), ("sell_split_rows", ctypes.c_int32),
+                ("sell_padded_nnz", ctypes.c_int64), ("spmv_kernels", ctypes.c_int32)]
 
 
 class lilac_cg_opts(ctypes.Structure):

@@ -58,5 +58,7 @@ def true_rel_residual(A, b, x):
     return float(np.linalg.norm(r) / np.linalg.norm(b))
 
 
+# (variant, lanes per row); for SLAB and SELL the width is the STAGED width
+# they fall back to where their copy is not built
 ALL_VARIANTS = ([(1, 1)] + [(2, w) for w in (2, 4, 8, 16, 32)] + [(3, w) for w in (1, 2, 4, 8, 16, 32)]
-                + [(4, 1)] + [(5, w) for w in (1, 2, 4, 8, 16)] + [(6, 1)])
+                + [(4, 1)] + [(5, 1), (5, 4)] + [(6, 1)] + [(7, 1), (7, 8)])

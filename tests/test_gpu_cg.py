@@ -31,7 +31,7 @@ def _solve(A, b, dtype=np.float64, **kw):
     return st, info, x
 
 
-@pytest.mark.parametrize("variant", [None, (1, 1), (2, 8), (3, 4)])
+@pytest.mark.parametrize("variant", [None, (1, 1), (2, 8), (3, 4), (4, 1), (7, 1)])
 def test_small_spd_converges_like_the_oracle(variant):
     A = inputs.spd_random(3000, 12, 20.0, 4)
     b = inputs.uniform(5, A.n)
@@ -50,6 +50,30 @@ def test_small_spd_converges_like_the_oracle(variant):
     assert true_rel_residual(A, b, x) <= 1e-10
     assert info.true_rel_res <= 1e-10
     assert np.linalg.norm(x - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
+def test_sell_split_epilogue_cg_matches_single_pass():
+    """SELL with the p.q reduction in a row-order pass (many short sorted
+    rows) converges like the oracle and, run twice, bitwise alike."""
+    A = inputs.spd_random(70000, 10, 20.0, 6)
+    b = inputs.uniform(7, A.n)
+    torch = torch_cuda()
+    M = L.CsrMatrix.from_csr(A)
+    M.set_variant(L.LILAC_VARIANT_SELL, 1)
+    info = M.info()
+    assert info["active_variant"] == L.LILAC_VARIANT_SELL and info["spmv_kernels"] == 2
+    xs = []
+    for _ in range(2):
+        bd, xd = dev(b), torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st, inf = M.cg(bd, xd, rtol=1e-10, max_iter=500)
+        torch.cuda.synchronize()
+        assert st == L.LILAC_OK
+        xs.append(host(xd))
+    M.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    _, itr, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=500, rtol=1e-10)
+    assert abs(inf.iters - itr) <= 1
+    assert true_rel_residual(A, b, xs[0]) <= 1e-10
 
 
 def test_laplacian_converges_and_eigenmode_in_one_step():

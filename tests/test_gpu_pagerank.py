@@ -38,6 +38,26 @@ def test_small_rmat_fp32_all_variants(variant):
     assert abs(x.astype(np.float64).sum() - xr.sum()) <= 1e-5
 
 
+def test_sell_split_epilogue_on_many_sorted_rows():
+    """SELL on a graph with many short rows sorted by length stores the rows
+    in one kernel and takes the L1 / dangling sums in a row-order pass."""
+    A = inputs.rmat_transposed(17, 8, seed=5)
+    xr, l1r = oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=20)
+    torch = torch_cuda()
+    M = L.CsrMatrix.from_csr(A)
+    M.set_variant(L.LILAC_VARIANT_SELL, 1)
+    info = M.info()
+    assert info["active_variant"] == L.LILAC_VARIANT_SELL and info["spmv_kernels"] == 2
+    assert info["sell_split_rows"] > 0
+    x = torch.empty(A.n, dtype=torch.float32, device="cuda")
+    l1 = M.pagerank(x, iters=20)
+    torch.cuda.synchronize()
+    x = host(x).astype(np.float64)
+    M.close()
+    assert np.abs(x - xr).sum() <= 1e-5
+    np.testing.assert_allclose(l1, l1r, rtol=1e-4, atol=1e-6)
+
+
 def test_fp64_pagerank_matches_oracle_tightly():
     A = inputs.rmat_transposed(12, 8, seed=4)
     xr, l1r = oracle.pagerank(A.row_ptr, A.col_ind, A.vals.astype(np.float64), iters=30)

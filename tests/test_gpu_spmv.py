@@ -131,6 +131,63 @@ def test_one_huge_row_and_tiny_shapes():
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_sell_row_order_sorted_and_split_rows(dtype):
+    """SELL: a stencil keeps row order, irregular rows are sorted by length,
+    and rows longer than the piece cap are cut into pieces that are finished
+    in piece order (powerlaw rows up to ~60,000 nonzeros)."""
+    cases = [(inputs.laplacian2d(97), False), (inputs.random_csr(3000, 2500, 40, 0.2, seed=5), False),
+             (inputs.powerlaw_csr(6000, 9000, 60000, power=8, seed=3), True)]
+    for A, split in cases:
+        Ad = A.astype(dtype)
+        M = L.CsrMatrix.from_csr(Ad, flags=L.LILAC_CREATE_NO_TUNE)
+        M.set_variant(L.LILAC_VARIANT_SELL, 1)
+        info = M.info()
+        assert info["active_variant"] == L.LILAC_VARIANT_SELL, A.name
+        assert (info["sell_split_rows"] > 0) == split
+        assert A.nnz <= info["sell_padded_nnz"] <= 1.5 * A.nnz + 64 * (A.n // 32 + 1)
+        x = inputs.uniform(21, A.ncols, dtype=dtype)
+        y1 = _run(M, x, dtype)
+        assert_spmv_close(Ad, x.astype(np.float64), y1, dtype == np.float32, f"sell {A.name}")
+        np.testing.assert_array_equal(_run(M, x, dtype), y1)  # fixed order: reproducible
+        M.close()
+
+
+@pytest.mark.parametrize("variant", [5, 7])
+def test_slab_and_sell_padding_ignore_nonfinite_x_and_follow_updates(variant):
+    """Padding elements contribute nothing even where x holds inf / nan (a
+    padding slot never reads a caller's x), and value updates reach the copy."""
+    torch = torch_cuda()
+    A = inputs.spd_random(20000, 30, 20.0, 2)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(variant, 4)
+    assert M.info()["active_variant"] == variant
+    x = inputs.uniform(4, A.n)
+    assert_spmv_close(A, x, _run(M, x, np.float64), False, f"variant {variant}")
+    # x[j] = inf for a column that few rows reference: the others stay finite
+    counts = np.bincount(A.col_ind, minlength=A.n)
+    j = int(np.argmin(np.where(counts > 0, counts, 1 << 30)))
+    xi = x.copy()
+    xi[j] = np.inf
+    y = _run(M, xi, np.float64)
+    touches = np.zeros(A.n, bool)
+    rows = np.repeat(np.arange(A.n), np.diff(A.row_ptr))
+    touches[rows[A.col_ind == j]] = True
+    ref = oracle.spmv(A.row_ptr, A.col_ind, A.vals, np.where(np.isfinite(xi), xi, 0.0))
+    assert np.all(np.isfinite(y[~touches]))
+    assert np.all(~np.isfinite(y[touches]))
+    tol = 1e-12 * oracle.spmv_abs_bound(A.row_ptr, A.col_ind, A.vals, x)
+    assert np.all(np.abs(y[~touches] - ref[~touches]) <= tol[~touches])
+    # new values reach the copy
+    v2 = inputs.uniform(6, A.nnz)
+    L.lilac_csr_update_values(M.handle, v2.ctypes.data, L.LILAC_MEM_HOST)
+    torch.cuda.synchronize()
+    A2 = inputs.CSR(A.n, A.ncols, A.row_ptr, A.col_ind, v2)
+    assert M.info()["active_variant"] == variant
+    assert_spmv_close(A2, x, _run(M, x, np.float64), False, f"variant {variant} after update")
+    M.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_merge_empty_runs_and_rows_across_ctas(dtype):
     """MERGE: runs of empty rows longer than a CTA's path range, rows whose
     nonzeros span many sub-tiles and CTAs, tiny rows between them, an empty
@@ -219,7 +276,7 @@ def test_autotuner_timed_and_heuristic_choices_are_valid():
     for flags in (0, L.LILAC_CREATE_NO_TUNE):
         M = L.CsrMatrix.from_csr(A, flags=flags)
         info = M.info()
-        assert info["variant"] in (1, 2, 3)
+        assert info["variant"] in ((1, 2, 3) if flags else (1, 2, 3, 4, 5, 6, 7))
         assert_spmv_close(A, x, _run(M, x, np.float64), False, f"tuned flags={flags}")
         M.close()
 
@@ -240,6 +297,10 @@ def test_full_spd_75k_fp64():
     x = inputs.uniform(7, A.n)
     M = L.CsrMatrix.from_csr(A)
     assert_spmv_close(A, x, _run(M, x, np.float64), False, "spd 75k")
+    for var in (L.LILAC_VARIANT_SLAB, L.LILAC_VARIANT_SELL):
+        M.set_variant(var, 4)
+        assert M.info()["active_variant"] == var
+        assert_spmv_close(A, x, _run(M, x, np.float64), False, f"spd 75k variant {var}")
     M.close()
 
 
@@ -250,6 +311,10 @@ def test_full_rmat22_fp32():
     M = L.CsrMatrix.from_csr(A)
     assert M.info()["num_long_rows"] > 0
     assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "rmat 22")
+    M.set_variant(L.LILAC_VARIANT_SELL, 1)
+    info = M.info()
+    assert info["active_variant"] == L.LILAC_VARIANT_SELL and info["sell_split_rows"] > 0
+    assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "rmat 22 sell")
     M.close()
 
 
@@ -260,4 +325,7 @@ def test_full_laplacian3d_192_fp32():
     x = inputs.uniform(9, A.n, dtype=np.float32)
     M = L.CsrMatrix.from_csr(A)
     assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "laplacian3d 192")
+    M.set_variant(L.LILAC_VARIANT_SELL, 1)
+    assert M.info()["active_variant"] == L.LILAC_VARIANT_SELL
+    assert_spmv_close(A, x.astype(np.float64), _run(M, x, np.float32), True, "laplacian3d 192 sell")
     M.close()
