@@ -138,7 +138,7 @@ def _kernel_name(M):
     w = info["vector_width"]
     return {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {w} lanes/row)",
             3: f"spmv_staged_kernel ({w} lanes/row)", 4: "spmv_merge_kernel",
-            5: "spmv_slab_kernel + slab_combine_kernel (sliced ELL over x slabs in shared memory)",
+            5: "spmv_slab_kernel (sliced ELL over x slabs in shared memory, slabs combined per row group)",
             6: "spmv_jds_kernel", 7: "spmv_sell_kernel (sliced ELL, one lane per row)"
             }.get(info["variant"], "spmv")
 

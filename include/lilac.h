@@ -81,11 +81,12 @@ typedef enum {
                                  walks 8 consecutive path items, rows split between threads or
                                  CTAs are finished from carries; no lanes-per-row setting */
     LILAC_VARIANT_SLAB = 5,   /* column slabs, built once per matrix: one CTA per SM holds a
-                                 slab of x (up to 192 KB) in shared memory and runs a range of
-                                 that slab's sliced ELL chunks (each row's piece in the slab
-                                 summed by one lane); partial sums combined per row in slab
-                                 order.  Matrices with more than 64 slabs, or whose pieces pad
-                                 by more than a quarter, run STAGED */
+                                 slab of x (up to 192 KB) in shared memory and runs the sliced
+                                 ELL chunks of that slab's pieces of one group of rows (each
+                                 row's piece summed by one lane); the last of a group's CTAs
+                                 adds the pieces in slab order and runs the epilogue.
+                                 Matrices with more than 64 slabs, or whose pieces pad by more
+                                 than a quarter, run STAGED */
     LILAC_VARIANT_JDS = 6,    /* jagged diagonal storage (Section 3.2), built once per matrix:
                                  rows sorted by length, one thread per row, nonzero d of all
                                  rows stored together; on another value array (an FP32 copy)
@@ -160,8 +161,8 @@ typedef struct {
     int32_t sell_split_rows; /* SELL copy: rows cut into pieces (0 without a copy) */
     int64_t sell_padded_nnz; /* SELL copy: stored elements including padding (0 without one) */
     int32_t spmv_kernels;    /* kernels one SpMV with a reducing epilogue (CG, PageRank) launches
-                                on the handle's own values: 2 for SLAB (slab + combine) and for
-                                SELL on many sorted short rows (SpMV + row-order reduction) */
+                                on the handle's own values: 2 for SELL on many sorted short rows
+                                (SpMV + row-order reduction), else 1 */
 } lilac_csr_info_t;
 
 /* Describe the handle.  Synchronous only on host state. */

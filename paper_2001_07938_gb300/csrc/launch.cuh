@@ -181,15 +181,14 @@ lilac_status launch_staged_any(lilac_csr_s* A, const typename Op::ValT* val,
 constexpr int kSellUnroll = 8;
 
 // SLAB: one CTA per SM holding a slab of x in shared memory (lilac_sell.cu
-// builds the sliced ELL copy of every slab).  The copy holds the handle's own
-// values; another value array (an FP32 copy) goes to STAGED, as does a handle
-// without a copy.
+// builds the sliced ELL copy of every slab and row group).  The copy holds the
+// handle's own values; another value array (an FP32 copy) goes to STAGED, as
+// does a handle without a copy.
 template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
     int& bps = bps_slot<V + 64, Op, true>(A->device);
     if (bps == 0) {
-        auto kern = spmv_slab_kernel<kSlabThreads, kSellUnroll, typename Op::ValT, typename Op::VecT,
-                                     typename Op::AccT>;
+        auto kern = spmv_slab_kernel<kSlabThreads, kSellUnroll, Op>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSlabMaxBytes + 64));
         bps = 1;
@@ -202,17 +201,14 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
                          const Op& op, cudaStream_t stream) {
     if (!A->slab_built || (const void*)val != A->val.p) return launch_staged_any<Op>(A, val, x, op, stream);
     LILAC_TRY(prepare_slab<V, Op>(A));
-    using AccT = typename Op::AccT;
     // the slab and the zero after it, in 16-byte units
     const size_t smem = (sizeof(typename Op::VecT) * ((size_t)A->slab_W + 1) + 15) & ~size_t(15);
-    spmv_slab_kernel<kSlabThreads, kSellUnroll, typename Op::ValT, typename Op::VecT, AccT>
-        <<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
-            A->slab_cptr.as<int>(), A->slab_crow.as<int>(), A->slab_col.as<uint16_t>(),
-            A->slab_val.as<typename Op::ValT>(), A->slab_ctas.as<int4>(), A->rows, A->ncols,
-            A->slab_W, x, A->slab_P.as<AccT>());
-    LILAC_CUDA_TRY(cudaGetLastError());
-    slab_combine_kernel<kVecThreads, Op><<<vec_grid(A, A->rows), kVecThreads, 0, stream>>>(
-        A->rows, A->slab_S, A->slab_P.as<AccT>(), op, A->scratch());
+    SlabView view{A->slab_cptr.as<int>(), A->slab_crow.as<int>(), A->slab_col.as<uint16_t>(),
+                  A->slab_ctas.as<int4>(), A->slab_groups.as<int2>(), A->slab_gcnt.as<unsigned>(),
+                  A->rows, A->ncols, A->slab_W, A->slab_S, A->slab_G};
+    spmv_slab_kernel<kSlabThreads, kSellUnroll, Op><<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
+        view, A->slab_val.as<typename Op::ValT>(), x, A->slab_P.as<typename Op::AccT>(), op,
+        A->scratch());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
 }
@@ -327,12 +323,11 @@ lilac_status prepare_slab_and_staged(lilac_csr_s* A) {
 }
 
 // Kernel launches one SpMV with epilogue Op of the handle's variant makes
-// with value array `val` (SLAB: the slab kernel and the combine kernel; SELL
-// with a split epilogue: the SpMV and the row-order reduction).
+// with value array `val` (SELL with a split epilogue: the SpMV and the
+// row-order reduction).
 template <class Op>
 int spmv_launch_count(const lilac_csr_s* A, const void* val) {
     if (val != A->val.p) return 1;
-    if (A->variant == LILAC_VARIANT_SLAB && A->slab_built) return 2;
     if (A->variant == LILAC_VARIANT_SELL && A->sell_built && sell_split_epilogue<Op>(A)) return 2;
     return 1;
 }

@@ -243,7 +243,7 @@ lilac::Scratch lilac_csr_s::scratch() const {
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
                                   &slab_cptr, &slab_crow, &slab_col, &slab_val, &slab_perm,
-                                  &slab_ctas, &slab_P, &sell_cptr, &sell_crow, &sell_col,
+                                  &slab_ctas, &slab_groups, &slab_gcnt, &slab_P, &sell_cptr, &sell_crow, &sell_col,
                                   &sell_val, &sell_splits, &sell_piece_split, &sell_part,
                                   &sell_red, &sell_cnt, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
@@ -259,7 +259,7 @@ int64_t lilac_csr_s::device_bytes() const {
 
 static lilac_status zero_scratch(lilac_csr A, cudaStream_t stream) {
     lilac::DevBuf* bufs[] = {&A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
-                             &A->status};
+                             &A->status, &A->slab_gcnt};
     for (auto* b : bufs)
         if (b->p) LILAC_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, stream));
     return sell_zero_counters(A, stream);
@@ -612,7 +612,7 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) {
     info->active_variant = active;
     info->sell_split_rows = A->sell_built ? A->sell_nsplit : 0;
     info->sell_padded_nnz = A->sell_built ? A->sell_elems : 0;
-    info->spmv_kernels = active == LILAC_VARIANT_SLAB || (active == LILAC_VARIANT_SELL && A->sell_two_pass) ? 2 : 1;
+    info->spmv_kernels = active == LILAC_VARIANT_SELL && A->sell_two_pass ? 2 : 1;
     return LILAC_OK;
 }
 

@@ -170,6 +170,65 @@ __device__ __forceinline__ T block_sum_all(T v, T* sh) {
 
 // Scratch memory a launch uses for cross-CTA work.  Counters are zero
 // between launches (each user resets what it incremented).
+// Per-thread accumulators of the FP64 grid sums.  FP64 work is scarce on
+// GB300 (a warp-wide FP64 add or conversion takes an FP64 issue slot), so
+// epilogues over FP32 vectors sum per thread in compensated FP32 instead:
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2) keeps the rounding error of every
+// addition and TwoProduct (an FMA gives the exact error of a product) that of
+// every product, as in the Sum2 / Dot2 algorithms of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SISC 2005): the thread's sum is as
+// accurate as one computed in twice the working precision.  The pair becomes
+// one FP64 value per thread; sums across threads and CTAs stay FP64.
+struct CompF32 {
+    float s = 0.0f, c = 0.0f;
+    __device__ __forceinline__ void add(float a) {
+        const float t = __fadd_rn(s, a);
+        const float z = __fsub_rn(t, s);
+        c += __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(a, z));
+        s = t;
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        const float p = __fmul_rn(a, b);      // not contracted into a later add
+        const float e = __fmaf_rn(a, b, -p);  // exact: a b = p + e
+        add(p);
+        c += e;
+    }
+    // |a - b| exactly as d + e (d = fl(a - b), e its rounding error; |e| <=
+    // ulp(d) / 2, so d + e has the sign of d, and d = 0 only when a == b)
+    __device__ __forceinline__ void add_absdiff(float a, float b) {
+        const float d = __fsub_rn(a, b);
+        const float z = __fsub_rn(d, a);
+        const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(d, z)), __fsub_rn(-b, z));
+        if (d < 0.0f) {
+            add(-d);
+            c -= e;
+        } else {
+            add(d);
+            c += e;
+        }
+    }
+};
+
+__device__ __forceinline__ double red_value(double v) { return v; }
+__device__ __forceinline__ double red_value(const CompF32& v) { return double(v.s) + double(v.c); }
+
+// FP64 accumulation for FP64 vectors, compensated FP32 for FP32 vectors.
+template <class T>
+struct RedOf {
+    using type = double;
+};
+template <>
+struct RedOf<float> {
+    using type = CompF32;
+};
+
+__device__ __forceinline__ void red_add(double& r, double a) { r += a; }
+__device__ __forceinline__ void red_add(CompF32& r, float a) { r.add(a); }
+__device__ __forceinline__ void red_add_prod(double& r, double a, double b) { r += a * b; }
+__device__ __forceinline__ void red_add_prod(CompF32& r, float a, float b) { r.add_prod(a, b); }
+__device__ __forceinline__ void red_add_absdiff(double& r, double a, double b) { r += fabs(a - b); }
+__device__ __forceinline__ void red_add_absdiff(CompF32& r, float a, float b) { r.add_absdiff(a, b); }
+
 struct Scratch {
     double* partials;         // [max_ctas * kMaxRed] per-CTA partial sums
     double* long_part;        // [num_long_chunks] partial sums of split rows
@@ -212,6 +271,42 @@ __device__ __forceinline__ void grid_reduce_finish(const Op& op, const double (&
     for (int i = threadIdx.x; i < num_long; i += THREADS) {
 #pragma unroll
         for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&s.long_red[i * kMaxRed + q]);
+    }
+    block_sum<NR, THREADS>(acc, tot, sh);
+    if (threadIdx.x == 0) {
+        op.finish(tot);
+        *s.ticket = 0u;
+    }
+}
+
+// Like grid_reduce_finish, but a CTA publishes its sums to partial slot
+// `slot` (none if negative) and the last CTA adds slots 0 .. nslots - 1 in
+// order: the order is fixed even when which CTA fills a slot is not.
+template <int NR, int THREADS, class Op>
+__device__ __forceinline__ void grid_reduce_slots(const Op& op, const double (&red)[NR],
+                                                  const Scratch& s, int slot, int nslots) {
+    __shared__ double sh[kMaxRed * 32];
+    __shared__ int am_last;
+    double tot[NR];
+    block_sum<NR, THREADS>(red, tot, sh);
+    if (threadIdx.x == 0) {
+        if (slot >= 0) {
+#pragma unroll
+            for (int q = 0; q < NR; ++q) s.partials[slot * NR + q] = tot[q];
+        }
+        __threadfence();
+        const unsigned t = atomicAdd(s.ticket, 1u);
+        am_last = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < nslots; i += THREADS) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&s.partials[i * NR + q]);
     }
     block_sum<NR, THREADS>(acc, tot, sh);
     if (threadIdx.x == 0) {

@@ -116,12 +116,14 @@ struct lilac_csr_s {
     // STAGED schedule
     lilac::DevBuf tiles, longs;
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
-    // SLAB copy (built on first use): sliced ELL chunks of every slab's row
-    // pieces (chunk offsets, lane rows, 16-bit local columns, values), the CSR
-    // index of each element (-1: padding; value updates), CTA ranges
-    // {slab, first chunk, end chunk, -}, and the partial sums P (S x rows)
-    lilac::DevBuf slab_cptr, slab_crow, slab_col, slab_val, slab_perm, slab_ctas, slab_P;
-    int slab_S = 0, slab_W = 0, slab_grid = 0;
+    // SLAB copy (built on first use): sliced ELL chunks of the row pieces of
+    // every (slab, row group) pair (chunk offsets, lane rows, 16-bit local
+    // columns, values), the CSR index of each element (-1: padding; value
+    // updates), CTA ranges {slab, first chunk, end chunk, group}, the groups'
+    // rows, their arrival counters, and the partial sums P (S x rows)
+    lilac::DevBuf slab_cptr, slab_crow, slab_col, slab_val, slab_perm, slab_ctas, slab_groups,
+        slab_gcnt, slab_P;
+    int slab_S = 0, slab_W = 0, slab_grid = 0, slab_G = 0;
     int64_t slab_elems = 0;
     bool slab_built = false;
     // SELL copy (built on first use): chunk offsets, lane rows / pieces,

@@ -10,15 +10,15 @@
 //       into place.
 //
 // SLAB  The columns are cut into S slabs of W columns, W * 8 bytes at most
-//       kSlabMaxBytes, S as small as that allows.  For every slab, the
-//       pieces of all rows (the row's nonzeros whose column lies in the slab,
-//       in CSR order, 16-bit local columns) are sorted by length and cut into
-//       chunks the same way; every row has a (possibly empty) piece in every
-//       slab, so P[s][row] is always written.  Padding points at local column
-//       W, a zero kept after the slab of x in shared memory.  The chunks of
-//       each slab are cut into G = SMs / S ranges of about equal size, one
-//       per CTA.  A permutation (element -> CSR position, -1 for padding)
-//       re-gathers the values after lilac_csr_update_values.
+//       kSlabMaxBytes, S as small as that allows, and the rows into G = SMs / S
+//       groups of about equal nonzero count.  For every (slab, group) pair,
+//       the pieces of the group's rows (the row's nonzeros whose column lies
+//       in the slab, in CSR order, 16-bit local columns) are sorted by length
+//       and cut into chunks the same way, one CTA per pair; every row has a
+//       (possibly empty) piece in every slab, so P[s][row] is always written.
+//       Padding points at local column W, a zero kept after the slab of x in
+//       shared memory.  A permutation (element -> CSR position, -1 for
+//       padding) re-gathers the values after lilac_csr_update_values.
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -299,36 +299,61 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     std::vector<int32_t> cnt((size_t)S * (size_t)n, 0);
     for (int r = 0; r < n; ++r)
         for (int k = rp[r]; k < rp[r + 1]; ++k) cnt[(size_t)(col[(size_t)k] / W) * n + r]++;
-    const int nch = (n + 31) / 32;
-    std::vector<int32_t> cptr((size_t)S * nch + 1), crow((size_t)S * nch * 32, -1);
+    // row groups of about equal nonzero count, one CTA per (slab, group)
+    const int G0 = std::max(1, A->sm_count / std::max(1, S));
+    std::vector<int2> groups;
+    {
+        int r = 0;
+        for (int g = 0; g < G0 && r < n; ++g) {
+            const int ra = r;
+            if (g == G0 - 1) {
+                r = n;
+            } else {
+                const int64_t target = nnz * (g + 1) / G0;
+                while (r < n && rp[r + 1] <= target) ++r;
+                if (r == ra) ++r;
+            }
+            groups.push_back(make_int2(ra, r));
+        }
+    }
+    const int G = (int)groups.size();
+    // sliced ELL chunks of each (slab, group): the group's rows sorted by piece
+    // length, longest first
+    std::vector<int32_t> cptr(1, 0), crow;
+    std::vector<int4> ctas;
     std::vector<int64_t> base((size_t)S * (size_t)n);  // first element of each piece
-    std::vector<int64_t> slab_elems((size_t)S);
-    cptr[0] = 0;
     int64_t elems = 0;
     for (int sl = 0; sl < S; ++sl) {
-        const std::vector<int32_t> len(cnt.begin() + (size_t)sl * n, cnt.begin() + (size_t)(sl + 1) * n);
-        const int maxlen = len.empty() ? 0 : *std::max_element(len.begin(), len.end());
-        const std::vector<int32_t> ord = order_by_length(len, maxlen);
-        const int64_t e0 = elems;
-        for (int c = 0; c < nch; ++c) {
-            const size_t gc = (size_t)sl * nch + c;
-            int32_t w = 0;
-            for (int l = 0; l < 32; ++l) {
-                const int i = c * 32 + l;
-                if (i >= n) break;
-                const int r = ord[(size_t)i];
-                crow[gc * 32 + l] = r;
-                base[(size_t)sl * n + r] = elems + l;
-                w = std::max(w, len[(size_t)r]);
+        for (int g = 0; g < G; ++g) {
+            const int r0 = groups[(size_t)g].x, r1 = groups[(size_t)g].y;
+            const std::vector<int32_t> len(cnt.begin() + (size_t)sl * n + r0,
+                                           cnt.begin() + (size_t)sl * n + r1);
+            const int maxlen = *std::max_element(len.begin(), len.end());
+            const std::vector<int32_t> ord = order_by_length(len, maxlen);
+            const int nr = r1 - r0;
+            const int first = (int)cptr.size() - 1;
+            for (int c = 0; c * 32 < nr; ++c) {
+                int32_t w = 0;
+                for (int l = 0; l < 32; ++l) {
+                    const int i = c * 32 + l;
+                    if (i >= nr) {
+                        crow.push_back(-1);
+                        continue;
+                    }
+                    const int r = r0 + ord[(size_t)i];
+                    crow.push_back(r);
+                    base[(size_t)sl * n + r] = elems + l;
+                    w = std::max(w, len[(size_t)ord[(size_t)i]]);
+                }
+                elems += 32 * (int64_t)w;
+                if (elems >= (int64_t(1) << 31) - 64) return LILAC_OK;  // offsets overflow: not built
+                cptr.push_back((int32_t)elems);
             }
-            elems += 32 * (int64_t)w;
-            if (elems >= (int64_t(1) << 31) - 64) return LILAC_OK;  // offsets overflow: not built
-            cptr[gc + 1] = (int32_t)elems;
+            ctas.push_back(make_int4(sl, first, (int)cptr.size() - 1, g));
         }
-        slab_elems[(size_t)sl] = elems - e0;
     }
     // padding of more than a quarter: not worth the copy (STAGED runs)
-    if ((double)elems > 1.25 * (double)nnz + 32.0 * S * nch) return LILAC_OK;
+    if ((double)elems > 1.25 * (double)nnz + 32.0 * (double)crow.size()) return LILAC_OK;
     std::vector<int32_t> perm((size_t)elems, -1);
     std::vector<uint16_t> c16((size_t)elems, (uint16_t)W);
     {
@@ -344,26 +369,6 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
             }
         }
     }
-    // ranges of chunks of about equal size, G per slab, one per CTA
-    const int G = std::max(1, A->sm_count / std::max(1, S));
-    std::vector<int4> ctas;
-    for (int sl = 0; sl < S; ++sl) {
-        const int c_first = sl * nch;
-        const int64_t e_first = cptr[(size_t)c_first];
-        const int64_t tot = slab_elems[(size_t)sl];
-        int c = 0;
-        for (int g = 0; g < G && c < nch; ++g) {
-            const int ca = c;
-            if (g == G - 1) {
-                c = nch;
-            } else {
-                const int64_t target = e_first + tot * (g + 1) / G;
-                while (c < nch && cptr[(size_t)(c_first + c + 1)] <= target) ++c;
-                if (c == ca) ++c;
-            }
-            ctas.push_back(make_int4(sl, c_first + ca, c_first + c, 0));
-        }
-    }
     const size_t vsz = A->dtype == LILAC_F64 ? 8 : 4;
     const size_t epad = (size_t)elems + 64;
     LILAC_TRY(A->ws_alloc(A->slab_cptr, sizeof(int32_t) * cptr.size()));
@@ -371,9 +376,12 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     LILAC_TRY(A->ws_alloc(A->slab_col, sizeof(uint16_t) * epad));
     LILAC_TRY(A->ws_alloc(A->slab_val, vsz * epad));
     LILAC_TRY(A->ws_alloc(A->slab_perm, sizeof(int32_t) * std::max<size_t>(1, (size_t)elems)));
-    LILAC_TRY(A->ws_alloc(A->slab_ctas, sizeof(int4) * std::max<size_t>(1, ctas.size())));
+    LILAC_TRY(A->ws_alloc(A->slab_ctas, sizeof(int4) * ctas.size()));
+    LILAC_TRY(A->ws_alloc(A->slab_groups, sizeof(int2) * groups.size()));
+    LILAC_TRY(A->ws_alloc(A->slab_gcnt, sizeof(unsigned) * groups.size()));
     LILAC_TRY(A->ws_alloc(A->slab_P, sizeof(double) * (size_t)S * (size_t)std::max(1, n)));
     LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_val.p, 0, A->slab_val.bytes, s));
+    LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_gcnt.p, 0, A->slab_gcnt.bytes, s));
     LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_P.p, 0, A->slab_P.bytes, s));
     auto up = [&](lilac::DevBuf& d, const void* h, size_t bytes) -> lilac_status {
         if (bytes) LILAC_CUDA_TRY(cudaMemcpyAsync(d.p, h, bytes, cudaMemcpyHostToDevice, s));
@@ -384,10 +392,12 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     LILAC_TRY(up(A->slab_col, c16.data(), sizeof(uint16_t) * c16.size()));
     LILAC_TRY(up(A->slab_perm, perm.data(), sizeof(int32_t) * perm.size()));
     LILAC_TRY(up(A->slab_ctas, ctas.data(), sizeof(int4) * ctas.size()));
+    LILAC_TRY(up(A->slab_groups, groups.data(), sizeof(int2) * groups.size()));
     LILAC_TRY(A->dtype == LILAC_F64 ? regather<double>(A, elems, s) : regather<float>(A, elems, s));
     LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     A->slab_S = S;
     A->slab_W = W;
+    A->slab_G = G;
     A->slab_grid = (int)ctas.size();
     A->slab_elems = elems;
     A->slab_built = !ctas.empty();
@@ -402,10 +412,10 @@ lilac_status slab_refresh_values(lilac_csr A, cudaStream_t s) {
 }
 
 void slab_release(lilac_csr A) {
-    lilac::DevBuf* b[] = {&A->slab_cptr, &A->slab_crow, &A->slab_col, &A->slab_val,
-                          &A->slab_perm, &A->slab_ctas, &A->slab_P};
+    lilac::DevBuf* b[] = {&A->slab_cptr, &A->slab_crow,   &A->slab_col,  &A->slab_val, &A->slab_perm,
+                          &A->slab_ctas, &A->slab_groups, &A->slab_gcnt, &A->slab_P};
     for (auto* d : b) d->release();
-    A->slab_S = A->slab_W = A->slab_grid = 0;
+    A->slab_S = A->slab_W = A->slab_grid = A->slab_G = 0;
     A->slab_elems = 0;
     A->slab_built = false;
 }

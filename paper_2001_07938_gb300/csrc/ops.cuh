@@ -17,14 +17,15 @@ struct OpStore {
     using ValT = V;
     using VecT = T;
     using AccT = T;
+    using RedT = double;
     static constexpr int NR = 0;
     static constexpr bool kTwoPhase = true;
     T* __restrict__ y;
     __device__ bool skip() const { return false; }
     __device__ void begin() {}
-    __device__ void row(int r, AccT s, double*) const { y[r] = s; }
+    __device__ void row(int r, AccT s, RedT*) const { y[r] = s; }
     __device__ void store(int r, AccT s) const { y[r] = s; }
-    __device__ void reduce(int, double*) const {}
+    __device__ void reduce(int, RedT*) const {}
     __device__ void finish(const double*) const {}
 };
 
@@ -60,6 +61,7 @@ struct OpCgPq {
     using ValT = V;
     using VecT = T;
     using AccT = T;
+    using RedT = typename RedOf<T>::type;
     static constexpr int NR = 1;
     static constexpr bool kTwoPhase = true;
     T* __restrict__ q;
@@ -67,14 +69,12 @@ struct OpCgPq {
     CgState* st;
     __device__ bool skip() const { return cg_done(st); }
     __device__ void begin() {}
-    __device__ void row(int r, AccT s, double* red) const {
+    __device__ void row(int r, AccT s, RedT* red) const {
         q[r] = s;
-        red[0] += double(p[r]) * double(s);
+        red_add_prod(red[0], p[r], s);
     }
     __device__ void store(int r, AccT s) const { q[r] = s; }
-    __device__ void reduce(int r, double* red) const {
-        red[0] += double(p[r]) * double(__ldcg(q + r));
-    }
+    __device__ void reduce(int r, RedT* red) const { red_add_prod(red[0], p[r], __ldcg(q + r)); }
     __device__ void finish(const double* tot) const {
         const double pq = tot[0];
         st->pq = pq;
@@ -98,6 +98,7 @@ struct OpResidual {
     using ValT = V;
     using VecT = double;
     using AccT = double;
+    using RedT = double;
     static constexpr int NR = 2;
     static constexpr bool kTwoPhase = false;
     double* __restrict__ r;
@@ -238,7 +239,7 @@ static __global__ void __launch_bounds__(kVecThreads)
     using V = typename VT::type;
     constexpr int N = VT::N;
     const T alpha = T(fin.st->alpha);
-    double red[1] = {0.0};
+    typename RedOf<T>::type rr{};  // FP32 vectors: compensated FP32 (see CompF32)
     const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
     const int nv = aligned16(x, r, p, q) ? n / N : 0;
     for (int i = g0; i < nv; i += gs) {
@@ -249,7 +250,7 @@ static __global__ void __launch_bounds__(kVecThreads)
             VT::set(xv, e, VT::get(xv, e) + alpha * VT::get(pv, e));
             const T ri = VT::get(rv, e) - alpha * VT::get(qv, e);
             VT::set(rv, e, ri);
-            red[0] += double(ri) * double(ri);
+            red_add_prod(rr, ri, ri);
         }
         reinterpret_cast<V*>(x)[i] = xv;
         reinterpret_cast<V*>(r)[i] = rv;
@@ -258,8 +259,9 @@ static __global__ void __launch_bounds__(kVecThreads)
         x[i] += alpha * p[i];
         const T ri = r[i] - alpha * q[i];
         r[i] = ri;
-        red[0] += double(ri) * double(ri);
+        red_add_prod(rr, ri, ri);
     }
+    double red[1] = {red_value(rr)};
     grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
 }
 
@@ -331,6 +333,7 @@ struct OpResidualRU {
     using ValT = V;
     using VecT = double;
     using AccT = double;
+    using RedT = double;
     static constexpr int NR = 2;
     static constexpr bool kTwoPhase = false;
     float* __restrict__ r;
@@ -462,6 +465,7 @@ struct OpPageRank {
     using ValT = V;
     using VecT = T;
     using AccT = T;
+    using RedT = typename RedOf<T>::type;
     static constexpr int NR = 2;
     static constexpr bool kTwoPhase = true;
     T* __restrict__ y;
@@ -477,17 +481,17 @@ struct OpPageRank {
     // (every thread reads it before its CTA takes a ticket, and this launch's
     // finish() writes it only after the last ticket).
     __device__ void begin() { tele = T(__ldcg(&st->teleport)); }
-    __device__ void row(int r, AccT s, double* red) const {
+    __device__ void row(int r, AccT s, RedT* red) const {
         const T yi = damping * s + tele;
         y[r] = yi;
-        red[0] += fabs(double(yi) - double(x[r]));
-        if (is_dangling(has_out, r)) red[1] += double(yi);
+        red_add_absdiff(red[0], yi, x[r]);
+        if (is_dangling(has_out, r)) red_add(red[1], yi);
     }
     __device__ void store(int r, AccT s) const { y[r] = damping * s + tele; }
-    __device__ void reduce(int r, double* red) const {
+    __device__ void reduce(int r, RedT* red) const {
         const T yi = __ldcg(y + r);
-        red[0] += fabs(double(yi) - double(x[r]));
-        if (is_dangling(has_out, r)) red[1] += double(yi);
+        red_add_absdiff(red[0], yi, x[r]);
+        if (is_dangling(has_out, r)) red_add(red[1], yi);
     }
     __device__ void finish(const double* tot) const {
         const int t = st->iter;

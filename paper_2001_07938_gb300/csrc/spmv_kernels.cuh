@@ -12,7 +12,9 @@
 //   static constexpr int NR                 number of FP64 reductions (0..kMaxRed)
 //   __device__ bool skip() const            true: the whole launch is a no-op
 //   __device__ void begin()                 every thread, once, before any row()
-//   __device__ void row(int r, AccT s, double* red) const
+//   using RedT                              per-thread accumulator of the FP64
+//                                           sums (double, or CompF32 for FP32)
+//   __device__ void row(int r, AccT s, RedT* red) const
 //   static constexpr bool kTwoPhase   true: also store(r, s) (writes only) and
 //       reduce(r, red) (reads back what store wrote); row() == store + reduce.
 //       The MERGE kernel stores while it walks and reduces later, one row per
@@ -55,7 +57,7 @@ __global__ void __launch_bounds__(THREADS)
     op.begin();
     using AccT = typename Op::AccT;
     constexpr int NR = Op::NR;
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
     const int lane = threadIdx.x & (V - 1);
     const int group = (int)((blockIdx.x * THREADS + threadIdx.x) / V);
     const int ngroups = (int)(gridDim.x * THREADS / V);
@@ -119,7 +121,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
     }
 }
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(THREADS)
     __shared__ AccT sh_sum[32];
     __shared__ int sh_ok;
 
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
     const int tid = threadIdx.x;
     const int lane = tid & (V - 1);
     const int group = tid / V;
@@ -321,10 +323,10 @@ __global__ void __launch_bounds__(THREADS)
                     __threadfence();
                     AccT rs = AccT(0);
                     for (int j = 0; j < lr.nchunks; ++j) rs += AccT(__ldcg(&s.long_part[lr.first_slot + j]));
-                    double lred[NR > 0 ? NR : 1] = {};
+                    typename Op::RedT lred[NR > 0 ? NR : 1] = {};
                     op.row(lr.row, rs, lred);
 #pragma unroll
-                    for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = lred[q];
+                    for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = red_value(lred[q]);
                     s.long_cnt[lid] = 0u;
                 }
             }
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_finish<NR, THREADS>(op, r2, s, nlong);
     }
 }
@@ -395,10 +397,10 @@ __device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& o
         if constexpr (kStoreOnly) {
             op.store(sp.x, rs);
         } else {
-            double lred[NR > 0 ? NR : 1] = {};
+            typename Op::RedT lred[NR > 0 ? NR : 1] = {};
             op.row(sp.x, rs, lred);
 #pragma unroll
-            for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = lred[q];
+            for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = red_value(lred[q]);
         }
         s.long_cnt[lid] = 0u;
         __threadfence();  // the epilogue sums before this CTA's grid-reduction ticket
@@ -418,7 +420,7 @@ __global__ void __launch_bounds__(THREADS)
     using VecT = typename Op::VecT;
     using AccT = typename Op::AccT;
     constexpr int NR = kStoreOnly ? 0 : Op::NR;
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)(gridDim.x * (THREADS / 32));
     for (int ch = (int)((blockIdx.x * THREADS + threadIdx.x) >> 5); ch < S.nchunks; ch += nwarps) {
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_finish<NR, THREADS>(op, r2, s, S.nsplit);
     }
 }
@@ -485,13 +487,13 @@ __global__ void __launch_bounds__(THREADS) rows_reduce_kernel(int rows, Op op, S
     if (op.skip()) return;
     op.begin();
     constexpr int NR = Op::NR;
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
     for (int r = blockIdx.x * THREADS + threadIdx.x; r < rows; r += gridDim.x * THREADS)
         op.reduce(r, red);
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
     }
 }
@@ -501,27 +503,46 @@ __global__ void __launch_bounds__(THREADS) rows_reduce_kernel(int rows, Op op, S
 // memory.  Random 8-byte gathers through L1 cost one tag lookup per distinct
 // line (about one per cycle per SM); from shared memory they cost one bank
 // access each.  The columns are cut into S slabs of W columns (x slab of at
-// most kSlabMaxBytes) and each slab's pieces of all rows (the nonzeros of the
-// row whose column lies in the slab, in CSR order, 16-bit local columns) form
-// their own sliced ELL chunks, rows sorted by piece length.  One CTA of
-// THREADS threads per SM loads slab s of x into shared memory (plus a zero at
-// index W that padding elements point to) and runs a range of that slab's
-// chunks, warps taking chunks from a shared counter; the lane's sum goes to
-// P[s][row].  The combine kernel adds P over the slabs in slab order and runs
-// the epilogue.
-template <int THREADS, int UNR, class ValT, class VecT, class AccT>
+// most kSlabMaxBytes) and the rows into G groups of about equal nonzero
+// count.  Each (slab, group) pair holds the pieces of the group's rows (the
+// nonzeros whose column lies in the slab, in CSR order, 16-bit local
+// columns) as sliced ELL chunks sorted by piece length.  One CTA of THREADS
+// threads per (slab, group), one per SM, loads slab s of x into shared memory
+// (plus a zero at index W that padding points to) and runs the pair's chunks,
+// warps taking chunks from a shared counter; a lane's piece sum goes to
+// P[s][row].  The last of the group's S CTAs to finish (arrival counter) adds
+// P over the slabs in slab order for every row of the group and runs the
+// epilogue; its reductions go to partial slot g, summed in slot order.
+struct SlabView {
+    const int* __restrict__ cptr;    // [S * chunks + 1]
+    const int* __restrict__ crow;    // [chunks * 32]: row, or -1 (padding lane)
+    const uint16_t* __restrict__ col;
+    const int4* __restrict__ ctas;   // {slab, first chunk, end chunk, group}
+    const int2* __restrict__ groups; // [G] rows [r0, r1)
+    unsigned* __restrict__ gcnt;     // [G] arrival counters (zero between launches)
+    int rows, ncols, W, S, G;
+};
+
+template <int THREADS, int UNR, class Op>
 __global__ void __launch_bounds__(THREADS, 1)
-    spmv_slab_kernel(const int* __restrict__ cptr, const int* __restrict__ crow,
-                     const uint16_t* __restrict__ scol, const ValT* __restrict__ sval,
-                     const int4* __restrict__ ctas, int rows, int ncols, int W,
-                     const VecT* __restrict__ x, AccT* __restrict__ P) {
+    spmv_slab_kernel(SlabView V, const typename Op::ValT* __restrict__ sval,
+                     const typename Op::VecT* __restrict__ x, typename Op::AccT* __restrict__ P,
+                     Op op, Scratch s) {
+    if (op.skip()) return;
+    op.begin();
+    using ValT = typename Op::ValT;
+    using VecT = typename Op::VecT;
+    using AccT = typename Op::AccT;
+    constexpr int NR = Op::NR;
     extern __shared__ __align__(16) unsigned char slab_smem[];
     __shared__ int next_chunk;
+    __shared__ int last_of_group;
     VecT* xs = reinterpret_cast<VecT*>(slab_smem);
-    const int4 c = ctas[blockIdx.x];  // {slab, first chunk, end chunk, -}
+    const int4 c = V.ctas[blockIdx.x];  // {slab, first chunk, end chunk, group}
     const int sl = c.x;
+    const int W = V.W;
     const int c0 = sl * W;
-    const int w = min(W, ncols - c0);
+    const int w = min(W, V.ncols - c0);
     {
         // the slab of x into shared memory: 16-byte loads when x is aligned
         // (c0 is a multiple of 8), eight in flight per thread
@@ -545,14 +566,14 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) next_chunk = c.y + THREADS / 32;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    AccT* __restrict__ Ps = P + (size_t)sl * rows;
+    AccT* __restrict__ Ps = P + (size_t)sl * V.rows;
     int ch = c.y + (int)(threadIdx.x >> 5);
     while (ch < c.z) {
-        const int base = __ldg(cptr + ch);
-        const int width = (__ldg(cptr + ch + 1) - base) >> 5;
-        const int row = __ldg(crow + (size_t)ch * 32 + lane);
+        const int base = __ldg(V.cptr + ch);
+        const int width = (__ldg(V.cptr + ch + 1) - base) >> 5;
+        const int row = __ldg(V.crow + (size_t)ch * 32 + lane);
         const ValT* __restrict__ vp = sval + base + lane;
-        const uint16_t* __restrict__ cp = scol + base + lane;
+        const uint16_t* __restrict__ cp = V.col + base + lane;
         AccT acc = AccT(0);
         int k = 0;
         for (; k + UNR <= width; k += UNR) {
@@ -567,7 +588,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
         }
         if (k < width) {
-            // the last (fewer than UNR) elements, loads issued together
+            // the last (fewer than UNR) elements, loads issued together; the
+            // bound is the same for the whole warp, so skipped FMAs cost nothing
             ValT vv[UNR];
             int cc[UNR];
 #pragma unroll
@@ -585,27 +607,29 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) nx = atomicAdd(&next_chunk, 1);
         ch = __shfl_sync(0xffffffffu, nx, 0);
     }
-}
-
-// y_r = sum over slabs s (in order) of P[s][r], then the epilogue.
-template <int THREADS, class Op>
-__global__ void __launch_bounds__(THREADS)
-    slab_combine_kernel(int rows, int S, const typename Op::AccT* __restrict__ P, Op op, Scratch s) {
-    if (op.skip()) return;
-    op.begin();
-    using AccT = typename Op::AccT;
-    constexpr int NR = Op::NR;
-    double red[NR > 0 ? NR : 1] = {};
-    for (int r = blockIdx.x * THREADS + threadIdx.x; r < rows; r += gridDim.x * THREADS) {
-        AccT sum = P[r];
-        for (int q = 1; q < S; ++q) sum += P[(size_t)q * rows + r];
-        op.row(r, sum, red);
+    // the last CTA of the row group combines the slabs and runs the epilogue
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0)
+        last_of_group = atomicAdd(&V.gcnt[c.w], 1u) == (unsigned)(V.S - 1) ? 1 : 0;
+    __syncthreads();
+    const bool last = last_of_group != 0;
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
+    if (last) {
+        __threadfence();
+        const int2 gr = V.groups[c.w];
+        for (int r = gr.x + (int)threadIdx.x; r < gr.y; r += THREADS) {
+            AccT sum = __ldcg(P + r);
+            for (int q = 1; q < V.S; ++q) sum += __ldcg(P + (size_t)q * V.rows + r);
+            op.row(r, sum, red);
+        }
+        if (threadIdx.x == 0) V.gcnt[c.w] = 0u;
     }
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
-        grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
+        grid_reduce_slots<NR, THREADS>(op, r2, s, last ? c.w : -1, V.G);
     }
 }
 
@@ -626,7 +650,7 @@ __global__ void __launch_bounds__(THREADS)
     op.begin();
     using AccT = typename Op::AccT;
     constexpr int NR = Op::NR;
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
     for (int sl = blockIdx.x * THREADS + threadIdx.x; sl < rows; sl += gridDim.x * THREADS) {
         const int L = __ldg(len + sl);
         AccT sum = AccT(0);
@@ -640,7 +664,7 @@ __global__ void __launch_bounds__(THREADS)
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_finish<NR, THREADS>(op, r2, s, 0);
     }
 }
@@ -742,7 +766,7 @@ __global__ void __launch_bounds__(THREADS, merge_min_blocks<Op, THREADS>())
     const int64_t total = (int64_t)rows + nnz;
     const int64_t D0 = (int64_t)blockIdx.x * per_cta;
     const int64_t D1 = D0 + per_cta < total ? D0 + per_cta : total;
-    double red[NR > 0 ? NR : 1] = {};
+    typename Op::RedT red[NR > 0 ? NR : 1] = {};
 
     if (tid == 0) {
         int2 st = make_int2(rows, (int)nnz);
@@ -918,7 +942,7 @@ __global__ void __launch_bounds__(THREADS, merge_min_blocks<Op, THREADS>())
     if constexpr (NR > 0) {
         double r2[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) r2[q] = red[q];
+        for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         block_sum<NR, THREADS>(r2, tot, sh_red);
     }
     if (tid == 0) {
@@ -939,7 +963,7 @@ __global__ void __launch_bounds__(THREADS, merge_min_blocks<Op, THREADS>())
     if (!am_last) return;
     __threadfence();
     const int G = (int)gridDim.x;
-    double fred[NR > 0 ? NR : 1] = {};
+    typename Op::RedT fred[NR > 0 ? NR : 1] = {};
     for (int c = tid; c < G; c += THREADS) {
         const int r = __ldcg(&carries[c].tail_row);
         if (r < 0 || (c > 0 && __ldcg(&carries[c - 1].tail_row) == r)) continue;
@@ -958,7 +982,7 @@ __global__ void __launch_bounds__(THREADS, merge_min_blocks<Op, THREADS>())
     if constexpr (NR > 0) {
         double acc[NR];
 #pragma unroll
-        for (int q = 0; q < NR; ++q) acc[q] = fred[q];
+        for (int q = 0; q < NR; ++q) acc[q] = red_value(fred[q]);
         for (int c = tid; c < G; c += THREADS) {
 #pragma unroll
             for (int q = 0; q < NR; ++q) acc[q] += __ldcg(&partials[c * NR + q]);

@@ -76,6 +76,31 @@ def test_sell_split_epilogue_cg_matches_single_pass():
     assert true_rel_residual(A, b, xs[0]) <= 1e-10
 
 
+@pytest.mark.parametrize("variant", [5, 7])
+def test_slab_and_sell_cg_converge_and_repeat_bitwise(variant):
+    """SLAB (the last CTA of each row group combines the slabs; its p.q sums
+    go to the group's slot) and SELL: CG as the oracle, bitwise run to run."""
+    A = inputs.spd_random(20000, 30, 20.0, 8)
+    b = inputs.uniform(9, A.n)
+    torch = torch_cuda()
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(variant, 4)
+    assert M.info()["active_variant"] == variant
+    xs = []
+    for _ in range(2):
+        bd, xd = dev(b), torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st, inf = M.cg(bd, xd, rtol=1e-10, max_iter=500)
+        torch.cuda.synchronize()
+        assert st == L.LILAC_OK
+        xs.append(host(xd))
+    M.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    xr, itr, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=500, rtol=1e-10)
+    assert abs(inf.iters - itr) <= 1
+    assert true_rel_residual(A, b, xs[0]) <= 1e-10
+    assert np.linalg.norm(xs[0] - xr) <= 1e-9 * np.linalg.norm(xr)
+
+
 def test_laplacian_converges_and_eigenmode_in_one_step():
     A = inputs.laplacian2d(40)
     b = np.ones(A.n)
