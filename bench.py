@@ -55,9 +55,21 @@ def _peaks():
     return 6800.0, "fallback"
 
 
+# FP64 rate of the GB300 (the recipe's nominal 1.25 TFLOP/s): 152 SMs x 2 FP64
+# FMA per clock x 2 FLOP x 2.07 GHz = 1.26 TFLOP/s.  A loop of independent
+# DFMAs measured 1.20 TFLOP/s on this machine.
+FP64_PEAK_TFLOPS = 1.25
+
+# --variant: the kernel to use instead of the tuner's choice (the matrix is
+# then created without the timed tuning, so that a run under a profiler uses
+# the same kernel as the plain run)
+FORCED_VARIANT = None
+VARIANT_CODES = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6, "sell": 7}
+
+
 def _kernel_src_hash():
     h = hashlib.sha256()
-    for f in ("spmv_kernels.cuh", "ops.cuh", "lilac_device.cuh", "launch.cuh"):
+    for f in ("spmv_kernels.cuh", "ops.cuh", "lilac_device.cuh", "launch.cuh", "lilac_sell.cu"):
         with open(os.path.join(ROOT, "paper_2001_07938_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -155,6 +167,19 @@ class Workload:
     def __init__(self, L, torch):
         self.L, self.torch = L, torch
 
+    def _matrix(self, A):
+        L = self.L
+        if FORCED_VARIANT is None:
+            return L.CsrMatrix.from_csr(A)
+        M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+        M.set_variant(*FORCED_VARIANT)
+        return M
+
+    def roofline_alu(self):
+        """(FLOP per SpMV launch, what) when the SpMV is bound by FP64
+        arithmetic rather than HBM, else None."""
+        return None
+
     def _profiled(self, k, nbytes, what):
         """Average SpMV launch duration over k steps (lilac_csr_profile:
         CUDA event pairs on the launching stream, inside the captured graphs)."""
@@ -177,6 +202,11 @@ class CG75k(Workload):
         from paper_2001_07938_gb300 import inputs
         self.A, self.b = inputs.workload_spd_cg()
 
+    def roofline_alu(self):
+        # one FP64 FMA per nonzero: ncu shows the FP64 pipe, not DRAM, nearest
+        # its limit for this matrix (random columns, FP64 values)
+        return 2.0 * self.A.nnz, "FP64 FMA per nonzero"
+
     def config(self):
         A = self.A
         mat = A.nnz * 12 + (A.n + 1) * 4
@@ -188,7 +218,7 @@ class CG75k(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.bd = torch.from_numpy(self.b).cuda()
         self.xd = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
         self.opts = L.lilac_cg_opts_default()
@@ -271,7 +301,7 @@ class SpMV2D(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.xd = torch.from_numpy(self.x).cuda()
         self.yd = torch.empty(self.A.n, dtype=torch.float64, device="cuda")
         self.launches_per_step = self.calls
@@ -358,7 +388,7 @@ class PageRank22(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.xd = torch.empty(self.A.n, dtype=torch.float32, device="cuda")
         self.launches_per_step = 1 + self.iters * self.M.info()["spmv_kernels"]
 
@@ -425,7 +455,7 @@ class IR192(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.bd = torch.from_numpy(self.b).cuda()
         self.xd = torch.zeros(self.A.n, dtype=torch.float64, device="cuda")
         self.opts = self._opts(self.precision)
@@ -543,7 +573,7 @@ class SpMM8(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.X = torch.rand(self.A.ncols, self.k, dtype=torch.float64, device="cuda")
         self.Y = torch.empty(self.A.n, self.k, dtype=torch.float64, device="cuda")
         self.launches_per_step = 1
@@ -629,7 +659,7 @@ class BFS22(Workload):
 
     def setup(self):
         torch, L = self.torch, self.L
-        self.M = L.CsrMatrix.from_csr(self.A)
+        self.M = self._matrix(self.A)
         self.lv = torch.empty(self.A.n, dtype=torch.int32, device="cuda")
         self.depth = self.M.bfs(self.src, self.lv)
         torch.cuda.synchronize()
@@ -983,13 +1013,12 @@ def run_lilac(args):
 
     barrier, max_over_ranks = collectives(ws, "cuda")
 
-    wl = WORKLOADS[args.workload](L, torch)
-    wl.setup()
+    global FORCED_VARIANT
     if args.variant:
         name, _, width = args.variant.partition(":")
-        codes = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6,
-                 "sell": 7}
-        wl.M.set_variant(codes[name], int(width or 0))
+        FORCED_VARIANT = (VARIANT_CODES[name], int(width or 0))
+    wl = WORKLOADS[args.workload](L, torch)
+    wl.setup()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None
     for _ in range(args.warmup):
@@ -1027,6 +1056,20 @@ def run_lilac(args):
                 "algorithmic_bytes_per_launch": kern_bytes, "avg_launch_ms": kern_ms,
                 "launches_timed": n_kern,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
+    roofline_hbm = None
+    alu = wl.roofline_alu()
+    if alu is not None:
+        flops, what = alu
+        tflops = flops / (kern_ms / 1000.0) / 1e12
+        roofline_hbm = roofline
+        roofline = {"bound": "alu", "achieved": tflops, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": tflops / FP64_PEAK_TFLOPS,
+                    "traffic": roofline_hbm["traffic"], "kernel": kname,
+                    "algorithmic_flops_per_launch": flops, "flops": what,
+                    "algorithmic_bytes_per_launch": kern_bytes, "avg_launch_ms": kern_ms,
+                    "launches_timed": n_kern,
+                    "peak_kind": "of nominal FP64 rate (152 SMs x 2 FMA/clk x 2.07 GHz; "
+                                 "a DFMA loop measured 1.20 TFLOP/s)"}
 
     # end to end through the C ABI with pinned host buffers
     wl.e2e_setup()
@@ -1055,6 +1098,7 @@ def run_lilac(args):
                 "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
                                "p99": float(np.percentile(step_ms, 99))},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                **({"roofline_hbm": roofline_hbm} if roofline_hbm else {}),
                 "gpu_launches": wl.launches_per_step * K,
                 "clocks": clk, "check": check,
                 "spmv": {"gbs": achieved, "hbm_frac": achieved / peak}}

@@ -308,8 +308,9 @@ lilac_status lilac_spmm(lilac_csr A, const void* X, void* Y, int32_t k, int32_t 
  *        compares with the hashes of the upload.  Changed structure rebuilds
  *        the copy; changed values alone are re-uploaded.
  *        At most 32 copies are kept (least recently used evicted).
- *   mode LILAC_HOST_NAIVE: create, upload, tune, multiply and free on every
- *        call (the naive insertion the paper measures against, Section 6.3).
+ *   mode LILAC_HOST_NAIVE: create (kernel chosen from row statistics, no
+ *        timed tuning), upload, multiply and free on every call (the naive
+ *        insertion the paper measures against, Section 6.3).
  *   ncols < 0: max(col_ind) + 1.  x (ncols) and y (rows) are host arrays of
  *   `dtype`; the call synchronizes `stream`.  The paper's page-protection
  *   change tracking is not reproduced: writes the caller hides behind an

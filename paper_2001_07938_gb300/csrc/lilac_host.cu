@@ -113,9 +113,11 @@ lilac_status lilac_spmv_host(int32_t rows, int32_t ncols, int64_t nnz, const int
     HostCache& c = cache();
     std::lock_guard<std::mutex> lock(c.mu);
     if (mode == LILAC_HOST_NAIVE) {
+        // upload, multiply, free: the kernel comes from row statistics, as a
+        // per-call timed tuning is no part of the naive insertion
         lilac_csr A = nullptr;
-        LILAC_TRY(lilac_csr_create(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, LILAC_MEM_HOST, 0,
-                                   stream, &A));
+        LILAC_TRY(lilac_csr_create(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, LILAC_MEM_HOST,
+                                   LILAC_CREATE_NO_TUNE, stream, &A));
         c.stats.uploads++;
         c.stats.calls++;
         const lilac_status st = lilac_spmv(A, x, y, LILAC_MEM_HOST, stream);
