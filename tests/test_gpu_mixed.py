@@ -19,9 +19,11 @@ from lilac_testutil import dev, host, torch_cuda, true_rel_residual
 pytestmark = pytest.mark.gpu
 
 
-def _mixed(A, b, precision=1, **kw):
+def _mixed(A, b, precision=1, variant=None, **kw):
     torch = torch_cuda()
     M = L.CsrMatrix.from_csr(A)
+    if variant:
+        M.set_variant(*variant)
     xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     st, info = M.cg(dev(b), xd, precision=precision, **kw)
     torch.cuda.synchronize()
@@ -50,6 +52,17 @@ def test_fp64_values_not_fp32_exact():
     assert true_rel_residual(A, b, x) <= 1e-10
     xr, _, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=5000, rtol=1e-12)
     assert np.linalg.norm(x - xr) <= 1e-8 * np.linalg.norm(xr)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_copy_variant_on_fp64_values_with_fp32_inner_solve(precision):
+    """FP64 handle pinned to SELL: the FP64 residual runs on the SELL copy, the
+    FP32 inner SpMV (a derived FP32 value array) falls back to STAGED."""
+    A = inputs.banded_spd(6000, 16, 1.0, seed=5, fp32_exact=False)
+    b = inputs.uniform(6, A.n)
+    st, info, x = _mixed(A, b, precision=precision, variant=(7, 4), rtol=1e-10, max_iter=3000)
+    assert st == L.LILAC_OK
+    assert true_rel_residual(A, b, x) <= 1e-10
 
 
 @pytest.mark.slow

@@ -187,6 +187,20 @@ def test_slab_and_sell_padding_ignore_nonfinite_x_and_follow_updates(variant):
     M.close()
 
 
+def test_slab_fp32_values_and_vectors():
+    """SLAB on an FP32 handle: the slab of x in shared memory holds FP32 values
+    and rows accumulate in FP32; two slabs of 20,000 columns."""
+    A = inputs.spd_random(40000, 30, 20.0, 3).astype(np.float32)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_SLAB, 4)
+    assert M.info()["active_variant"] == L.LILAC_VARIANT_SLAB
+    x = inputs.uniform(12, A.n, dtype=np.float32)
+    y = _run(M, x, np.float32)
+    assert_spmv_close(A, x.astype(np.float64), y, True, "slab fp32")
+    np.testing.assert_array_equal(_run(M, x, np.float32), y)
+    M.close()
+
+
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_merge_empty_runs_and_rows_across_ctas(dtype):
     """MERGE: runs of empty rows longer than a CTA's path range, rows whose
