@@ -73,3 +73,39 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(L, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="no CPU path"):
         L.load()
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """Every struct the binding mirrors has the size and field offsets the C
+    compiler gives the header's declaration (the binding is plain ctypes, so a
+    field added on one side only would shift every later field)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        pytest.skip("no C compiler")
+    structs = [L.lilac_csr_info_t, L.lilac_cg_opts, L.lilac_cg_info, L.lilac_server_opts,
+               L.lilac_request, L.lilac_completion, L.lilac_server_stats_t, L.lilac_host_stats_t]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "lilac.h"', "int main(void) {"]
+    for st in structs:
+        n = st.__name__
+        lines.append(f'printf("{n} sizeof %zu\\n", sizeof({n}));')
+        for f, _ in st._fields_:
+            # a trailing underscore stands for a C field named like a Python keyword
+            lines.append(f'printf("{n} {f} %zu\\n", offsetof({n}, {f.rstrip("_")}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c_layout = {}
+    for line in out.splitlines():
+        n, f, v = line.split()
+        c_layout[(n, f)] = int(v)
+    for st in structs:
+        n = st.__name__
+        assert c_layout[(n, "sizeof")] == ctypes.sizeof(st), n
+        for f, _ in st._fields_:
+            assert c_layout[(n, f)] == getattr(st, f).offset, f"{n}.{f}"
