@@ -24,9 +24,10 @@
  *    kernels use, and the dangling-vertex set PageRank needs (on first use).
  *
  * Conventions for every entry point:
- *  - Every function returns a lilac_status; no exception crosses the ABI.
- *    lilac_last_error() gives a one-line message for the calling thread's
- *    last failure.
+ *  - Every function returns a lilac_status; no exception crosses the ABI
+ *    (a failed host allocation returns LILAC_ERR_OOM, any other internal
+ *    failure LILAC_ERR_CUDA).  lilac_last_error() gives a one-line message
+ *    for the calling thread's last failure.
  *  - Indices are int32 and 0-based; nnz < 2^31.  Empty rows are allowed
  *    (their y is 0), so are duplicate (i, j) entries (they add up) and
  *    unsorted columns.

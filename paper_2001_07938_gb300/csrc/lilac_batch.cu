@@ -228,7 +228,7 @@ struct lilac_batch_s {
     DevBuf arena;  // workspaces of the current call's problems
 };
 
-extern "C" lilac_status lilac_batch_create(lilac_batch* out) {
+extern "C" lilac_status lilac_batch_create(lilac_batch* out) try {
     if (!out) {
         set_last_error("out is NULL");
         return LILAC_ERR_INVALID_ARG;
@@ -241,15 +241,19 @@ extern "C" lilac_status lilac_batch_create(lilac_batch* out) {
         B->eng.sm_count = 1;
     *out = B;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-extern "C" lilac_status lilac_batch_destroy(lilac_batch B) {
+extern "C" lilac_status lilac_batch_destroy(lilac_batch B) try {
     if (!B) return LILAC_OK;
     DeviceGuard g(B->eng.device);
     cudaDeviceSynchronize();
     B->arena.release();
     delete B;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
 static lilac_status batch_check(lilac_batch B, int32_t count, const lilac_csr* A) {
@@ -295,7 +299,7 @@ static lilac_status batch_workspaces(lilac_batch B, int32_t count, const lilac_c
 }
 
 extern "C" lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
-                                         const double* const* x, double* const* y, void* stream) {
+                                         const double* const* x, double* const* y, void* stream) try {
     LILAC_TRY(batch_check(B, count, A));
     if (count > 0 && (!x || !y)) {
         set_last_error("x and y arrays are required");
@@ -312,12 +316,14 @@ extern "C" lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lil
                                         BP_F64, 0.0));
     LILAC_TRY(B->eng.upload(probs, s));
     return B->eng.spmv_phase(s);
+} catch (...) {
+    return lilac::api_failure();
 }
 
 extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
                                        const double* const* b, double* const* x, int32_t max_iter,
                                        double rtol, int32_t precision, lilac_cg_info* infos,
-                                       void* stream) {
+                                       void* stream) try {
     LILAC_TRY(batch_check(B, count, A));
     if ((count > 0 && (!b || !x)) || max_iter < 0 || (precision != 0 && precision != 2)) {
         set_last_error("invalid argument to lilac_batch_cg");
@@ -380,4 +386,6 @@ extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac
         if (hs[i].status != LILAC_OK && worst == LILAC_OK) worst = (lilac_status)hs[i].status;
     }
     return worst;
+} catch (...) {
+    return lilac::api_failure();
 }

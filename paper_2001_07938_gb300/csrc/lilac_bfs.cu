@@ -113,7 +113,7 @@ static lilac_status bfs_impl(lilac_csr A, int source, int* level, int* depth, cu
 using namespace lilac;
 
 extern "C" lilac_status lilac_bfs(lilac_csr A, int32_t source, int32_t* level, lilac_mem where,
-                                  int32_t* depth, void* stream) {
+                                  int32_t* depth, void* stream) try {
     LILAC_TRY(check_handle(A));
     if (A->rows != A->ncols) {
         set_last_error("BFS needs a square matrix");
@@ -138,4 +138,6 @@ extern "C" lilac_status lilac_bfs(lilac_csr A, int32_t source, int32_t* level, l
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     }
     return check_device_status(A, s);
+} catch (...) {
+    return lilac::api_failure();
 }

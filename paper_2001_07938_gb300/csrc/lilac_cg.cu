@@ -374,7 +374,7 @@ extern "C" void lilac_cg_opts_default(lilac_cg_opts* o) {
 }
 
 extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_mem where,
-                                 const lilac_cg_opts* opts, lilac_cg_info* info, void* stream) {
+                                 const lilac_cg_opts* opts, lilac_cg_info* info, void* stream) try {
     LILAC_TRY(check_handle(A));
     lilac_cg_opts o;
     lilac_cg_opts_default(&o);
@@ -454,4 +454,6 @@ extern "C" lilac_status lilac_cg(lilac_csr A, const double* b, double* x, lilac_
             return (lilac_status)local.status;
     }
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }

@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -17,6 +18,26 @@ namespace lilac {
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+// Status for an exception about to leave an entry point (called from its
+// catch block): a host allocation failure is LILAC_ERR_OOM, anything else an
+// internal failure reported as LILAC_ERR_CUDA.  No exception crosses the C ABI.
+lilac_status api_failure() noexcept {
+    lilac_status st = LILAC_ERR_CUDA;
+    const char* msg = "internal error";
+    try {
+        throw;
+    } catch (const std::bad_alloc&) {
+        st = LILAC_ERR_OOM;
+        msg = "host allocation failed";
+    } catch (...) {
+    }
+    try {
+        set_last_error(msg);
+    } catch (...) {
+    }
+    return st;
+}
 
 // Test hook: the n-th device allocation from now fails as out of memory.
 static std::atomic<int64_t> g_fail_alloc_in{0};
@@ -519,7 +540,7 @@ extern "C" {
 
 lilac_status lilac_csr_create(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
                               const int32_t* col_ind, const void* vals, lilac_dtype dtype,
-                              lilac_mem where, uint32_t flags, void* stream, lilac_csr* out) {
+                              lilac_mem where, uint32_t flags, void* stream, lilac_csr* out) try {
     if (!out) {
         set_last_error("out is NULL");
         return LILAC_ERR_INVALID_ARG;
@@ -541,8 +562,13 @@ lilac_status lilac_csr_create(int32_t rows, int32_t ncols, int64_t nnz, const in
     if (cudaDeviceGetAttribute(&A->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
         A->sm_count <= 0)
         A->sm_count = 1;
-    lilac_status st = create_impl(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, where, flags,
-                                  static_cast<cudaStream_t>(stream), A);
+    lilac_status st;
+    try {
+        st = create_impl(rows, ncols, nnz, row_ptr, col_ind, vals, dtype, where, flags,
+                         static_cast<cudaStream_t>(stream), A);
+    } catch (...) {
+        st = api_failure();  // the handle built so far is freed below
+    }
     if (st != LILAC_OK) {
         cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
         free_handle(A);
@@ -550,9 +576,11 @@ lilac_status lilac_csr_create(int32_t rows, int32_t ncols, int64_t nnz, const in
     }
     *out = A;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem where, void* stream) {
+lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem where, void* stream) try {
     LILAC_TRY(check_handle(A));
     if ((A->nnz > 0 && !vals) || (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE)) {
         set_last_error("invalid argument to lilac_csr_update_values");
@@ -572,17 +600,21 @@ lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem wh
     LILAC_TRY(sell_refresh_values(A, s));
     LILAC_TRY(jds_refresh_values(A, s));
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_csr_destroy(lilac_csr A) {
+lilac_status lilac_csr_destroy(lilac_csr A) try {
     if (!A) return LILAC_OK;
     DeviceGuard g(A->device);
     cudaDeviceSynchronize();
     free_handle(A);
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) {
+lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) try {
     if (!A || !info) {
         set_last_error("NULL argument to lilac_csr_info");
         return LILAC_ERR_INVALID_ARG;
@@ -614,9 +646,11 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) {
     info->sell_padded_nnz = A->sell_built ? A->sell_elems : 0;
     info->spmv_kernels = active == LILAC_VARIANT_SELL && A->sell_two_pass ? 2 : 1;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width) {
+lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width) try {
     if (!A) {
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
@@ -646,10 +680,12 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         A->vwidth = 1;
     if (variant == LILAC_VARIANT_VECTOR && A->vwidth < 2) A->vwidth = 2;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
 lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms,
-                               int64_t* spmv_launches) {
+                               int64_t* spmv_launches) try {
     if (!A) {
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
@@ -662,9 +698,11 @@ lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms,
     }
     A->profiling = enable != 0;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg) {
+lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg) try {
     if (what == LILAC_INJECT_ALLOC_FAIL) {
         if (arg < 0) {
             set_last_error("lilac_debug_inject: allocation count must be >= 0");
@@ -685,9 +723,11 @@ lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg) {
     }
     set_last_error("lilac_debug_inject: unknown hook");
     return LILAC_ERR_INVALID_ARG;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_csr_reset_error(lilac_csr A) {
+lilac_status lilac_csr_reset_error(lilac_csr A) try {
     if (!A) {
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
@@ -697,6 +737,8 @@ lilac_status lilac_csr_reset_error(lilac_csr A) {
     LILAC_CUDA_TRY(cudaDeviceSynchronize());
     A->sticky_error = false;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
 const char* lilac_status_string(lilac_status s) {

@@ -103,7 +103,7 @@ using namespace lilac;
 
 lilac_status lilac_spmv_host(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
                              const int32_t* col_ind, const void* vals, lilac_dtype dtype,
-                             const void* x, void* y, uint64_t version, uint32_t mode, void* stream) {
+                             const void* x, void* y, uint64_t version, uint32_t mode, void* stream) try {
     if (rows < 0 || nnz < 0 || (rows > 0 && (!row_ptr || !y)) || (nnz > 0 && (!col_ind || !vals || !x)) ||
         (dtype != LILAC_F64 && dtype != LILAC_F32) || (mode != LILAC_HOST_CACHED && mode != LILAC_HOST_NAIVE)) {
         set_last_error("invalid argument to lilac_spmv_host");
@@ -167,9 +167,11 @@ lilac_status lilac_spmv_host(int32_t rows, int32_t ncols, int64_t nnz, const int
     it->second.last_use = ++c.clock;
     c.stats.calls++;
     return lilac_spmv(it->second.A, x, y, LILAC_MEM_HOST, stream);
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_host_cache_stats(lilac_host_stats_t* st) {
+lilac_status lilac_host_cache_stats(lilac_host_stats_t* st) try {
     if (!st) {
         set_last_error("NULL argument to lilac_host_cache_stats");
         return LILAC_ERR_INVALID_ARG;
@@ -179,13 +181,17 @@ lilac_status lilac_host_cache_stats(lilac_host_stats_t* st) {
     *st = c.stats;
     st->resident = (int32_t)c.entries.size();
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_host_cache_clear(void) {
+lilac_status lilac_host_cache_clear(void) try {
     HostCache& c = cache();
     std::lock_guard<std::mutex> lock(c.mu);
     for (auto& kv : c.entries) lilac_csr_destroy(kv.second.A);
     c.entries.clear();
     c.stats = lilac_host_stats_t{};
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }

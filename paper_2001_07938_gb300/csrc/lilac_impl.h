@@ -48,6 +48,7 @@ constexpr int kMergeItems = LILAC_MERGE_ITEMS;
 constexpr int kMaxCtas = 8192;  // bound of the per-CTA partial-sum buffer
 
 void set_last_error(const std::string& msg);
+lilac_status api_failure() noexcept;
 
 #define LILAC_CUDA_TRY(...)                                                                   \
     do {                                                                                      \

@@ -129,7 +129,7 @@ void jds_release(lilac_csr A) {
 using namespace lilac;
 
 lilac_status lilac_csr_jds(lilac_csr A, int32_t* perm, int32_t* jd_ptr, int32_t* col_ind, void* vals,
-                           int32_t* nzcnt) {
+                           int32_t* nzcnt) try {
     if (!A) {
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
@@ -148,4 +148,6 @@ lilac_status lilac_csr_jds(lilac_csr A, int32_t* perm, int32_t* jd_ptr, int32_t*
     LILAC_TRY(down(vals, A->jds_val, vsz * nnz));
     LILAC_TRY(down(nzcnt, A->jds_len, sizeof(int32_t) * n));
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }

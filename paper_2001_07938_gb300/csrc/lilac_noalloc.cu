@@ -90,7 +90,7 @@ using namespace lilac;
 extern "C" lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz,
                                            const int32_t* row_ptr, const int32_t* col_ind,
                                            const void* vals, lilac_dtype dtype, const void* x,
-                                           void* y, void* stream) {
+                                           void* y, void* stream) try {
     if (rows < 0 || ncols < 0 || nnz < 0 || nnz >= (int64_t(1) << 31) ||
         (int64_t)rows + nnz >= (int64_t(1) << 31) || (rows > 0 && (!row_ptr || !y)) ||
         (nnz > 0 && (!col_ind || !vals || !x)) || (dtype != LILAC_F64 && dtype != LILAC_F32)) {
@@ -111,4 +111,6 @@ extern "C" lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t 
                                       scratch, sms, s);
     return noalloc_launch<float>(rows, nnz, row_ptr, col_ind, static_cast<const float*>(vals),
                                  static_cast<const float*>(x), static_cast<float*>(y), scratch, sms, s);
+} catch (...) {
+    return lilac::api_failure();
 }

@@ -89,7 +89,7 @@ using namespace lilac;
 
 extern "C" lilac_status lilac_pagerank(lilac_csr A, void* x, int32_t init_uniform, int32_t iters,
                                        double damping, double* l1_per_iter, lilac_mem where,
-                                       void* stream) {
+                                       void* stream) try {
     LILAC_TRY(check_handle(A));
     if ((A->rows > 0 && !x) || iters < 0 || !(damping >= 0.0 && damping <= 1.0) ||
         (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE)) {
@@ -123,4 +123,6 @@ extern "C" lilac_status lilac_pagerank(lilac_csr A, void* x, int32_t init_unifor
     }
     if (l1_per_iter || where == LILAC_MEM_HOST) LILAC_TRY(check_device_status(A, s));
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }

@@ -367,7 +367,7 @@ void lilac_server_opts_default(lilac_server_opts* o) {
     o->pad = 0;
 }
 
-lilac_status lilac_server_create(const lilac_server_opts* opts, void* stream, lilac_server* out) {
+lilac_status lilac_server_create(const lilac_server_opts* opts, void* stream, lilac_server* out) try {
     if (!out) {
         set_last_error("out is NULL");
         return LILAC_ERR_INVALID_ARG;
@@ -393,9 +393,11 @@ lilac_status lilac_server_create(const lilac_server_opts* opts, void* stream, li
     }
     *out = S;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_server_destroy(lilac_server S) {
+lilac_status lilac_server_destroy(lilac_server S) try {
     if (!S) return LILAC_OK;
     DeviceGuard g(S->device);
     cudaDeviceSynchronize();
@@ -409,11 +411,13 @@ lilac_status lilac_server_destroy(lilac_server S) {
     S->states_d.release();
     delete S;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
 lilac_status lilac_server_add_matrix(lilac_server S, int32_t rows, int32_t ncols, int64_t nnz,
                                      const int32_t* row_ptr, const int32_t* col_ind,
-                                     const double* vals, int32_t* id) {
+                                     const double* vals, int32_t* id) try {
     if (!S || !id || rows <= 0 || ncols <= 0 || nnz < 0 || !row_ptr || (nnz > 0 && (!col_ind || !vals))) {
         set_last_error("invalid argument to lilac_server_add_matrix");
         return LILAC_ERR_INVALID_ARG;
@@ -428,9 +432,11 @@ lilac_status lilac_server_add_matrix(lilac_server S, int32_t rows, int32_t ncols
     S->mats.push_back(m);
     *id = (int32_t)S->mats.size() - 1;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_server_submit(lilac_server S, const lilac_request* r) {
+lilac_status lilac_server_submit(lilac_server S, const lilac_request* r) try {
     if (!S || !r || r->matrix < 0 || r->matrix >= (int32_t)S->mats.size() || !r->in || !r->out ||
         (r->kind != LILAC_REQ_SPMV && r->kind != LILAC_REQ_CG) ||
         (r->kind == LILAC_REQ_SPMV && r->nvec < 1) || (r->kind == LILAC_REQ_CG && r->max_iter < 1) ||
@@ -453,9 +459,11 @@ lilac_status lilac_server_submit(lilac_server S, const lilac_request* r) {
     S->queue.push_back(q);
     S->stats.submitted++;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_server_step(lilac_server S, int32_t* active_out) {
+lilac_status lilac_server_step(lilac_server S, int32_t* active_out) try {
     if (!S) {
         set_last_error("NULL server");
         return LILAC_ERR_INVALID_ARG;
@@ -469,9 +477,11 @@ lilac_status lilac_server_step(lilac_server S, int32_t* active_out) {
     S->stats.queued = (int32_t)S->queue.size();
     S->stats.active = (int32_t)S->active.size();
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_server_poll(lilac_server S, lilac_completion* out, int32_t max, int32_t* n) {
+lilac_status lilac_server_poll(lilac_server S, lilac_completion* out, int32_t max, int32_t* n) try {
     if (!S || !n || max < 0 || (max > 0 && !out)) {
         set_last_error("invalid argument to lilac_server_poll");
         return LILAC_ERR_INVALID_ARG;
@@ -481,15 +491,19 @@ lilac_status lilac_server_poll(lilac_server S, lilac_completion* out, int32_t ma
     S->done.erase(S->done.begin(), S->done.begin() + k);
     *n = k;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
-lilac_status lilac_server_stats(lilac_server S, lilac_server_stats_t* st) {
+lilac_status lilac_server_stats(lilac_server S, lilac_server_stats_t* st) try {
     if (!S || !st) {
         set_last_error("invalid argument to lilac_server_stats");
         return LILAC_ERR_INVALID_ARG;
     }
     *st = S->stats;
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
 
 double lilac_server_now(void) { return now_s(); }

@@ -138,7 +138,7 @@ static lilac_status spmm_impl(lilac_csr A, const T* X, T* Y, int k, int layout, 
 using namespace lilac;
 
 extern "C" lilac_status lilac_spmm(lilac_csr A, const void* X, void* Y, int32_t k, int32_t layout,
-                                   lilac_mem where, void* stream) {
+                                   lilac_mem where, void* stream) try {
     LILAC_TRY(check_handle(A));
     if (k < 1 || k > 32 || (layout != LILAC_LAYOUT_ROWS && layout != LILAC_LAYOUT_VECTORS) ||
         (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE) ||
@@ -156,4 +156,6 @@ extern "C" lilac_status lilac_spmm(lilac_csr A, const void* X, void* Y, int32_t 
         LILAC_TRY(spmm_impl<float>(A, static_cast<const float*>(X), static_cast<float*>(Y), k,
                                    layout, where, s));
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }

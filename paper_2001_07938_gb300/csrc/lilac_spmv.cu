@@ -7,7 +7,7 @@
 using namespace lilac;
 
 extern "C" lilac_status lilac_spmv(lilac_csr A, const void* x, void* y, lilac_mem where,
-                                   void* stream) {
+                                   void* stream) try {
     LILAC_TRY(check_handle(A));
     if ((A->rows > 0 && !y) || (A->ncols > 0 && !x) ||
         (where != LILAC_MEM_HOST && where != LILAC_MEM_DEVICE)) {
@@ -48,4 +48,6 @@ extern "C" lilac_status lilac_spmv(lilac_csr A, const void* x, void* y, lilac_me
         }
     }
     return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
 }
