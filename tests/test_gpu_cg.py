@@ -1,7 +1,7 @@
 """GPU conjugate gradient (lilac_cg through the C ABI) against the FP64 oracle.
 
 The GPU and the oracle reduce in different orders, so their CG iterates
-differ at rounding level; the GPU result is judged by its own true residual
+differ at rounding level; the GPU result is checked by its own true residual
 ||b - A x|| / ||b|| computed by the oracle's SpMV (tolerance 1e-10), by the
 iteration count against the oracle's, and by the distance to the oracle's
 solution on well-conditioned systems.
