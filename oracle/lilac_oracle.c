@@ -3,7 +3,11 @@
  *
  * Plain, sequential FP64 C versions of what the CUDA library computes, written
  * straight from the definitions, so that a reader can check them against the
- * paper by eye.  Only the tests, the smoke check and the benchmark's CPU
+ * paper by eye.  The benchmark also builds this file with OpenMP, to time the
+ * oracle on all host cores: then only the row loop of oracle_spmv is shared
+ * among threads (static schedule); every row is still summed alone in
+ * ascending order and everything else stays sequential, so both builds give
+ * bitwise the same results.  Only the tests, the smoke check and the benchmark's CPU
  * baseline use this file; the library never calls it, and it shares no code,
  * header or constant with the library's sources.
  *
@@ -17,6 +21,18 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads an oracle_spmv call uses: 1 in the sequential build. */
+int32_t oracle_threads(void) {
+#ifdef _OPENMP
+    return (int32_t)omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 /*
  * spmv_csr (Section 3.2, CSR paragraph; the spmv_csr computation of
@@ -25,6 +41,7 @@
  */
 void oracle_spmv(int32_t rows, const int32_t* row_ptr, const int32_t* col_ind,
                  const double* val, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
     for (int32_t i = 0; i < rows; ++i) {
         double s = 0.0;
         for (int32_t j = row_ptr[i]; j < row_ptr[i + 1]; ++j) s += val[j] * x[col_ind[j]];

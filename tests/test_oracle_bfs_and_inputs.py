@@ -52,3 +52,28 @@ def test_banded_structure_and_fp32_exact():
     assert np.all(off[np.abs(np.subtract.outer(np.arange(100), np.arange(100))) > 5] == 0)
     offv = off[off != 0]
     np.testing.assert_array_equal(offv.astype(np.float32).astype(np.float64), offv)
+
+
+def test_all_cores_oracle_is_bitwise_the_sequential_one():
+    """The OpenMP build (timed by the benchmark on all host cores) shares only
+    the rows of an SpMV among threads, each row still summed alone in
+    ascending order: SpMV, CG and PageRank results are bitwise those of the
+    sequential build."""
+    import pytest
+    if oracle.build_parallel() is None:
+        pytest.skip("no OpenMP in the host compiler")
+    A = inputs.spd_random(3000, 20, 20.0, 3)
+    x = inputs.uniform(4, A.n)
+    np.testing.assert_array_equal(oracle.spmv(A.row_ptr, A.col_ind, A.vals, x),
+                                  oracle.spmv(A.row_ptr, A.col_ind, A.vals, x, parallel=True))
+    b = inputs.uniform(5, A.n)
+    xs, its, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=30)
+    xp, itp, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=30, parallel=True)
+    assert its == itp
+    np.testing.assert_array_equal(xs, xp)
+    G = inputs.rmat_transposed(12, 8, seed=2)
+    ps, ls = oracle.pagerank(G.row_ptr, G.col_ind, G.vals, iters=8)
+    pp, lp = oracle.pagerank(G.row_ptr, G.col_ind, G.vals, iters=8, parallel=True)
+    np.testing.assert_array_equal(ps, pp)
+    np.testing.assert_array_equal(ls, lp)
+    assert oracle.threads(False) == 1 and oracle.threads(True) >= 1
