@@ -16,9 +16,14 @@ size_t batch_workspace_bytes(const lilac_csr_s* A, int kind, int prec);
 
 // prec: BP_F64 or BP_F32_RU (then the handle's FP32 values must exist:
 // make_val32); delta: the reliable-update threshold of BP_F32_RU.
-BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* y_out,
+BatchProb make_batch_prob(lilac_csr_s* A, int kind, const void* x_in, void* y_out,
                           const double* b, double* x, double rtol, int max_iter, void* ws,
                           int prec, double delta);
+
+// Build, once, the copy the problems of this handle run on in the batch
+// (the sliced ELL copy for SELL- or SLAB-tuned handles); call before
+// batch_workspace_bytes and make_batch_prob.
+lilac_status batch_prepare_layout(lilac_csr_s* A, int kind, int prec, cudaStream_t s);
 
 struct BatchEngine {
     int device = 0;

@@ -21,32 +21,50 @@ namespace lilac {
 
 enum BatchKind : int { BK_SPMV = 0, BK_CG = 1 };
 enum BatchPrec : int { BP_F64 = 0, BP_F32_RU = 2 };
+// How a problem's SpMV is cut into work items: the handle's STAGED tiles, or
+// groups of chunks of its sliced ELL copy (the layout the handle's tuner
+// picked for SELL and SLAB matrices).
+enum BatchLayout : int { BL_TILES = 0, BL_SELL = 1 };
 
 constexpr int kBatchThreads = 256;
 constexpr int kBatchItems = 2048;   // nonzeros per tile: matches the STAGED tile list
 constexpr int kBatchRows = 1024;    // rows per tile: matches the STAGED tile list
 constexpr int kBatchChunk = 4096;   // vector elements per chunk item
+constexpr int kBatchSellChunks = kBatchThreads / 32;  // SELL chunks per item (one per warp)
 
 struct BatchProb {
-    // matrix (a handle's arrays and STAGED tile list)
+    // matrix (a handle's arrays and STAGED tile list, or its SELL copy)
     const int* row_ptr;
     const int* col_ind;
-    const double* val;
-    const float* val32;  // FP32 values (BP_F32_RU)
+    const double* val;   // FP64 values (FP64 handles; null for FP32 handles)
+    const float* val32;  // FP32 values: the handle's own (FP32 handles) or its FP32 copy
     const TileDesc* tiles;
     const LongRow* longs;
+    // split rows: STAGED chunk sums / SELL piece sums, arrival counters and
+    // epilogue sums (per problem, in its workspace)
     double* long_part;
     unsigned* long_cnt;
     double* long_red;
     int rows;
-    int ntiles;
-    int nlong;
+    int ntiles;  // SpMV-phase items: tiles (BL_TILES) or chunk groups (BL_SELL)
+    int nlong;   // split rows
     int kind;
     int nchunks;
     int prec;
-    // SpMV: y = A x
-    const double* x_in;
-    double* y_out;
+    int layout;
+    int f32;     // 1: FP32 handle (FP32 values; SpMV vectors x_in / y_out are float)
+    // BL_SELL: the handle's sliced ELL copy (values of the handle's type)
+    const int* scptr;
+    const int* scrow;
+    const int* scol;
+    const void* sval;
+    const int4* ssplits;
+    const int* spiece_split;
+    int snchunks;
+    int spad;
+    // SpMV: y = A x (double, or float for FP32 handles)
+    const void* x_in;
+    void* y_out;
     // CG: b, x (FP64); r, p, q (FP64) or r32, p32, q32 and the FP32 correction d32
     const double* b;
     double* x;
@@ -87,9 +105,10 @@ __device__ __forceinline__ bool batch_ru_due(const CgState* st) {
 }
 
 // Epilogues of the batched SpMV phases (row r's sum s; up to two FP64 sums).
+template <class T>
 struct BEpiStore {  // y = A x
-    double* y;
-    __device__ void row(int r, double s, double*) const { y[r] = s; }
+    T* y;
+    __device__ void row(int r, T s, double*) const { y[r] = s; }
 };
 template <class T>
 struct BEpiPq {  // q = A p, p.q
@@ -157,7 +176,7 @@ __device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t
         __syncthreads();
         AccT sum = AccT(0);
         for (int k = tid; k < t.k1 - t.k0; k += THREADS) sum += prod[k];
-        sum = block_sum_all<THREADS, AccT>(sum, sh);
+        sum = block_sum_lead<THREADS, AccT>(sum, sh);
         if (tid == 0) {
             const int lid = t.r0, slot = -t.r1 - 1;
             P.long_part[slot] = double(sum);
@@ -175,6 +194,83 @@ __device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t
             }
         }
     }
+}
+
+// One chunk group of a problem's sliced ELL copy (BL_SELL): warp w sums chunk
+// kBatchSellChunks * idx + w the way spmv_sell_kernel does (one lane per row
+// or piece, one FMA per element in element order, padding column -1).  A
+// lane holding a whole row runs the epilogue; a piece of a split row goes to
+// its slot, and the last piece to arrive adds the pieces in piece order and
+// runs the epilogue (its sums to long_red).  The group's FP64 sums are left
+// in red[0..1] of every thread.
+template <class ValT, class VecT, class AccT, class Epi>
+__device__ __forceinline__ void batch_sell_item(const BatchProb& P, int idx,
+                                                const ValT* __restrict__ val,
+                                                const VecT* __restrict__ xin, const Epi& epi,
+                                                double* red) {
+    constexpr int UNR = 8;
+    const int lane = threadIdx.x & 31;
+    const int ch = idx * kBatchSellChunks + (int)(threadIdx.x >> 5);
+    if (ch >= P.snchunks) return;
+    const int base = __ldg(P.scptr + ch);
+    const int width = (__ldg(P.scptr + ch + 1) - base) >> 5;
+    const int who = __ldg(P.scrow + (size_t)ch * 32 + lane);
+    const ValT* __restrict__ vp = val + base + lane;
+    const int* __restrict__ cp = P.scol + base + lane;
+    AccT acc = AccT(0);
+    for (int k = 0; k < width; k += UNR) {
+        ValT vv[UNR];
+        int cc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const bool q = k + u < width;
+            vv[u] = q ? ld_stream(vp + 32 * (k + u)) : ValT(0);
+            cc[u] = q ? ld_stream(cp + 32 * (k + u)) : -1;
+        }
+        VecT xx[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) xx[u] = cc[u] >= 0 ? __ldg(xin + cc[u]) : VecT(0);
+        if (k + UNR <= width) {
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xx[u]);
+        } else {
+            // the bound is the same for the whole warp: skipped FMAs cost nothing
+#pragma unroll
+            for (int u = 0; u < UNR; ++u)
+                if (k + u < width) acc += AccT(vv[u]) * AccT(xx[u]);
+        }
+    }
+    if (who >= 0) {
+        epi.row(who, acc, red);
+    } else if (who < -1) {
+        const int p = -who - 2;
+        P.long_part[p] = double(acc);
+        __threadfence();
+        const int lid = __ldg(P.spiece_split + p);
+        const int4 sp = P.ssplits[lid];
+        if (atomicAdd(&P.long_cnt[lid], 1u) == (unsigned)sp.z - 1u) {
+            __threadfence();
+            AccT rs = AccT(0);
+            for (int j = 0; j < sp.z; ++j) rs += AccT(__ldcg(&P.long_part[sp.y + j]));
+            double lred[2] = {0.0, 0.0};
+            epi.row(sp.x, rs, lred);
+            P.long_red[lid * kMaxRed] = lred[0];
+            P.long_red[lid * kMaxRed + 1] = lred[1];
+            P.long_cnt[lid] = 0u;
+        }
+    }
+}
+
+// One SpMV-phase item of a problem in its layout.
+template <class ValT, class VecT, class AccT, class Epi>
+__device__ __forceinline__ void batch_item(const BatchProb& P, int idx, const ValT* __restrict__ val,
+                                           const ValT* __restrict__ sval,
+                                           const VecT* __restrict__ xin, const Epi& epi,
+                                           double* red, unsigned char* smem, int* rp_s, AccT* sh) {
+    if (P.layout == BL_SELL)
+        batch_sell_item<ValT, VecT, AccT>(P, idx, sval, xin, epi, red);
+    else
+        batch_tile<ValT, VecT, AccT>(P, P.tiles[idx], val, xin, epi, red, smem, rp_s, sh);
 }
 
 // Problem-level ends of the SpMV phases (last tile of the problem, thread 0).
@@ -232,20 +328,34 @@ static __global__ void __launch_bounds__(kBatchThreads)
         // uniform over the block: flags change only in earlier launches
         if (MODE == 0 && kind == BK_CG && cg_done(P.st)) continue;
         if (MODE == 1 && !(kind == BK_CG && P.prec == BP_F32_RU && batch_ru_due(P.st))) continue;
-        const TileDesc t = P.tiles[item.idx];
         double red[2] = {0.0, 0.0};
+        const float* sv32 = static_cast<const float*>(P.sval);
+        const double* sv64 = static_cast<const double*>(P.sval);
         if (MODE == 1) {
-            batch_tile<double, double, double>(P, t, P.val, P.x, BEpiResid{P.r32, P.b}, red, smem,
-                                               rp_s, sh);
+            // FP64 residual b - A x with the handle's values (FP32 ones promoted)
+            if (P.f32)
+                batch_item<float, double, double>(P, item.idx, P.val32, sv32, P.x,
+                                                  BEpiResid{P.r32, P.b}, red, smem, rp_s, sh);
+            else
+                batch_item<double, double, double>(P, item.idx, P.val, sv64, P.x,
+                                                   BEpiResid{P.r32, P.b}, red, smem, rp_s, sh);
         } else if (kind == BK_SPMV) {
-            batch_tile<double, double, double>(P, t, P.val, P.x_in, BEpiStore{P.y_out}, red, smem,
-                                               rp_s, sh);
+            if (P.f32)
+                batch_item<float, float, float>(P, item.idx, P.val32, sv32,
+                                                static_cast<const float*>(P.x_in),
+                                                BEpiStore<float>{static_cast<float*>(P.y_out)}, red,
+                                                smem, rp_s, shf);
+            else
+                batch_item<double, double, double>(P, item.idx, P.val, sv64,
+                                                   static_cast<const double*>(P.x_in),
+                                                   BEpiStore<double>{static_cast<double*>(P.y_out)},
+                                                   red, smem, rp_s, sh);
         } else if (P.prec == BP_F32_RU) {
-            batch_tile<float, float, float>(P, t, P.val32, P.p32, BEpiPq<float>{P.q32, P.p32}, red,
-                                            smem, rp_s, shf);
+            batch_item<float, float, float>(P, item.idx, P.val32, sv32, P.p32,
+                                            BEpiPq<float>{P.q32, P.p32}, red, smem, rp_s, shf);
         } else {
-            batch_tile<double, double, double>(P, t, P.val, P.p, BEpiPq<double>{P.q, P.p}, red,
-                                               smem, rp_s, sh);
+            batch_item<double, double, double>(P, item.idx, P.val, sv64, P.p,
+                                               BEpiPq<double>{P.q, P.p}, red, smem, rp_s, sh);
         }
         if (kind == BK_CG) {
             // this tile's share of the sums; the problem's last tile finishes

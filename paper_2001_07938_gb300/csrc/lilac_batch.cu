@@ -20,40 +20,84 @@ namespace lilac {
 static_assert(kBatchItems == kTileNnz && kBatchRows == kTileRows,
               "batched tiles are the handles' STAGED tiles");
 
+// The layout a problem of this handle runs in: the sliced ELL copy's chunk
+// groups when the handle's tuner chose a sliced ELL kernel (SELL, or SLAB,
+// whose column slabs need a whole SM each and cannot share a persistent CTA
+// with other problems) and the copy holds the values the phase multiplies
+// (an FP64 handle's FP32 copy for mixed precision is only in CSR form); the
+// STAGED tiles otherwise.
+static bool batch_wants_sell(const lilac_csr_s* A, int kind, int prec) {
+    if (A->variant != LILAC_VARIANT_SELL && A->variant != LILAC_VARIANT_SLAB) return false;
+    if (kind == BK_CG && prec == BP_F32_RU && A->dtype == LILAC_F64) return false;
+    return true;
+}
+
+static bool batch_uses_sell(const lilac_csr_s* A, int kind, int prec) {
+    return batch_wants_sell(A, kind, prec) && A->sell_built;
+}
+
+// Build the sliced ELL copy a problem of this handle would run on (once).
+lilac_status batch_prepare_layout(lilac_csr_s* A, int kind, int prec, cudaStream_t s) {
+    if (batch_wants_sell(A, kind, prec) && !A->sell_built) LILAC_TRY(ensure_sell(A, s));
+    return LILAC_OK;
+}
+
+static int batch_items(const lilac_csr_s* A, int kind, int prec) {
+    return batch_uses_sell(A, kind, prec)
+               ? (A->sell_nchunks + kBatchSellChunks - 1) / kBatchSellChunks
+               : A->ntiles;
+}
+
 size_t batch_workspace_bytes(const lilac_csr_s* A, int kind, int prec) {
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
     const size_t n = (size_t)std::max(1, A->rows);
     const size_t nchunks = (n + kBatchChunk - 1) / kBatchChunk;
+    const bool sell = batch_uses_sell(A, kind, prec);
+    const size_t nlong = (size_t)std::max(1, sell ? A->sell_nsplit : A->nlong);
+    const size_t nparts = (size_t)std::max(1, sell ? A->sell_npieces : A->nlong_chunks);
     size_t bytes = al(sizeof(CgState)) + al(4 * sizeof(unsigned));
-    bytes += al(sizeof(double) * (2 * (size_t)A->ntiles + nchunks + 1));
-    bytes += al(sizeof(double) * (size_t)std::max(1, A->nlong_chunks));
-    bytes += al(sizeof(double) * kMaxRed * (size_t)std::max(1, A->nlong));
-    bytes += al(sizeof(unsigned) * (size_t)std::max(1, A->nlong));
+    bytes += al(sizeof(double) * (2 * (size_t)batch_items(A, kind, prec) + nchunks + 1));
+    bytes += al(sizeof(double) * nparts);
+    bytes += al(sizeof(double) * kMaxRed * nlong);
+    bytes += al(sizeof(unsigned) * nlong);
     if (kind == BK_CG) bytes += prec == BP_F32_RU ? 4 * al(sizeof(float) * n) : 3 * al(sizeof(double) * n);
     return bytes;
 }
 
 // Fill a problem descriptor from a handle and a workspace block (which must
 // hold batch_workspace_bytes and have been zeroed).
-BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* y_out,
+BatchProb make_batch_prob(lilac_csr_s* A, int kind, const void* x_in, void* y_out,
                           const double* b, double* x, double rtol, int max_iter, void* ws,
                           int prec, double delta) {
     auto al = [](size_t b_) { return (b_ + 255) & ~size_t(255); };
     unsigned char* w = static_cast<unsigned char*>(ws);
     const size_t n = (size_t)std::max(1, A->rows);
     const size_t nchunks = (n + kBatchChunk - 1) / kBatchChunk;
+    const int pr = kind == BK_CG ? prec : BP_F64;
+    const bool sell = batch_uses_sell(A, kind, pr);
     BatchProb P{};
     P.row_ptr = A->row_ptr.as<int>();
     P.col_ind = A->col_ind.as<int>();
-    P.val = A->val.as<double>();
-    P.val32 = A->val32.as<float>();
-    P.prec = kind == BK_CG ? prec : BP_F64;
+    P.f32 = A->dtype == LILAC_F32 ? 1 : 0;
+    P.val = P.f32 ? nullptr : A->val.as<double>();
+    P.val32 = P.f32 ? A->val.as<float>() : A->val32.as<float>();
+    P.prec = pr;
     P.delta2 = delta * delta;
     P.tiles = A->tiles.as<TileDesc>();
     P.longs = A->longs.as<LongRow>();
     P.rows = A->rows;
-    P.ntiles = A->ntiles;
-    P.nlong = A->nlong;
+    P.layout = sell ? BL_SELL : BL_TILES;
+    P.ntiles = batch_items(A, kind, pr);
+    P.nlong = sell ? A->sell_nsplit : A->nlong;
+    if (sell) {
+        P.scptr = A->sell_cptr.as<int>();
+        P.scrow = A->sell_crow.as<int>();
+        P.scol = A->sell_col.as<int>();
+        P.sval = A->sell_val.p;
+        P.ssplits = A->sell_splits.as<int4>();
+        P.spiece_split = A->sell_piece_split.as<int>();
+        P.snchunks = A->sell_nchunks;
+    }
     P.kind = kind;
     P.nchunks = (int)((A->rows + kBatchChunk - 1) / kBatchChunk);
     P.x_in = x_in;
@@ -67,13 +111,15 @@ BatchProb make_batch_prob(lilac_csr_s* A, int kind, const double* x_in, double* 
     P.cnt = reinterpret_cast<unsigned*>(w);
     w += al(4 * sizeof(unsigned));
     P.part = reinterpret_cast<double*>(w);
-    w += al(sizeof(double) * (2 * (size_t)A->ntiles + nchunks + 1));
+    const size_t nlong = (size_t)std::max(1, P.nlong);
+    const size_t nparts = (size_t)std::max(1, sell ? A->sell_npieces : A->nlong_chunks);
+    w += al(sizeof(double) * (2 * (size_t)P.ntiles + nchunks + 1));
     P.long_part = reinterpret_cast<double*>(w);
-    w += al(sizeof(double) * (size_t)std::max(1, A->nlong_chunks));
+    w += al(sizeof(double) * nparts);
     P.long_red = reinterpret_cast<double*>(w);
-    w += al(sizeof(double) * kMaxRed * (size_t)std::max(1, A->nlong));
+    w += al(sizeof(double) * kMaxRed * nlong);
     P.long_cnt = reinterpret_cast<unsigned*>(w);
-    w += al(sizeof(unsigned) * (size_t)std::max(1, A->nlong));
+    w += al(sizeof(unsigned) * nlong);
     if (kind == BK_CG && P.prec == BP_F32_RU) {
         float** v[4] = {&P.r32, &P.p32, &P.q32, &P.d32};
         for (float** f : v) {
@@ -263,10 +309,6 @@ static lilac_status batch_check(lilac_batch B, int32_t count, const lilac_csr* A
     }
     for (int i = 0; i < count; ++i) {
         LILAC_TRY(check_handle(A[i]));
-        if (A[i]->dtype != LILAC_F64) {
-            set_last_error("batched calls take FP64 matrices (mixed precision derives FP32 values)");
-            return LILAC_ERR_DTYPE;
-        }
         if (A[i]->device != B->eng.device) {
             set_last_error("matrix lives on another device than the batch");
             return LILAC_ERR_INVALID_ARG;
@@ -299,7 +341,7 @@ static lilac_status batch_workspaces(lilac_batch B, int32_t count, const lilac_c
 }
 
 extern "C" lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
-                                         const double* const* x, double* const* y, void* stream) try {
+                                         const void* const* x, void* const* y, void* stream) try {
     LILAC_TRY(batch_check(B, count, A));
     if (count > 0 && (!x || !y)) {
         set_last_error("x and y arrays are required");
@@ -308,6 +350,7 @@ extern "C" lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lil
     if (count == 0) return LILAC_OK;
     DeviceGuard g(B->eng.device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int i = 0; i < count; ++i) LILAC_TRY(batch_prepare_layout(A[i], BK_SPMV, BP_F64, s));
     std::vector<void*> ws;
     LILAC_TRY(batch_workspaces(B, count, A, BK_SPMV, BP_F64, ws, s));
     std::vector<BatchProb> probs;
@@ -329,18 +372,25 @@ extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac
         set_last_error("invalid argument to lilac_batch_cg");
         return LILAC_ERR_INVALID_ARG;
     }
-    for (int i = 0; i < count; ++i)
+    for (int i = 0; i < count; ++i) {
         if (A[i]->rows != A[i]->ncols || A[i]->rows == 0) {
             set_last_error("lilac_batch_cg needs square, non-empty matrices");
             return LILAC_ERR_INVALID_ARG;
         }
+        if (A[i]->dtype == LILAC_F32 && precision != 2) {
+            set_last_error("FP32 matrices run batched CG in precision 2 (FP32 CG, FP64 updates)");
+            return LILAC_ERR_DTYPE;
+        }
+    }
     if (count == 0) return LILAC_OK;
     DeviceGuard g(B->eng.device);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     std::vector<void*> ws;
     const int prec = precision == 2 ? BP_F32_RU : BP_F64;
-    if (prec == BP_F32_RU)
-        for (int i = 0; i < count; ++i) LILAC_TRY(make_val32(A[i], s));
+    for (int i = 0; i < count; ++i) {
+        if (prec == BP_F32_RU && A[i]->dtype == LILAC_F64) LILAC_TRY(make_val32(A[i], s));
+        LILAC_TRY(batch_prepare_layout(A[i], BK_CG, prec, s));
+    }
     LILAC_TRY(batch_workspaces(B, count, A, BK_CG, prec, ws, s));
     std::vector<BatchProb> probs;
     for (int i = 0; i < count; ++i)

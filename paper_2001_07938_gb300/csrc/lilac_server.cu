@@ -200,6 +200,14 @@ static lilac_status admit(lilac_server_s* S) {
         bool ok = false;
         LILAC_TRY(make_resident(S, q->r.matrix, &ok));
         if (!ok) break;  // wait for memory to be released
+        {
+            // the copy the batched kernels run on (once per matrix)
+            const int kind = q->r.kind == LILAC_REQ_SPMV ? BK_SPMV : BK_CG;
+            LILAC_TRY(batch_prepare_layout(m.h, kind, req_prec(q), S->stream));
+            lilac_csr_info_t info;
+            lilac_csr_info(m.h, &info);
+            m.bytes = info.device_bytes;
+        }
         const size_t need = request_bytes(S, q);
         // a mixed-precision solve derives the matrix's FP32 values on first use
         const bool needs_val32 = req_prec(q) == BP_F32_RU && !m.h->val32_valid;
