@@ -163,9 +163,14 @@ class Workload:
     `unit` x seconds per step."""
     flush_l2 = False
     work_per_step = 1.0
+    traffic_key = None  # the profiles/traffic.json entry of the dominant kernel
 
     def __init__(self, L, torch):
         self.L, self.torch = L, torch
+
+    def extra(self):
+        """Further measurements of the workload for its JSON object."""
+        return {}
 
     def _matrix(self, A):
         L = self.L
@@ -193,6 +198,7 @@ class Workload:
 
 class CG75k(Workload):
     name = "cg_spd_n75000_75it"
+    traffic_key = "cg75k"
     unit = "solves/s"
     dtype = "f64"
     iters = 75
@@ -253,17 +259,17 @@ class CG75k(Workload):
         L.lilac_cg(self.M.handle, self.bh.data_ptr(), self.xh.data_ptr(), L.LILAC_MEM_HOST,
                    self.opts, want_info=False)
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         """Oracle CG on the same system; a full 75-iteration solve if it fits
         the budget, else the first k iterations scaled to a solve."""
         import oracle
         A, b = self.A, self.b
         t0 = time.perf_counter()
-        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=2, rtol=0.0)
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=2, rtol=0.0, parallel=parallel)
         t_it = (time.perf_counter() - t0) / 2
         k = int(max(1, min(self.iters, budget_s / max(t_it, 1e-9))))
         t0 = time.perf_counter()
-        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=k, rtol=0.0)
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=k, rtol=0.0, parallel=parallel)
         t = time.perf_counter() - t0
         solve_s = t * self.iters / k
         sample = (f"one full {self.iters}-iteration oracle CG solve" if k == self.iters else
@@ -276,6 +282,7 @@ class CG75k(Workload):
 
 class SpMV2D(Workload):
     name = "spmv_laplacian2d_m64_1000calls"
+    traffic_key = "spmv2d"
     unit = "GB/s"
     dtype = "f64"
     flush_l2 = True
@@ -331,6 +338,45 @@ class SpMV2D(Workload):
         ms = sum(evs[2 * i].elapsed_time(evs[2 * i + 1]) for i in range(n))
         return ms / n, n, self.spmv_bytes(), _kernel_name(self.M)
 
+    def extra(self):
+        """The same 1000 calls captured once into one CUDA graph and replayed:
+        the launch cost of the API calls removed (L2 flushed before each
+        replay, as between the API steps)."""
+        torch, L, h = self.torch, self.L, self.M.handle
+        flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda")
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(3):
+                L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE, side.cuda_stream)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cs = torch.cuda.current_stream().cuda_stream
+            for _ in range(self.calls):
+                L.lilac_spmv(h, self.px, self.py, L.LILAC_MEM_DEVICE, cs)
+        stream = torch.cuda.current_stream()
+        for _ in range(3):
+            g.replay()
+        reps = 10
+        ms = []
+        for k in range(reps):
+            flush.fill_(k & 0xFF)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        del g
+        t = sum(ms) / reps
+        return {"graph_1000_calls": {"us_per_call": 1000.0 * t / self.calls,
+                                     "gbs": self.calls * self.spmv_bytes() / (t / 1000.0) / 1e9,
+                                     "replays": reps,
+                                     "note": "1000 lilac_spmv calls captured in one CUDA graph"},
+                "api_1000_calls": {"us_per_call": None}}
+
     def e2e_setup(self):
         torch = self.torch
         self.xh = torch.from_numpy(self.x).pin_memory()
@@ -343,13 +389,13 @@ class SpMV2D(Workload):
         for _ in range(self.calls):
             L.lilac_spmv(h, px, py, L.LILAC_MEM_HOST)
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         import oracle
         A, x = self.A, self.x
         t0 = time.perf_counter()
         n = 0
         while time.perf_counter() - t0 < min(budget_s, 2.0) or n == 0:
-            oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
+            oracle.spmv(A.row_ptr, A.col_ind, A.vals, x, parallel=parallel)
             n += 1
         t = (time.perf_counter() - t0) / n
         return self.spmv_bytes() / t / 1e9, f"{n} oracle SpMV calls on the same matrix"
@@ -360,17 +406,22 @@ class SpMV2D(Workload):
 
 class PageRank22(Workload):
     name = "pagerank_rmat22_20it"
+    traffic_key = "pagerank22"
     unit = "GB/s"
     dtype = "f32"
     iters = 20
     scale = 22  # --rmat-scale: smaller graphs of the same recipe for profiling
+    permute = True  # --rmat-unpermuted: the graph without the random vertex relabelling
 
-    def __init__(self, L, torch):
+    def __init__(self, L, torch, permute=None):
         super().__init__(L, torch)
         from paper_2001_07938_gb300 import inputs
-        if self.scale != 22:
-            self.name = f"pagerank_rmat{self.scale}_20it"
-        self.A = inputs.workload_rmat_pagerank(scale=self.scale)
+        if permute is not None:
+            self.permute = permute
+        self.name = f"pagerank_rmat{self.scale}{'' if self.permute else '_unpermuted'}_20it"
+        if not self.permute:
+            self.traffic_key = "pagerank22_unpermuted"
+        self.A = inputs.workload_rmat_pagerank(scale=self.scale, permute=self.permute)
         self.work_per_step = self.iters * self.iter_bytes() / 1e9
 
     def iter_bytes(self):
@@ -381,7 +432,10 @@ class PageRank22(Workload):
     def config(self):
         A = self.A
         return {"workload": self.name,
-                "matrix": "R-MAT a=.57 b=c=.19, relabelled, no self-loops/duplicates, transposed",
+                "matrix": ("R-MAT a=.57 b=c=.19, " +
+                           ("relabelled (seeded random permutation)" if self.permute else
+                            "unpermuted (R-MAT vertex ids)") +
+                           ", no self-loops/duplicates, transposed"),
                 "n": A.n, "nnz": A.nnz, "iterations": self.iters, "damping": 0.85,
                 "precision": "fp32 (D, L1 in fp64)", "index": "int32",
                 "l2": f"inputs larger than L2: matrix {A.nnz * 8 / 1e6:.0f} MB, no flush"}
@@ -414,16 +468,16 @@ class PageRank22(Workload):
         L.lilac_pagerank(self.M.handle, self.xh.data_ptr(), 1, self.iters, 0.85, None,
                          L.LILAC_MEM_HOST)
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         import oracle
         A = self.A
         t0 = time.perf_counter()
-        oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=1)
+        oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=1, parallel=parallel)
         t1 = time.perf_counter() - t0
         k = int(max(1, min(self.iters, budget_s / max(t1, 1e-9))))
         if k > 1:
             t0 = time.perf_counter()
-            oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=k)
+            oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=k, parallel=parallel)
             t1 = (time.perf_counter() - t0) / k
         return self.iter_bytes() / t1 / 1e9, f"{k} oracle PageRank iterations"
 
@@ -433,6 +487,7 @@ class PageRank22(Workload):
 
 class IR192(Workload):
     name = "cg_mixed_poisson3d_m192_to_1e-10"
+    traffic_key = "ir192"
     unit = "solves/s"
     dtype = "f32 inner / f64 refinement"
     precision = 2  # --ir-precision: 2 reliable updates, 1 restarted refinement
@@ -528,17 +583,17 @@ class IR192(Workload):
         L.lilac_cg(self.M.handle, self.bh.data_ptr(), self.xh.data_ptr(), L.LILAC_MEM_HOST,
                    self.opts, want_info=False)
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         """Oracle FP64 CG: k iterations timed, scaled to the FP64 CG iteration
         count to 1e-10 (a full oracle solve takes far longer than a step)."""
         import oracle
         A, b = self.A, self.b
         t0 = time.perf_counter()
-        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=2, rtol=0.0)
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=2, rtol=0.0, parallel=parallel)
         t_it = (time.perf_counter() - t0) / 2
         k = int(max(1, min(200, budget_s / max(t_it, 1e-9))))
         t0 = time.perf_counter()
-        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=k, rtol=0.0)
+        oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=k, rtol=0.0, parallel=parallel)
         t_it = (time.perf_counter() - t0) / k
         n_it = self.fp64_iters or 1400
         return 1.0 / (t_it * n_it), (f"{k} oracle FP64 CG iterations, scaled to {n_it} "
@@ -552,6 +607,7 @@ class SpMM8(Workload):
     """Y = A X for 8 vectors at once (row-major X), the random SPD n=75,000
     FP64 matrix: each nonzero is streamed once for all 8 vectors."""
     name = "spmm_spd_n75000_k8"
+    traffic_key = "spmm8"
     unit = "GB/s"
     dtype = "f64"
     k = 8
@@ -620,7 +676,7 @@ class SpMM8(Workload):
     def e2e_step(self):
         self.M.spmm(self.Xh, self.Yh, self.k)
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         import oracle
         A = self.A
         x = np.random.default_rng(0).random(A.ncols)
@@ -639,6 +695,7 @@ class BFS22(Workload):
     the vertex of largest out-degree; GTEPS = edges of the reached component /
     time (the GAP convention)."""
     name = "bfs_rmat22"
+    traffic_key = "bfs22"
     unit = "GTEPS"
     dtype = "int32"
 
@@ -701,7 +758,7 @@ class BFS22(Workload):
     def close(self):
         self.M.close()
 
-    def cpu_sample(self, budget_s):
+    def cpu_sample(self, budget_s, parallel=False):
         import oracle
         A = self.A
         rows = np.repeat(np.arange(A.n, dtype=np.int32), np.diff(A.row_ptr))
@@ -971,7 +1028,7 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    wl = WORKLOADS[args.workload](None, None)
+    wl = WORKLOADS["cg75k" if args.workload == "all" else args.workload](None, None)
     steps, warm = args.steps, args.warmup
     budget = max(0.05, args.ref_seconds / max(1, steps + warm))
     vals, sample = [], ""
@@ -993,31 +1050,47 @@ def run_reference(args):
     return 0
 
 
-def run_lilac(args):
-    import torch
-    from paper_2001_07938_gb300 import build as lbuild
-    from paper_2001_07938_gb300 import lilac as L
+VARIANT_NAMES = {v: k for k, v in VARIANT_CODES.items()}
 
-    ws, rank, local = _dist()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    else:
-        torch.cuda.set_device(0)
-    if rank == 0:
-        lbuild.build()
-    if ws > 1:
-        dist.barrier()
-    L.load()
 
-    barrier, max_over_ranks = collectives(ws, "cuda")
+def _tuner(wl):
+    """The kernel the handle runs and the autotuner's trial (ms per call)."""
+    M = getattr(wl, "M", None)
+    if M is None:
+        return None
+    info = M.info()
+    table = M.tune_table()
+    return {"variant": VARIANT_NAMES.get(info["variant"], str(info["variant"])),
+            "width": info["vector_width"],
+            "forced": FORCED_VARIANT is not None,
+            "trial_ms_per_call": {f"{VARIANT_NAMES.get(t['variant'], t['variant'])}:{t['width']}":
+                                  round(t["ms"], 5) for t in table}}
 
-    global FORCED_VARIANT
-    if args.variant:
-        name, _, width = args.variant.partition(":")
-        FORCED_VARIANT = (VARIANT_CODES[name], int(width or 0))
-    wl = WORKLOADS[args.workload](L, torch)
+
+def _cpu_baseline(wl, budget_s):
+    """The oracle on one host core (the paper's sequential -O2 baseline kind),
+    and the same oracle with its SpMV rows shared among all host cores."""
+    import oracle
+    v, sample = wl.cpu_sample(budget_s)
+    out = {"value": v, "unit": wl.unit, "cores": 1, "kind": "oracle", "sample": sample}
+    try:
+        cores = oracle.threads(True)
+        vp, sp = wl.cpu_sample(budget_s / 2, parallel=True)
+        out["all_cores"] = {"value": vp, "unit": wl.unit, "cores": cores, "kind": "oracle",
+                            "sample": sp + " (OpenMP build: SpMV rows on all cores, static "
+                                           "schedule, results bitwise the sequential ones)"}
+    except RuntimeError as e:
+        out["all_cores"] = {"unavailable": str(e)}
+    return out
+
+
+def measure(wl, args, ctx, cpu_budget_s=20.0):
+    """Warm up, time K steps with CUDA events (clocks sampled meanwhile), the
+    dominant kernel's launches, the end-to-end form through the C ABI with
+    host buffers, and the CPU oracle; returns the workload's JSON object
+    (rank 0) or None."""
+    torch, ws, rank = ctx["torch"], ctx["ws"], ctx["rank"]
+    barrier, max_over_ranks = ctx["barrier"], ctx["max_over_ranks"]
     wl.setup()
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device="cuda") if wl.flush_l2 else None
@@ -1052,7 +1125,7 @@ def run_lilac(args):
     peak, peak_kind = _peaks()
     achieved = kern_bytes / (kern_ms / 1000.0) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _ncu_traffic(args.workload), "kernel": kname,
+                "frac": achieved / peak, "traffic": _ncu_traffic(wl.traffic_key), "kernel": kname,
                 "algorithmic_bytes_per_launch": kern_bytes, "avg_launch_ms": kern_ms,
                 "launches_timed": n_kern,
                 "peak_kind": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs)"}
@@ -1070,6 +1143,7 @@ def run_lilac(args):
                     "launches_timed": n_kern,
                     "peak_kind": "of nominal FP64 rate (152 SMs x 2 FMA/clk x 2.07 GHz; "
                                  "a DFMA loop measured 1.20 TFLOP/s)"}
+    extra = wl.extra()
 
     # end to end through the C ABI with pinned host buffers
     wl.e2e_setup()
@@ -1085,25 +1159,74 @@ def run_lilac(args):
     e2e_ms = max_over_ranks(e0.elapsed_time(e1))
     e2e = {"value": ws * K * wl.work_per_step / (e2e_ms / 1000.0), "unit": wl.unit,
            "h2d_bytes_per_step": wl.e2e_bytes[0], "d2h_bytes_per_step": wl.e2e_bytes[1]}
-
-    if rank == 0:
-        cpu = None
-        if not args.no_cpu_baseline and ws == 1:
-            v, sample = wl.cpu_sample(budget_s=20.0)
-            cpu = {"value": v, "unit": wl.unit, "cores": 1, "kind": "oracle", "sample": sample}
-        line = {"metric": METRIC, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": K,
-                "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
-                "config": wl.config() | {"parallelism": f"replicas{ws}"},
-                "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
-                               "p99": float(np.percentile(step_ms, 99))},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                **({"roofline_hbm": roofline_hbm} if roofline_hbm else {}),
-                "gpu_launches": wl.launches_per_step * K,
-                "clocks": clk, "check": check,
-                "spmv": {"gbs": achieved, "hbm_frac": achieved / peak}}
-        print(json.dumps(line), flush=True)
+    tuner = _tuner(wl)
     wl.close()
+    if rank != 0:
+        return None
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        cpu = _cpu_baseline(wl, cpu_budget_s)
+    line = {"metric": METRIC, "value": value, "unit": wl.unit, "n_gpus": ws, "steps": K,
+            "warmup": args.warmup, "ms_per_step": total_ms / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic",
+            "config": wl.config() | {"parallelism": f"replicas{ws}"},
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            **({"roofline_hbm": roofline_hbm} if roofline_hbm else {}),
+            "gpu_launches": wl.launches_per_step * K,
+            "clocks": clk, "check": check, "tuner": tuner,
+            "spmv": {"gbs": achieved, "hbm_frac": achieved / peak}}
+    if extra:
+        if "api_1000_calls" in extra:
+            extra["api_1000_calls"] = {"us_per_call": 1000.0 * (total_ms / K) / wl.calls,
+                                       "note": "1000 lilac_spmv API calls per step"}
+        line.update(extra)
+    return line
+
+
+# The default run: the FP64 CG workload is the headline; the other configs
+# of the benchmark suite ride along as keyed objects of the same line.
+ALSO = [("spmv2d", "spmv2d", {}), ("pagerank22", "pagerank22", {}),
+        ("pagerank22_unpermuted", "pagerank22", {"permute": False}), ("ir192", "ir192", {})]
+SUB_KEYS_DROP = ("metric", "n_gpus", "scaling", "vs_baseline", "data", "higher_is_better")
+
+
+def run_lilac(args):
+    import torch
+    from paper_2001_07938_gb300 import build as lbuild
+    from paper_2001_07938_gb300 import lilac as L
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0:
+        lbuild.build()
+    if ws > 1:
+        dist.barrier()
+    L.load()
+
+    barrier, max_over_ranks = collectives(ws, "cuda")
+    ctx = {"torch": torch, "ws": ws, "rank": rank, "barrier": barrier,
+           "max_over_ranks": max_over_ranks}
+
+    global FORCED_VARIANT
+    if args.variant:
+        name, _, width = args.variant.partition(":")
+        FORCED_VARIANT = (VARIANT_CODES[name], int(width or 0))
+    head = "cg75k" if args.workload == "all" else args.workload
+    line = measure(WORKLOADS[head](L, torch), args, ctx)
+    if args.workload == "all" and not args.variant:
+        for key, wname, kw in ALSO:
+            sub = measure(WORKLOADS[wname](L, torch, **kw), args, ctx, cpu_budget_s=10.0)
+            if rank == 0:
+                line[key] = {k: v for k, v in sub.items() if k not in SUB_KEYS_DROP}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if ws > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -1116,8 +1239,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["lilac", "reference"], default="lilac")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["served", "marshal"],
-                    default="cg75k")
+    ap.add_argument("--workload", choices=["all"] + sorted(WORKLOADS) + ["served", "marshal"],
+                    default="all",
+                    help="all (default): the FP64 CG headline with the 2D Laplacian SpMV, "
+                         "PageRank (relabelled and unpermuted R-MAT) and mixed-precision CG "
+                         "workloads as keyed objects of the same line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=120.0,
                     help="reference arm: total seconds of oracle work over all steps")

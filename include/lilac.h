@@ -85,7 +85,9 @@ typedef enum {
                                  slab of x (up to 192 KB) in shared memory and runs the sliced
                                  ELL chunks of that slab's pieces of one group of rows (each
                                  row's piece summed by one lane); the last of a group's CTAs
-                                 adds the pieces in slab order and runs the epilogue.
+                                 adds the pieces in slab order and runs the epilogue.  Inside
+                                 FP64 CG the CTAs take equal runs of their slab's pieces and
+                                 leave q as the slab partials, which the CG update adds.
                                  Matrices with more than 64 slabs, or whose pieces pad by more
                                  than a quarter, run STAGED */
     LILAC_VARIANT_JDS = 6,    /* jagged diagonal storage (Section 3.2), built once per matrix:
@@ -106,6 +108,13 @@ typedef enum {
  * phase of an autotuning sparse library, paid at create like the paper's
  * cached invariants). */
 #define LILAC_CREATE_NO_TUNE 0x1u /* skip the timing; keep the choice made from row statistics */
+/* The choice from row statistics (mean row length m, coefficient of variation
+ * cv, longest row): short regular rows (m <= 12, cv <= 1): STAGED with one
+ * lane per row; irregular rows (cv > 1, or a row longer than a 2048-nonzero
+ * tile) and other short rows: STAGED with min(w, 8) lanes per row, w the
+ * smallest power of two >= m / 2; long regular rows: VECTOR with the smallest
+ * power of two >= m / 16 lanes per row (2 .. 32).  The timed trial starts
+ * from this choice and keeps it unless another candidate is faster. */
 
 /*
  * Upload a CSR matrix once and return a handle (construct + update of the
@@ -177,6 +186,19 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info);
  * (synchronous; errors OOM, CUDA); a matrix the copy does not suit runs
  * STAGED. */
 lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_width);
+
+/* The autotuner's trial on this handle (the tuning phase that an autotuning
+ * library runs once per matrix, Section 5 (SparseX); the paper's finding that
+ * no single implementation wins, Section 6.2): candidate i ran variant
+ * `variants[i]` at `widths[i]` lanes per row in `ms[i]` milliseconds per call
+ * (y = A x, the fastest of two rounds of three calls, after two warm-up
+ * calls), in the order tried.  Up to `max` entries are written to the
+ * caller's host arrays (NULL skips an array); *n receives the number of
+ * candidates, 0 when the handle was created with LILAC_CREATE_NO_TUNE or is
+ * empty.  Host state only: no synchronisation.  Errors: INVALID_ARG (NULL
+ * handle or n, max < 0). */
+lilac_status lilac_csr_tune_table(lilac_csr A, int32_t max, int32_t* variants, int32_t* widths,
+                                  float* ms, int32_t* n);
 
 /*
  * The handle's jagged diagonal storage (the JDS format of Section 3.2), built
@@ -371,13 +393,19 @@ lilac_status lilac_bfs(lilac_csr AT, int32_t source, int32_t* level, lilac_mem w
  *   dtype              type of vals, x and y (FP64 accumulates in FP64, FP32 in FP32)
  *   stream             cudaStream_t; the call is asynchronous
  * Runs the MERGE kernel with its scratch (carry records, per-CTA partial sums,
- * arrival counter; 82,176 bytes, at most 2048 CTA ranges) in one fixed array
- * in device memory that every GPU loading this library holds until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress) with the device current; make that first
- * call before any stream capture.  Every call shares the array: calls whose
- * kernels overlap on the GPU (e.g. on two streams at once) race and give
- * wrong results.  Each call clears the counter that must start at zero.
+ * arrival counter; 82,176 bytes, room for the at most 2048 CTA ranges a call
+ * launches whatever the size) in one fixed array in device memory that every
+ * GPU loading this library holds until the process exits.  The only size
+ * refused is rows + nnz >= 2^31.  The first call on a device looks up that
+ * array's device address (cudaGetSymbolAddress) with the device current, and
+ * where modules load lazily it also loads the library's kernels and their
+ * array onto the device, which allocates and can synchronise: make that first
+ * call a warm-up outside the latency-critical loop and before any stream
+ * capture.  The address is kept for the life of the process, so resetting
+ * the device (cudaDeviceReset) after the first call is not supported.  Every
+ * call shares the array: calls whose kernels overlap on the GPU (e.g. on two
+ * streams at once) race and give wrong results.  Each call clears the counter
+ * that must start at zero.
  */
 lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz, const int32_t* row_ptr,
                                 const int32_t* col_ind, const void* vals, lilac_dtype dtype,
@@ -394,13 +422,20 @@ lilac_status lilac_spmv_noalloc(int32_t rows, int32_t ncols, int64_t nnz, const 
 lilac_status lilac_csr_profile(lilac_csr A, int32_t enable, double* spmv_ms, int64_t* spmv_launches);
 
 /*
- * Batched execution: many FP64 problems of uneven size in one persistent
- * launch per phase (north of the paper, which issues one library call per
- * detected loop; batching many small problems addresses the paper's finding
- * that small sizes are not profitable alone, Section 6.2).  The work list
- * holds (problem, tile) items built from each handle's tile schedule; every
- * reduction of a problem is kept per item and added in item order, so a
- * problem's result is bitwise the same alone and in any batch.
+ * Batched execution: many problems of uneven size (FP64 or FP32 handles) in
+ * one persistent launch per phase (beyond the paper, which issues one library
+ * call per detected loop; batching many small problems addresses the paper's
+ * finding that small sizes are not profitable alone, Section 6.2).  The work
+ * list holds one kind of item per problem, following the kernel the handle's
+ * autotuner chose (the paper's finding that no single implementation wins,
+ * Section 6.2): groups of eight chunks of the sliced ELL copy for handles
+ * tuned to SELL or SLAB (the copy is built on first batched use; SLAB's
+ * column slabs need a whole SM each, so its problems run the sliced ELL form
+ * of the same layout), the STAGED tiles for the others and where the copy
+ * does not hold the values multiplied (an FP64 handle's FP32 values).
+ * Every reduction of a problem is kept per item and added in
+ * item order, so a problem's result is bitwise the same alone and in any
+ * batch.
  */
 typedef struct lilac_batch_s* lilac_batch;
 
@@ -409,11 +444,13 @@ typedef struct lilac_batch_s* lilac_batch;
 lilac_status lilac_batch_create(lilac_batch* out);
 lilac_status lilac_batch_destroy(lilac_batch B); /* NULL is a no-op */
 
-/* y[i] = A[i] x[i] for i < count: FP64 handles, device vectors (y[i] of
- * A[i]'s rows, x[i] of its columns); A[i] may repeat.  Asynchronous on
- * `stream` after a short synchronous set-up of the work lists. */
+/* y[i] = A[i] x[i] for i < count: device vectors of A[i]'s value type
+ * (double for FP64 handles, float for FP32 ones; y[i] of A[i]'s rows, x[i]
+ * of its columns); A[i] may repeat.  Asynchronous on `stream` after a short
+ * synchronous set-up of the work lists (and, on first use of a handle, of
+ * its sliced ELL copy). */
 lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
-                              const double* const* x, double* const* y, void* stream);
+                              const void* const* x, void* const* y, void* stream);
 
 /* CG on count systems A[i] x[i] = b[i] at once (x0 = 0), each stopping at
  * ||r|| <= rtol ||b|| (rtol <= 0: exactly max_iter iterations); iterations
@@ -422,8 +459,10 @@ lilac_status lilac_batch_spmv(lilac_batch B, int32_t count, const lilac_csr* A,
  * reliable updates (as lilac_cg precision 2, residual replaced when it fell
  * by 0.1; FP32 values derived once per handle).  infos (nullable) receives
  * per-system iterations, status, residual replacements and relative residual
- * (recursive for FP64, the last FP64 b - A x for precision 2).  Returns OK or
- * the first non-OK status. */
+ * (recursive for FP64, the last FP64 b - A x for precision 2).  FP32 handles
+ * take precision 2 only (their own values are the FP32 values; the FP64
+ * residual promotes them), else LILAC_ERR_DTYPE.  b and x are FP64 device
+ * vectors for every handle.  Returns OK or the first non-OK status. */
 lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
                             const double* const* b, double* const* x, int32_t max_iter,
                             double rtol, int32_t precision, lilac_cg_info* infos, void* stream);

@@ -177,8 +177,12 @@ lilac_status launch_staged_any(lilac_csr_s* A, const typename Op::ValT* val,
     }
 }
 
-// Elements in flight per lane in the sliced ELL kernels.
+// Elements in flight per lane in the sliced ELL kernels (SELL, SLAB).
 constexpr int kSellUnroll = 8;
+#ifndef LILAC_SLAB_UNROLL
+#define LILAC_SLAB_UNROLL 4
+#endif
+constexpr int kSlabUnroll = LILAC_SLAB_UNROLL;
 
 // SLAB: one CTA per SM holding a slab of x in shared memory (lilac_sell.cu
 // builds the sliced ELL copy of every slab and row group).  The copy holds the
@@ -188,7 +192,7 @@ template <int V, class Op>
 lilac_status prepare_slab(lilac_csr_s* A) {
     int& bps = bps_slot<V + 64, Op, true>(A->device);
     if (bps == 0) {
-        auto kern = spmv_slab_kernel<kSlabThreads, kSellUnroll, Op>;
+        auto kern = spmv_slab_kernel<kSlabThreads, kSlabUnroll, Op>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSlabMaxBytes + 64));
         bps = 1;
@@ -206,9 +210,44 @@ lilac_status launch_slab(lilac_csr_s* A, const typename Op::ValT* val, const typ
     SlabView view{A->slab_cptr.as<int>(), A->slab_crow.as<int>(), A->slab_col.as<uint16_t>(),
                   A->slab_ctas.as<int4>(), A->slab_groups.as<int2>(), A->slab_gcnt.as<unsigned>(),
                   A->rows, A->ncols, A->slab_W, A->slab_S, A->slab_G};
-    spmv_slab_kernel<kSlabThreads, kSellUnroll, Op><<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
+    spmv_slab_kernel<kSlabThreads, kSlabUnroll, Op><<<(unsigned)A->slab_grid, kSlabThreads, smem, stream>>>(
         view, A->slab_val.as<typename Op::ValT>(), x, A->slab_P.as<typename Op::AccT>(), op,
         A->scratch());
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+// SLAB, CG form (FP64 q = A p with p.q; spmv_slab_cg_kernel): runs when the
+// handle's SLAB copy holds the values being multiplied.
+inline bool slab_cg_active(const lilac_csr_s* A, const void* val) {
+    return A->variant == LILAC_VARIANT_SLAB && A->slab_built && val == A->val.p &&
+           A->dtype == LILAC_F64 && A->slab_pq.p != nullptr && A->rows == A->ncols;
+}
+
+inline lilac_status prepare_slab_cg(lilac_csr_s* A) {
+    static int done[64] = {};
+    if (!done[A->device & 63]) {
+        auto kern = spmv_slab_cg_kernel<kSlabThreads, kSlabUnroll>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)kSlabCgSmemBytes + 64));
+        done[A->device & 63] = 1;
+    }
+    return LILAC_OK;
+}
+
+// q = A p as slab partials (slab_P) and p.q as per-CTA sums (slab_pq).
+inline lilac_status launch_slab_cg(lilac_csr_s* A, const double* p, const CgState* st,
+                                   cudaStream_t stream) {
+    LILAC_TRY(prepare_slab_cg(A));
+    SlabView view{A->slab_cptr.as<int>(), A->slab_crow.as<int>(), A->slab_col.as<uint16_t>(),
+                  A->slab_ctas.as<int4>(), A->slab_groups.as<int2>(), A->slab_gcnt.as<unsigned>(),
+                  A->rows, A->ncols, A->slab_W, A->slab_S, A->slab_G};
+    Scratch sc = A->scratch();
+    sc.partials = A->slab_pq.as<double>();
+    spmv_slab_cg_kernel<kSlabThreads, kSlabUnroll>
+        <<<(unsigned)A->slab_grid, kSlabThreads, A->slab_cg_smem, stream>>>(
+            view, A->slab_ranges.as<int4>(), A->slab_tsm, A->slab_val.as<double>(), p,
+            A->slab_P.as<double>(), A->slab_T.as<double>(), st, sc);
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
 }

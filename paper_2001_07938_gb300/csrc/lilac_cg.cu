@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 
 #include "launch.cuh"
 
@@ -69,10 +70,29 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
     const int n = A->rows;
     const int vg = vec_grid(A, n);
     CgState* st = W.state.as<CgState>();
+    bool slab_cg = false;
+    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
+        slab_cg = slab_cg_active(A, val);
     for (int it = 0; it < nit; ++it) {
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it], s, cudaEventRecordExternal));
-        LILAC_TRY(launch_spmv(A, val, W.p.as<T>(), OpCgPq<V, T>{W.q.as<T>(), W.p.as<T>(), st}, s));
+        if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value) {
+            if (slab_cg) {
+                // SLAB CG form: q stays as the slab partials and p.q as per-CTA
+                // sums; the update adds them and takes alpha itself
+                LILAC_TRY(launch_slab_cg(A, W.p.as<double>(), st, s));
+                if (profile)
+                    LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s,
+                                                            cudaEventRecordExternal));
+                cg_update_slabs_kernel<<<vg, kVecThreads, 0, s>>>(
+                    n, x, W.r.as<double>(), W.p.as<double>(), A->slab_P.as<double>(), A->slab_S,
+                    A->slab_pq.as<double>(), A->slab_grid, st, A->scratch());
+                cg_direction_kernel<T><<<vg, kVecThreads, 0, s>>>(n, W.r.as<T>(), W.p.as<T>(), st);
+                continue;
+            }
+        }
+        const OpCgPq<V, T> op{W.q.as<T>(), W.p.as<T>(), st};
+        LILAC_TRY(launch_spmv(A, val, W.p.as<T>(), op, s));
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
         cg_update_kernel<T><<<vg, kVecThreads, 0, s>>>(n, x, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(),
@@ -81,6 +101,14 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
     }
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
+}
+
+// Kernels one CG iteration launches.
+template <class V, class T>
+static int iter_kernels(lilac_csr A, const V* val) {
+    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
+        if (slab_cg_active(A, val)) return 3;
+    return 2 + spmv_launch_count<OpCgPq<V, T>>(A, val);
 }
 
 // Run CG iterations until the device says done: either one graph of
@@ -92,6 +120,8 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
                                 int kind_chunk, const void* key_b, Start&& start, cudaStream_t s,
                                 CgState* host_state, Prof& prof) {
     LILAC_TRY(prepare_spmv<OpCgPq<V, T>>(A));
+    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
+        if (slab_cg_active(A, val)) LILAC_TRY(prepare_slab_cg(A));
     const uint64_t pflag = prof.on ? 1 : 0;
     if (!has_tol) {
         if (prof.on) LILAC_TRY(ensure_prof_events(A, max_iter));
@@ -100,7 +130,7 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
             LILAC_TRY(start(cs));
             return enqueue_iters<V, T>(A, val, x, W, max_iter, cs, prof.on);
         }));
-        prof.kernels += 2 + (2 + spmv_launch_count<OpCgPq<V, T>>(A, val)) * max_iter;
+        prof.kernels += 2 + iter_kernels<V, T>(A, val) * max_iter;
         if (prof.on) {
             LILAC_CUDA_TRY(cudaStreamSynchronize(s));
             LILAC_TRY(collect_prof(A, max_iter, prof));
@@ -118,7 +148,7 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
             return enqueue_iters<V, T>(A, val, x, W, nit, cs, prof.on);
         }));
         done_iters += nit;
-        prof.kernels += (2 + spmv_launch_count<OpCgPq<V, T>>(A, val)) * nit;
+        prof.kernels += iter_kernels<V, T>(A, val) * nit;
         LILAC_CUDA_TRY(cudaMemcpyAsync(host_state, W.state.p, sizeof(CgState),
                                        cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));

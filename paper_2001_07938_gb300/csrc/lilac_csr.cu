@@ -264,7 +264,8 @@ lilac::Scratch lilac_csr_s::scratch() const {
 int64_t lilac_csr_s::device_bytes() const {
     const lilac::DevBuf* all[] = {&row_ptr, &col_ind, &val, &val32, &tiles, &longs, &partials,
                                   &slab_cptr, &slab_crow, &slab_col, &slab_val, &slab_perm,
-                                  &slab_ctas, &slab_groups, &slab_gcnt, &slab_P, &sell_cptr, &sell_crow, &sell_col,
+                                  &slab_ctas, &slab_groups, &slab_gcnt, &slab_P, &slab_ranges, &slab_T, &slab_pq,
+                                  &sell_cptr, &sell_crow, &sell_col,
                                   &sell_val, &sell_splits, &sell_piece_split, &sell_part,
                                   &sell_red, &sell_cnt, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
@@ -496,6 +497,7 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
             ms = std::min(ms, t);
         }
         if (st != LILAC_OK) continue;
+        A->tune_table.emplace_back(c.variant, c.width, ms / 3.0f);
         if (ms < best) {
             best = ms;
             bestc = c;
@@ -645,6 +647,24 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) try {
     info->sell_split_rows = A->sell_built ? A->sell_nsplit : 0;
     info->sell_padded_nnz = A->sell_built ? A->sell_elems : 0;
     info->spmv_kernels = active == LILAC_VARIANT_SELL && A->sell_two_pass ? 2 : 1;
+    return LILAC_OK;
+} catch (...) {
+    return lilac::api_failure();
+}
+
+lilac_status lilac_csr_tune_table(lilac_csr A, int32_t max, int32_t* variants, int32_t* widths,
+                                  float* ms, int32_t* n) try {
+    if (!A || !n || max < 0) {
+        set_last_error("invalid argument to lilac_csr_tune_table");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    const int32_t cnt = (int32_t)A->tune_table.size();
+    for (int32_t i = 0; i < cnt && i < max; ++i) {
+        if (variants) variants[i] = std::get<0>(A->tune_table[(size_t)i]);
+        if (widths) widths[i] = std::get<1>(A->tune_table[(size_t)i]);
+        if (ms) ms[i] = std::get<2>(A->tune_table[(size_t)i]);
+    }
+    *n = cnt;
     return LILAC_OK;
 } catch (...) {
     return lilac::api_failure();

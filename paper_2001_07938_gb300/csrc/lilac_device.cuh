@@ -152,9 +152,11 @@ __device__ __forceinline__ void block_sum(const double (&v)[NR], double (&out)[N
     __syncthreads();
 }
 
-// Sum one value of type T over the block; result valid in every thread.
+// Sum one value of type T over the block; the result is valid in thread 0
+// only, which adds the warps' sums in warp order (the other threads do no
+// second-level adds: FP64 adds take the narrow FP64 pipe on GB300).
 template <int THREADS, class T>
-__device__ __forceinline__ T block_sum_all(T v, T* sh) {
+__device__ __forceinline__ T block_sum_lead(T v, T* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = THREADS / 32;
 #pragma unroll
@@ -162,8 +164,10 @@ __device__ __forceinline__ T block_sum_all(T v, T* sh) {
     if (lane == 0) sh[warp] = v;
     __syncthreads();
     T s = T(0);
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int w = 0; w < NW; ++w) s += sh[w];
+        for (int w = 0; w < NW; ++w) s += sh[w];
+    }
     __syncthreads();
     return s;
 }

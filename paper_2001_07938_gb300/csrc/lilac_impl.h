@@ -35,6 +35,9 @@ constexpr int kRowsThreads = 256;
 // most kSlabMaxBytes (x elements counted as 8 bytes) in shared memory.
 constexpr int kSlabThreads = 1024;
 constexpr int kSlabMaxBytes = 192 * 1024;
+// Shared memory of the CG form of SLAB at most: the slab plus its chunks'
+// p.q terms when they fit.
+constexpr size_t kSlabCgSmemBytes = 224 * 1024;
 // MERGE kernel shape: 256 threads, sub-tiles of 2048 path items (8 per
 // thread); overridable at build time.
 #ifndef LILAC_MERGE_THREADS
@@ -111,9 +114,10 @@ struct lilac_csr_s {
     // row statistics (the invariants cached at create)
     int32_t max_row_len = 0, empty_rows = 0;
     double mean_row_len = 0.0, std_row_len = 0.0;
-    // kernel choice
+    // kernel choice, and the timed tuner's trial {variant, width, ms per call}
     int variant = LILAC_VARIANT_STAGED;
     int vwidth = 32;
+    std::vector<std::tuple<int, int, float>> tune_table;
     // STAGED schedule
     lilac::DevBuf tiles, longs;
     int ntiles = 0, nlong = 0, nlong_chunks = 0;
@@ -124,6 +128,12 @@ struct lilac_csr_s {
     // rows, their arrival counters, and the partial sums P (S x rows)
     lilac::DevBuf slab_cptr, slab_crow, slab_col, slab_val, slab_perm, slab_ctas, slab_groups,
         slab_gcnt, slab_P;
+    // CG form of SLAB: per-CTA runs of a slab's chunks with equal element
+    // counts, one p[row] * piece per chunk lane (used when they do not fit in
+    // shared memory: slab_tsm == 0), and the per-CTA p.q sums
+    lilac::DevBuf slab_ranges, slab_T, slab_pq;
+    int slab_tsm = 0;
+    size_t slab_cg_smem = 0;
     int slab_S = 0, slab_W = 0, slab_grid = 0, slab_G = 0;
     int64_t slab_elems = 0;
     bool slab_built = false;

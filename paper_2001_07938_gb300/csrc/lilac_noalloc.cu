@@ -64,11 +64,9 @@ lilac_status noalloc_launch(int32_t rows, int64_t nnz, const int32_t* row_ptr, c
     const int64_t total = (int64_t)rows + nnz;
     const int64_t target = std::min<int64_t>((int64_t)sms * 4, kNoAllocMaxCtas);
     const int64_t per_cta = std::max<int64_t>(kMergeItems, (total + target - 1) / target);
+    // per_cta >= ceil(total / target), so G <= target <= kNoAllocMaxCtas: the
+    // scratch always has room, whatever the matrix size
     const int64_t G = (total + per_cta - 1) / per_cta;
-    if (G > kNoAllocMaxCtas) {
-        set_last_error("lilac_spmv_noalloc: matrix needs more CTA ranges than the scratch holds");
-        return LILAC_ERR_INVALID_ARG;
-    }
     unsigned* ticket = reinterpret_cast<unsigned*>(scratch + kNoAllocTicketOff);
     // the arrival counter must start at zero
     LILAC_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));

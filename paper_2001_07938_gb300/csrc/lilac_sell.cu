@@ -354,6 +354,24 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     }
     // padding of more than a quarter: not worth the copy (STAGED runs)
     if ((double)elems > 1.25 * (double)nnz + 32.0 * (double)crow.size()) return LILAC_OK;
+    // CG form: the chunks of slab s (all its groups, contiguous) cut into G
+    // runs of about equal padded element counts, one CTA each
+    std::vector<int4> ranges;
+    for (int sl = 0; sl < S; ++sl) {
+        const int cb = ctas[(size_t)sl * G].y, ce = ctas[(size_t)sl * G + G - 1].z;
+        const int64_t eb = cptr[(size_t)cb], ee = cptr[(size_t)ce];
+        int cur = cb;
+        for (int j = 0; j < G; ++j) {
+            int nxt = ce;
+            if (j < G - 1) {
+                const int64_t target = eb + (ee - eb) * (j + 1) / G;
+                nxt = cur;
+                while (nxt < ce && cptr[(size_t)nxt + 1] <= target) ++nxt;
+            }
+            ranges.push_back(make_int4(sl, cur, nxt, 0));
+            cur = nxt;
+        }
+    }
     std::vector<int32_t> perm((size_t)elems, -1);
     std::vector<uint16_t> c16((size_t)elems, (uint16_t)W);
     {
@@ -380,6 +398,17 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     LILAC_TRY(A->ws_alloc(A->slab_groups, sizeof(int2) * groups.size()));
     LILAC_TRY(A->ws_alloc(A->slab_gcnt, sizeof(unsigned) * groups.size()));
     LILAC_TRY(A->ws_alloc(A->slab_P, sizeof(double) * (size_t)S * (size_t)std::max(1, n)));
+    LILAC_TRY(A->ws_alloc(A->slab_ranges, sizeof(int4) * ranges.size()));
+    LILAC_TRY(A->ws_alloc(A->slab_pq, sizeof(double) * ranges.size()));
+    // the CG form keeps its chunks' p[row] * piece in shared memory after the
+    // slab when the longest run fits (kSlabCgSmemBytes in all), else in T
+    int maxch = 0;
+    for (const int4& rg : ranges) maxch = std::max(maxch, rg.z - rg.y);
+    const size_t slab_bytes = sizeof(double) * (((size_t)W + 2) & ~size_t(1));
+    const size_t t_bytes = sizeof(double) * 32 * (size_t)maxch;
+    A->slab_tsm = slab_bytes + t_bytes <= kSlabCgSmemBytes ? 1 : 0;
+    A->slab_cg_smem = A->slab_tsm ? slab_bytes + t_bytes : slab_bytes;
+    if (!A->slab_tsm) LILAC_TRY(A->ws_alloc(A->slab_T, sizeof(double) * crow.size()));
     LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_val.p, 0, A->slab_val.bytes, s));
     LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_gcnt.p, 0, A->slab_gcnt.bytes, s));
     LILAC_CUDA_TRY(cudaMemsetAsync(A->slab_P.p, 0, A->slab_P.bytes, s));
@@ -393,6 +422,7 @@ static lilac_status build_slab(lilac_csr A, cudaStream_t s) {
     LILAC_TRY(up(A->slab_perm, perm.data(), sizeof(int32_t) * perm.size()));
     LILAC_TRY(up(A->slab_ctas, ctas.data(), sizeof(int4) * ctas.size()));
     LILAC_TRY(up(A->slab_groups, groups.data(), sizeof(int2) * groups.size()));
+    LILAC_TRY(up(A->slab_ranges, ranges.data(), sizeof(int4) * ranges.size()));
     LILAC_TRY(A->dtype == LILAC_F64 ? regather<double>(A, elems, s) : regather<float>(A, elems, s));
     LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     A->slab_S = S;
@@ -412,10 +442,13 @@ lilac_status slab_refresh_values(lilac_csr A, cudaStream_t s) {
 }
 
 void slab_release(lilac_csr A) {
-    lilac::DevBuf* b[] = {&A->slab_cptr, &A->slab_crow,   &A->slab_col,  &A->slab_val, &A->slab_perm,
-                          &A->slab_ctas, &A->slab_groups, &A->slab_gcnt, &A->slab_P};
+    lilac::DevBuf* b[] = {&A->slab_cptr,  &A->slab_crow,   &A->slab_col,  &A->slab_val,
+                          &A->slab_perm,  &A->slab_ctas,   &A->slab_groups, &A->slab_gcnt,
+                          &A->slab_P,     &A->slab_ranges, &A->slab_T, &A->slab_pq};
     for (auto* d : b) d->release();
     A->slab_S = A->slab_W = A->slab_grid = A->slab_G = 0;
+    A->slab_tsm = 0;
+    A->slab_cg_smem = 0;
     A->slab_elems = 0;
     A->slab_built = false;
 }

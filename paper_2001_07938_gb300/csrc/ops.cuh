@@ -265,6 +265,138 @@ static __global__ void __launch_bounds__(kVecThreads)
     grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
 }
 
+// SLAB, CG form: one FP64 CG step q = A p with p.q, leaving the ends of the
+// step to the update kernel that follows.  q is left as the S slab partials
+// P[s][row]: the update adds them in slab order where it reads q (the same
+// sums as the row-group combine of spmv_slab_kernel).  p.q is taken from the
+// pieces instead of the rows: lane l of chunk c keeps t = p[row] * piece (0
+// on padding lanes), and each CTA adds the t of its own chunks in chunk
+// order, so no CTA waits for the other slabs of its rows.  That frees the
+// CTAs from row groups: `ranges` gives each CTA a run of its slab's chunks
+// with about equal padded element counts, and warps take the run's chunks
+// from a shared counter.  The t live in shared memory after the slab when
+// they fit (tsm), else in T.  The CTA's sum goes to slot blockIdx.x of
+// s.partials and the kernel ends there, with no grid ticket:
+// cg_update_slabs_kernel adds the slots (fixed order) and takes alpha.
+template <int THREADS, int UNR>
+__global__ void __launch_bounds__(THREADS, 1)
+    spmv_slab_cg_kernel(SlabView V, const int4* __restrict__ ranges, int tsm,
+                        const double* __restrict__ sval, const double* __restrict__ p,
+                        double* __restrict__ P, double* __restrict__ T, const CgState* st,
+                        Scratch s) {
+    if (cg_done(st)) return;
+    extern __shared__ __align__(16) unsigned char slab_smem[];
+    __shared__ int next_chunk;
+    double* xs = reinterpret_cast<double*>(slab_smem);
+    const int4 c = ranges[blockIdx.x];  // {slab, first chunk, end chunk, -}
+    const int sl = c.x;
+    const int c0 = sl * V.W;
+    slab_load_x<THREADS>(xs, p, c0, min(V.W, V.ncols - c0), V.W);
+    // the chunk lanes' p[row] * piece: after the slab (and its zero) in
+    // shared memory, 16-byte aligned, or in T
+    double* ts = tsm ? xs + ((V.W + 2) & ~1) : T + (size_t)c.y * 32;
+    if (threadIdx.x == 0) next_chunk = c.y + THREADS / 32;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    double* __restrict__ Ps = P + (size_t)sl * V.rows;
+    int ch = c.y + (int)(threadIdx.x >> 5);
+    while (ch < c.z) {
+        const int row = __ldg(V.crow + (size_t)ch * 32 + lane);
+        const double acc = slab_chunk_sum<UNR, kSlabPipe, double>(V, sval, xs, ch, lane);
+        double t = 0.0;
+        if (row >= 0) {
+            Ps[row] = acc;
+            t = __ldg(p + row) * acc;
+        }
+        ts[(ch - c.y) * 32 + lane] = t;
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&next_chunk, 1);
+        ch = __shfl_sync(0xffffffffu, nx, 0);
+    }
+    __syncthreads();  // this CTA's t are written and visible to the block
+    double red[1] = {0.0};
+    const int nt = (c.z - c.y) * 32;
+    for (int i = (int)threadIdx.x; i < nt; i += THREADS) red[0] += tsm ? ts[i] : __ldcg(ts + i);
+    // block sum with the second level in warp 0 only: FP64 adds take the
+    // narrow FP64 pipe, so no thread repeats the warps' sum
+    __shared__ double sh[32];
+    double tot[1];
+    block_sum<1, THREADS>(red, tot, sh);
+    if (threadIdx.x == 0) s.partials[blockIdx.x] = tot[0];
+}
+
+// The update after the CG form of the SLAB SpMV (spmv_slab_cg_kernel):
+// p.q arrives as that kernel's per-CTA sums, which every CTA here adds in
+// slot order (so all take the same alpha = r.r / p.q; breakdown when
+// p.q <= 0 or not finite), and q as the S slab partials P[s][i], added in
+// slab order.  Then x += alpha p, r -= alpha q and r.r as cg_update_kernel.
+struct FinCgUpdateSlabs {
+    CgState* st;
+    double pq, alpha;
+    __device__ void finish(const double* tot) const {
+        st->pq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+            st->status = LILAC_ERR_BREAKDOWN;
+            st->done = 1;
+            return;
+        }
+        st->alpha = alpha;
+        FinCgUpdate<double>{st, nullptr}.finish(tot);
+    }
+};
+
+static __global__ void __launch_bounds__(kVecThreads)
+    cg_update_slabs_kernel(int n, double* __restrict__ x, double* __restrict__ r,
+                           const double* __restrict__ p, const double* __restrict__ P, int S,
+                           const double* __restrict__ pq_parts, int nparts, CgState* st,
+                           Scratch s) {
+    if (cg_done(st)) return;
+    const double rr = st->rr;  // in flight while warp 0 adds the SpMV's sums
+    __shared__ double sh_pq;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = (int)threadIdx.x; i < nparts; i += 32) v += __ldcg(pq_parts + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sh_pq = v;
+    }
+    __syncthreads();
+    const double pq = sh_pq;
+    const bool ok = pq > 0.0 && isfinite(pq);
+    const double alpha = ok ? rr / pq : 0.0;
+    double rr_new = 0.0;
+    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
+    const int nv = (ok && aligned16(x, r, p, P) && (n & 1) == 0) ? n / 2 : 0;
+    for (int i = g0; i < nv; i += gs) {
+        double2 xv = reinterpret_cast<const double2*>(x)[i], rv = reinterpret_cast<const double2*>(r)[i];
+        const double2 pv = reinterpret_cast<const double2*>(p)[i];
+        double2 qv = reinterpret_cast<const double2*>(P)[i];
+        for (int q = 1; q < S; ++q) {
+            const double2 t = reinterpret_cast<const double2*>(P + (size_t)q * n)[i];
+            qv.x += t.x;
+            qv.y += t.y;
+        }
+        xv.x += alpha * pv.x;
+        xv.y += alpha * pv.y;
+        rv.x -= alpha * qv.x;
+        rv.y -= alpha * qv.y;
+        rr_new += rv.x * rv.x;
+        rr_new += rv.y * rv.y;
+        reinterpret_cast<double2*>(x)[i] = xv;
+        reinterpret_cast<double2*>(r)[i] = rv;
+    }
+    for (int i = nv * 2 + g0; ok && i < n; i += gs) {
+        double qi = P[i];
+        for (int q = 1; q < S; ++q) qi += P[(size_t)q * n + i];
+        x[i] += alpha * p[i];
+        const double ri = r[i] - alpha * qi;
+        r[i] = ri;
+        rr_new += ri * ri;
+    }
+    double red[1] = {rr_new};
+    grid_reduce_finish<1, kVecThreads>(FinCgUpdateSlabs{st, pq, alpha}, red, s, 0);
+}
+
 // p = r + beta p.
 template <class T>
 static __global__ void __launch_bounds__(kVecThreads)

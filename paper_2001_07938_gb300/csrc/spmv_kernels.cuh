@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(THREADS)
                 const int k = kb0 + j * THREADS + tid;
                 if (k < ke0) sum += AccT(vs[k]) * AccT(xj[j]);
             }
-            sum = block_sum_all<THREADS, AccT>(sum, sh_sum);
+            sum = block_sum_lead<THREADS, AccT>(sum, sh_sum);
             if (tid == 0) {
                 const int lid = t.r0;
                 const int slot = -t.r1 - 1;
@@ -355,6 +355,30 @@ __global__ void __launch_bounds__(THREADS)
 }  // namespace lilac
 
 namespace lilac {
+
+// Slab s of x, x[c0 .. c0 + w), into shared memory xs[0 .. w), with zeros in
+// xs[w .. W] (padding points at W): 16-byte loads when x + c0 is aligned (c0
+// is a multiple of 8), eight in flight per thread.
+template <int THREADS, class VecT>
+__device__ __forceinline__ void slab_load_x(VecT* xs, const VecT* __restrict__ x, int c0, int w,
+                                            int W) {
+    constexpr int E = 16 / sizeof(VecT);
+    const bool al = (reinterpret_cast<uintptr_t>(x + c0) & 15u) == 0;
+    const int nv = al ? w / E : 0;
+    const uint4* __restrict__ xv = reinterpret_cast<const uint4*>(x + c0);
+    uint4* xsv = reinterpret_cast<uint4*>(xs);
+    int i = threadIdx.x;
+    for (; i + 7 * THREADS < nv; i += 8 * THREADS) {
+        uint4 t[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) t[u] = __ldg(xv + i + u * THREADS);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) xsv[i + u * THREADS] = t[u];
+    }
+    for (; i < nv; i += THREADS) xsv[i] = __ldg(xv + i);
+    for (int j = nv * E + threadIdx.x; j < w; j += THREADS) xs[j] = __ldg(x + c0 + j);
+    for (int j = w + threadIdx.x; j <= W; j += THREADS) xs[j] = VecT(0);
+}
 
 // ---------------------------------------------------------------------------
 // SELL kernels: a sliced ELLPACK copy of the matrix (SELL-C-sigma with C = 32,
@@ -513,6 +537,11 @@ __global__ void __launch_bounds__(THREADS) rows_reduce_kernel(int rows, Op op, S
 // P[s][row].  The last of the group's S CTAs to finish (arrival counter) adds
 // P over the slabs in slab order for every row of the group and runs the
 // epilogue; its reductions go to partial slot g, summed in slot order.
+#ifndef LILAC_SLAB_PIPE
+#define LILAC_SLAB_PIPE 0
+#endif
+constexpr bool kSlabPipe = LILAC_SLAB_PIPE != 0;
+
 struct SlabView {
     const int* __restrict__ cptr;    // [S * chunks + 1]
     const int* __restrict__ crow;    // [chunks * 32]: row, or -1 (padding lane)
@@ -523,6 +552,84 @@ struct SlabView {
     int rows, ncols, W, S, G;
 };
 
+// The piece sum of one lane of chunk `ch`: one FMA per element in element
+// order, UNR elements (value, 16-bit column, x from shared memory) in flight.
+// PIPE: the loads of the next UNR elements are issued before the FMAs of the
+// current ones, so a warp keeps loads in flight while it waits for the FP64
+// pipe.
+template <int UNR, bool PIPE, class AccT, class ValT, class VecT>
+__device__ __forceinline__ AccT slab_chunk_sum(const SlabView& V, const ValT* __restrict__ sval,
+                                               const VecT* xs, int ch, int lane) {
+    const int base = __ldg(V.cptr + ch);
+    const int width = (__ldg(V.cptr + ch + 1) - base) >> 5;
+    const ValT* __restrict__ vp = sval + base + lane;
+    const uint16_t* __restrict__ cp = V.col + base + lane;
+    AccT acc = AccT(0);
+    if constexpr (PIPE) {
+        ValT va[UNR];
+        int ca[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const bool q = u < width;
+            va[u] = q ? ld_stream(vp + 32 * u) : ValT(0);
+            ca[u] = q ? (int)ld_stream(cp + 32 * u) : V.W;
+        }
+        for (int k = 0; k < width; k += UNR) {
+            ValT vb[UNR];
+            int cb[UNR];
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                const bool q = k + UNR + u < width;
+                vb[u] = q ? ld_stream(vp + 32 * (k + UNR + u)) : ValT(0);
+                cb[u] = q ? (int)ld_stream(cp + 32 * (k + UNR + u)) : V.W;
+            }
+            if (k + UNR <= width) {
+#pragma unroll
+                for (int u = 0; u < UNR; ++u) acc += AccT(va[u]) * AccT(xs[ca[u]]);
+            } else {
+                // the bound is the same for the whole warp: skipped FMAs cost nothing
+#pragma unroll
+                for (int u = 0; u < UNR; ++u)
+                    if (k + u < width) acc += AccT(va[u]) * AccT(xs[ca[u]]);
+            }
+#pragma unroll
+            for (int u = 0; u < UNR; ++u) {
+                va[u] = vb[u];
+                ca[u] = cb[u];
+            }
+        }
+        return acc;
+    }
+    int k = 0;
+    for (; k + UNR <= width; k += UNR) {
+        ValT vv[UNR];
+        int cc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            vv[u] = ld_stream(vp + 32 * (k + u));
+            cc[u] = ld_stream(cp + 32 * (k + u));
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
+    }
+    if (k < width) {
+        // the last (fewer than UNR) elements, loads issued together; the
+        // bound is the same for the whole warp, so skipped FMAs cost nothing
+        ValT vv[UNR];
+        int cc[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const bool q = k + u < width;
+            vv[u] = q ? ld_stream(vp + 32 * (k + u)) : ValT(0);
+            cc[u] = q ? (int)ld_stream(cp + 32 * (k + u)) : V.W;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (k + u < width) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
+    }
+    return acc;
+}
+
 template <int THREADS, int UNR, class Op>
 __global__ void __launch_bounds__(THREADS, 1)
     spmv_slab_kernel(SlabView V, const typename Op::ValT* __restrict__ sval,
@@ -530,7 +637,6 @@ __global__ void __launch_bounds__(THREADS, 1)
                      Op op, Scratch s) {
     if (op.skip()) return;
     op.begin();
-    using ValT = typename Op::ValT;
     using VecT = typename Op::VecT;
     using AccT = typename Op::AccT;
     constexpr int NR = Op::NR;
@@ -540,68 +646,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     VecT* xs = reinterpret_cast<VecT*>(slab_smem);
     const int4 c = V.ctas[blockIdx.x];  // {slab, first chunk, end chunk, group}
     const int sl = c.x;
-    const int W = V.W;
-    const int c0 = sl * W;
-    const int w = min(W, V.ncols - c0);
-    {
-        // the slab of x into shared memory: 16-byte loads when x is aligned
-        // (c0 is a multiple of 8), eight in flight per thread
-        constexpr int E = 16 / sizeof(VecT);
-        const bool al = (reinterpret_cast<uintptr_t>(x) & 15u) == 0;
-        const int nv = al ? w / E : 0;
-        const uint4* __restrict__ xv = reinterpret_cast<const uint4*>(x + c0);
-        uint4* xsv = reinterpret_cast<uint4*>(xs);
-        int i = threadIdx.x;
-        for (; i + 7 * THREADS < nv; i += 8 * THREADS) {
-            uint4 t[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) t[u] = __ldg(xv + i + u * THREADS);
-#pragma unroll
-            for (int u = 0; u < 8; ++u) xsv[i + u * THREADS] = t[u];
-        }
-        for (; i < nv; i += THREADS) xsv[i] = __ldg(xv + i);
-        for (int j = nv * E + threadIdx.x; j < w; j += THREADS) xs[j] = __ldg(x + c0 + j);
-        for (int j = w + threadIdx.x; j <= W; j += THREADS) xs[j] = VecT(0);
-    }
+    const int c0 = sl * V.W;
+    slab_load_x<THREADS>(xs, x, c0, min(V.W, V.ncols - c0), V.W);
     if (threadIdx.x == 0) next_chunk = c.y + THREADS / 32;
     __syncthreads();
     const int lane = threadIdx.x & 31;
     AccT* __restrict__ Ps = P + (size_t)sl * V.rows;
     int ch = c.y + (int)(threadIdx.x >> 5);
     while (ch < c.z) {
-        const int base = __ldg(V.cptr + ch);
-        const int width = (__ldg(V.cptr + ch + 1) - base) >> 5;
         const int row = __ldg(V.crow + (size_t)ch * 32 + lane);
-        const ValT* __restrict__ vp = sval + base + lane;
-        const uint16_t* __restrict__ cp = V.col + base + lane;
-        AccT acc = AccT(0);
-        int k = 0;
-        for (; k + UNR <= width; k += UNR) {
-            ValT vv[UNR];
-            int cc[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                vv[u] = ld_stream(vp + 32 * (k + u));
-                cc[u] = ld_stream(cp + 32 * (k + u));
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
-        }
-        if (k < width) {
-            // the last (fewer than UNR) elements, loads issued together; the
-            // bound is the same for the whole warp, so skipped FMAs cost nothing
-            ValT vv[UNR];
-            int cc[UNR];
-#pragma unroll
-            for (int u = 0; u < UNR; ++u) {
-                const bool q = k + u < width;
-                vv[u] = q ? ld_stream(vp + 32 * (k + u)) : ValT(0);
-                cc[u] = q ? (int)ld_stream(cp + 32 * (k + u)) : W;
-            }
-#pragma unroll
-            for (int u = 0; u < UNR; ++u)
-                if (k + u < width) acc += AccT(vv[u]) * AccT(xs[cc[u]]);
-        }
+        const AccT acc = slab_chunk_sum<UNR, kSlabPipe, AccT>(V, sval, xs, ch, lane);
         if (row >= 0) Ps[row] = acc;
         int nx = 0;
         if (lane == 0) nx = atomicAdd(&next_chunk, 1);

@@ -49,6 +49,7 @@ EXPORTS = (
     "lilac_server_submit", "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
     "lilac_server_now", "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host",
     "lilac_host_cache_stats", "lilac_host_cache_clear", "lilac_spmm", "lilac_debug_inject",
+    "lilac_csr_tune_table",
 )
 
 LILAC_INJECT_ALLOC_FAIL, LILAC_INJECT_SKIP_COPY = 1, 2
@@ -154,6 +155,7 @@ def _lib():
         lib.lilac_csr_destroy.argtypes = [vp]
         lib.lilac_csr_info.argtypes = [vp, c.POINTER(lilac_csr_info_t)]
         lib.lilac_csr_set_variant.argtypes = [vp, i32, i32]
+        lib.lilac_csr_tune_table.argtypes = [vp, i32, vp, vp, vp, c.POINTER(i32)]
         lib.lilac_csr_jds.argtypes = [vp, vp, vp, vp, vp, vp]
         lib.lilac_bfs.argtypes = [vp, i32, vp, c.c_int, c.POINTER(i32), vp]
         lib.lilac_spmv_host.argtypes = [i32, i32, i64, vp, vp, vp, c.c_int, vp, vp, c.c_uint64,
@@ -201,7 +203,8 @@ def _lib():
                      "lilac_server_destroy", "lilac_server_add_matrix", "lilac_server_submit",
                      "lilac_server_step", "lilac_server_poll", "lilac_server_stats",
                      "lilac_csr_jds", "lilac_bfs", "lilac_spmv_host", "lilac_host_cache_stats",
-                     "lilac_host_cache_clear", "lilac_spmm", "lilac_debug_inject"):
+                     "lilac_host_cache_clear", "lilac_spmm", "lilac_debug_inject",
+                     "lilac_csr_tune_table"):
             getattr(lib, name).restype = st
         _LIB = lib
     return _LIB
@@ -289,6 +292,19 @@ def lilac_csr_set_variant(A, variant, vector_width=0):
     _check(_lib().lilac_csr_set_variant(A, variant, vector_width), "lilac_csr_set_variant")
 
 
+def lilac_csr_tune_table(A):
+    """The autotuner's trial: a list of {variant, width, ms} per candidate."""
+    n = ctypes.c_int32(0)
+    _check(_lib().lilac_csr_tune_table(A, 0, None, None, None, ctypes.byref(n)),
+           "lilac_csr_tune_table")
+    m = n.value
+    v = (ctypes.c_int32 * max(1, m))()
+    w = (ctypes.c_int32 * max(1, m))()
+    t = (ctypes.c_float * max(1, m))()
+    _check(_lib().lilac_csr_tune_table(A, m, v, w, t, ctypes.byref(n)), "lilac_csr_tune_table")
+    return [{"variant": int(v[i]), "width": int(w[i]), "ms": float(t[i])} for i in range(m)]
+
+
 def lilac_csr_jds(A, perm, jd_ptr, col_ind, vals, nzcnt):
     """Copy the handle's JDS form into host numpy arrays (None entries skipped)."""
     p = [a.ctypes.data if a is not None else None for a in (perm, jd_ptr, col_ind, vals, nzcnt)]
@@ -366,7 +382,7 @@ def lilac_pagerank(A, x, init_uniform, iters, damping, l1_per_iter, where, strea
 
 
 class Batch:
-    """Owns a lilac_batch context (batched SpMV / CG over FP64 handles)."""
+    """Owns a lilac_batch context (batched SpMV / CG over FP64 or FP32 handles)."""
 
     def __init__(self):
         h = ctypes.c_void_p()
@@ -543,6 +559,9 @@ class CsrMatrix:
 
     def set_variant(self, variant: int, width: int = 0):
         lilac_csr_set_variant(self.handle, variant, width)
+
+    def tune_table(self) -> list:
+        return lilac_csr_tune_table(self.handle)
 
     def spmm(self, X, Y, k, layout=LILAC_LAYOUT_ROWS, stream=None):
         """Y = A X for k vectors (numpy host or torch arrays, flat or 2D)."""
