@@ -557,8 +557,16 @@ lilac_status lilac_csr_reset_error(lilac_csr A);
  *       timeout and returns, and A reports LILAC_ERR_TIMEOUT from its next
  *       synchronizing call until lilac_csr_reset_error.  Every wait in the
  *       kernels is bounded, so nothing hangs or faults.
+ *   LILAC_INJECT_SKIP_BARRIER (arg unused): in the next fused CG step of A
+ *       (FP64 CG on a SLAB handle), CTA 0 does not arrive at the step's grid
+ *       barrier; the other CTAs give up after about 2 s and record a device
+ *       timeout, reported as above.
  */
-typedef enum { LILAC_INJECT_ALLOC_FAIL = 1, LILAC_INJECT_SKIP_COPY = 2 } lilac_inject;
+typedef enum {
+    LILAC_INJECT_ALLOC_FAIL = 1,
+    LILAC_INJECT_SKIP_COPY = 2,
+    LILAC_INJECT_SKIP_BARRIER = 3
+} lilac_inject;
 lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg);
 
 /* Static text for a status code. */

@@ -62,6 +62,13 @@ static lilac_status collect_prof(lilac_csr A, int pairs, Prof& prof) {
     return collect_prof_events(A, pairs, &prof.ms, &prof.launches);
 }
 
+// Grid of the fused CG step: at most one CTA per SM (its grid barrier needs
+// every CTA resident), about two elements per thread.
+static int step_grid(lilac_csr A, int n) {
+    const int64_t need = ((int64_t)n + 2 * kVecThreads - 1) / (2 * kVecThreads);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
+}
+
 // Enqueue `nit` iterations of CG on the work set W (vectors of type T; the
 // matrix values `val` of type V).
 template <class V, class T>
@@ -84,10 +91,13 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
                 if (profile)
                     LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s,
                                                             cudaEventRecordExternal));
-                cg_update_slabs_kernel<<<vg, kVecThreads, 0, s>>>(
+                // the rest of the step (update, r.r, direction) in one launch
+                // whose CTAs are all resident: at most one per SM
+                unsigned* bar = A->cg_step.as<unsigned>();
+                double* rr_parts = reinterpret_cast<double*>(bar + 4);
+                cg_step_slabs_kernel<<<step_grid(A, n), kVecThreads, 0, s>>>(
                     n, x, W.r.as<double>(), W.p.as<double>(), A->slab_P.as<double>(), A->slab_S,
-                    A->slab_pq.as<double>(), A->slab_grid, st, A->scratch());
-                cg_direction_kernel<T><<<vg, kVecThreads, 0, s>>>(n, W.r.as<T>(), W.p.as<T>(), st);
+                    A->slab_pq.as<double>(), A->slab_grid, st, rr_parts, bar, A->status.as<int>());
                 continue;
             }
         }
@@ -107,7 +117,7 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
 template <class V, class T>
 static int iter_kernels(lilac_csr A, const V* val) {
     if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
-        if (slab_cg_active(A, val)) return 3;
+        if (slab_cg_active(A, val)) return 2;
     return 2 + spmv_launch_count<OpCgPq<V, T>>(A, val);
 }
 
@@ -120,8 +130,16 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
                                 int kind_chunk, const void* key_b, Start&& start, cudaStream_t s,
                                 CgState* host_state, Prof& prof) {
     LILAC_TRY(prepare_spmv<OpCgPq<V, T>>(A));
-    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
-        if (slab_cg_active(A, val)) LILAC_TRY(prepare_slab_cg(A));
+    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value) {
+        if (slab_cg_active(A, val)) {
+            LILAC_TRY(prepare_slab_cg(A));
+            const size_t need = 4 * sizeof(unsigned) + sizeof(double) * (size_t)A->sm_count;
+            if (!A->cg_step.p || A->cg_step.bytes < need) {
+                LILAC_TRY(A->ws_alloc(A->cg_step, need));
+                LILAC_CUDA_TRY(cudaMemsetAsync(A->cg_step.p, 0, A->cg_step.bytes, s));
+            }
+        }
+    }
     const uint64_t pflag = prof.on ? 1 : 0;
     if (!has_tol) {
         if (prof.on) LILAC_TRY(ensure_prof_events(A, max_iter));

@@ -269,7 +269,7 @@ int64_t lilac_csr_s::device_bytes() const {
                                   &sell_val, &sell_splits, &sell_piece_split, &sell_part,
                                   &sell_red, &sell_cnt, &merge_coords, &merge_carries,
                                   &long_part, &long_red, &long_cnt, &ticket, &status, &stage_x,
-                                  &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg32.r,
+                                  &stage_y, &cg64.r, &cg64.p, &cg64.q, &cg64.state, &cg_step, &cg32.r,
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
                                   &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out,
                                   &jds_slot_row, &jds_row_slot, &jds_len, &jds_ptr, &jds_col,
@@ -281,7 +281,7 @@ int64_t lilac_csr_s::device_bytes() const {
 
 static lilac_status zero_scratch(lilac_csr A, cudaStream_t stream) {
     lilac::DevBuf* bufs[] = {&A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
-                             &A->status, &A->slab_gcnt};
+                             &A->status, &A->slab_gcnt, &A->cg_step};
     for (auto* b : bufs)
         if (b->p) LILAC_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, stream));
     return sell_zero_counters(A, stream);
@@ -527,7 +527,7 @@ static void free_handle(lilac_csr A) {
                             &A->merge_coords, &A->merge_carries,
                             &A->partials, &A->long_part, &A->long_red, &A->long_cnt, &A->ticket,
                             &A->status, &A->stage_x, &A->stage_y, &A->cg64.r, &A->cg64.p,
-                            &A->cg64.q, &A->cg64.state, &A->cg32.r, &A->cg32.p, &A->cg32.q,
+                            &A->cg64.q, &A->cg64.state, &A->cg_step, &A->cg32.r, &A->cg32.p, &A->cg32.q,
                             &A->cg32.state, &A->cg_outer_state, &A->cg_outer_r, &A->ir_x, &A->ir_b,
                             &A->pr_y, &A->pr_state, &A->pr_l1, &A->pr_has_out, &A->bfs_row,
                             &A->bfs_state, &A->bfs_level, &A->spmm_buf};
@@ -731,13 +731,13 @@ lilac_status lilac_debug_inject(lilac_csr A, int32_t what, int64_t arg) try {
         g_fail_alloc_in.store(arg);
         return LILAC_OK;
     }
-    if (what == LILAC_INJECT_SKIP_COPY) {
+    if (what == LILAC_INJECT_SKIP_COPY || what == LILAC_INJECT_SKIP_BARRIER) {
         if (!A) {
             set_last_error("NULL handle");
             return LILAC_ERR_INVALID_ARG;
         }
         DeviceGuard g(A->device);
-        const int v = DEV_INJECT_SKIP_COPY;
+        const int v = what == LILAC_INJECT_SKIP_COPY ? DEV_INJECT_SKIP_COPY : DEV_INJECT_SKIP_BARRIER;
         LILAC_CUDA_TRY(cudaMemcpy(A->status.as<int>() + 1, &v, sizeof(int), cudaMemcpyHostToDevice));
         return LILAC_OK;
     }

@@ -13,7 +13,9 @@ namespace lilac {
 enum : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
 // Test hook word (Scratch::status[1]): the next STAGED launch leaves the first
 // tile copy of CTA 0 unissued, so its bounded wait expires.
-enum : int { DEV_INJECT_NONE = 0, DEV_INJECT_SKIP_COPY = 2 };
+// DEV_INJECT_SKIP_BARRIER: in the next fused CG step, CTA 0 does not arrive
+// at the grid barrier, so the other CTAs' bounded waits expire.
+enum : int { DEV_INJECT_NONE = 0, DEV_INJECT_SKIP_COPY = 2, DEV_INJECT_SKIP_BARRIER = 3 };
 
 // A bounded wait gives up after this many nanoseconds of %globaltimer.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s
@@ -72,6 +74,45 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
         if (global_timer_ns() - t0 > kWaitLimitNs) return false;
     }
     return true;
+}
+
+// Grid-wide barrier for a launch whose CTAs are all resident at once (a grid
+// of at most one small CTA per SM): thread 0 of every CTA adds one to bar[0]
+// and waits until all gridDim.x have, bounded by kWaitLimitNs of
+// %globaltimer; the last CTA to leave resets both counters (bar[1] counts
+// departures), so the next launch finds them zero.  A CTA whose wait runs out
+// records DEV_TIMEOUT in *status and gets false (its counters stay set until
+// the handle's scratch is cleared).  skip (test hook, thread 0): this CTA
+// does not arrive, so the others' waits run out.
+__device__ __forceinline__ bool grid_barrier_bounded(unsigned* bar, int* status, bool skip) {
+    __shared__ int ok_s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = skip ? 0 : 1;
+        if (ok) {
+            __threadfence();
+            atomicAdd(bar, 1u);
+            const uint64_t t0 = global_timer_ns();
+            while (*reinterpret_cast<volatile unsigned*>(bar) < gridDim.x) {
+                if (global_timer_ns() - t0 > kWaitLimitNs) {
+                    ok = 0;
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        if (ok) {
+            if (atomicAdd(bar + 1, 1u) == gridDim.x - 1u) {
+                atomicExch(bar, 0u);
+                atomicExch(bar + 1, 0u);
+            }
+        } else {
+            atomicExch(status, DEV_TIMEOUT);
+        }
+        ok_s = ok;
+    }
+    __syncthreads();
+    return ok_s != 0;
 }
 
 // L2 eviction policies for bulk copies of data read once per pass.

@@ -163,6 +163,9 @@ struct lilac_csr_s {
     // solvers
     lilac::CgWork cg64, cg32;
     lilac::DevBuf cg_outer_state, cg_outer_r, ir_x, ir_b;  // mixed precision outer loop
+    // fused CG step after the SLAB CG form: grid barrier counters [2] (zero
+    // between launches), then one r.r partial per CTA
+    lilac::DevBuf cg_step;
     lilac::DevBuf pr_y, pr_state, pr_l1, pr_has_out;
     bool pr_has_out_valid = false;
     // BFS: row index of every nonzero (built on first use), state, staged levels

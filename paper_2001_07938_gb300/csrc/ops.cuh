@@ -277,7 +277,7 @@ static __global__ void __launch_bounds__(kVecThreads)
 // from a shared counter.  The t live in shared memory after the slab when
 // they fit (tsm), else in T.  The CTA's sum goes to slot blockIdx.x of
 // s.partials and the kernel ends there, with no grid ticket:
-// cg_update_slabs_kernel adds the slots (fixed order) and takes alpha.
+// cg_step_slabs_kernel adds the slots (fixed order) and takes alpha.
 template <int THREADS, int UNR>
 __global__ void __launch_bounds__(THREADS, 1)
     spmv_slab_cg_kernel(SlabView V, const int4* __restrict__ ranges, int tsm,
@@ -325,48 +325,44 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (threadIdx.x == 0) s.partials[blockIdx.x] = tot[0];
 }
 
-// The update after the CG form of the SLAB SpMV (spmv_slab_cg_kernel):
-// p.q arrives as that kernel's per-CTA sums, which every CTA here adds in
-// slot order (so all take the same alpha = r.r / p.q; breakdown when
-// p.q <= 0 or not finite), and q as the S slab partials P[s][i], added in
-// slab order.  Then x += alpha p, r -= alpha q and r.r as cg_update_kernel.
-struct FinCgUpdateSlabs {
-    CgState* st;
-    double pq, alpha;
-    __device__ void finish(const double* tot) const {
-        st->pq = pq;
-        if (!(pq > 0.0) || !isfinite(pq)) {
-            st->status = LILAC_ERR_BREAKDOWN;
-            st->done = 1;
-            return;
-        }
-        st->alpha = alpha;
-        FinCgUpdate<double>{st, nullptr}.finish(tot);
-    }
-};
-
+// One whole CG step after the CG form of the SLAB SpMV, in one launch: the
+// update (alpha = r.r / p.q with p.q from the SpMV's CTA sums, added in slot
+// order by every CTA; q from the slab partials added in slab order;
+// x += alpha p, r -= alpha q), then a grid barrier, then
+// r.r from this kernel's CTA sums (every CTA adds them in slot order, so all
+// take the same beta = r.r / r.r_old and the same convergence decision) and
+// p = r + beta p on the elements the thread updated.  CTA 0 records the step
+// in the solver state (iterations, alpha, beta, r.r, done / status) with the
+// rules of FinCgUpdate, and a breakdown when p.q <= 0 or is not finite.  The
+// grid must fit on the GPU at once (at
+// most one CTA per SM, see grid_barrier_bounded); a barrier that times out
+// leaves DEV_TIMEOUT in the handle's status word.
 static __global__ void __launch_bounds__(kVecThreads)
-    cg_update_slabs_kernel(int n, double* __restrict__ x, double* __restrict__ r,
-                           const double* __restrict__ p, const double* __restrict__ P, int S,
-                           const double* __restrict__ pq_parts, int nparts, CgState* st,
-                           Scratch s) {
+    cg_step_slabs_kernel(int n, double* __restrict__ x, double* __restrict__ r,
+                         double* __restrict__ p, const double* __restrict__ P, int S,
+                         const double* __restrict__ pq_parts, int nparts, CgState* st,
+                         double* __restrict__ rr_parts, unsigned* bar, int* status) {
     if (cg_done(st)) return;
-    const double rr = st->rr;  // in flight while warp 0 adds the SpMV's sums
-    __shared__ double sh_pq;
+    const double rr = st->rr;
+    const int it = st->iters + 1;
+    const int max_iter = st->max_iter;
+    const double tol2 = st->tol2;
+    __shared__ double sh_v;
     if (threadIdx.x < 32) {
         double v = 0.0;
         for (int i = (int)threadIdx.x; i < nparts; i += 32) v += __ldcg(pq_parts + i);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) sh_pq = v;
+        if (threadIdx.x == 0) sh_v = v;
     }
     __syncthreads();
-    const double pq = sh_pq;
+    const double pq = sh_v;
     const bool ok = pq > 0.0 && isfinite(pq);
     const double alpha = ok ? rr / pq : 0.0;
-    double rr_new = 0.0;
+    double red[1] = {0.0};
     const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
-    const int nv = (ok && aligned16(x, r, p, P) && (n & 1) == 0) ? n / 2 : 0;
+    const bool vec = aligned16(x, r, p, P) && (n & 1) == 0;
+    const int nv = (ok && vec) ? n / 2 : 0;
     for (int i = g0; i < nv; i += gs) {
         double2 xv = reinterpret_cast<const double2*>(x)[i], rv = reinterpret_cast<const double2*>(r)[i];
         const double2 pv = reinterpret_cast<const double2*>(p)[i];
@@ -380,8 +376,8 @@ static __global__ void __launch_bounds__(kVecThreads)
         xv.y += alpha * pv.y;
         rv.x -= alpha * qv.x;
         rv.y -= alpha * qv.y;
-        rr_new += rv.x * rv.x;
-        rr_new += rv.y * rv.y;
+        red[0] += rv.x * rv.x;
+        red[0] += rv.y * rv.y;
         reinterpret_cast<double2*>(x)[i] = xv;
         reinterpret_cast<double2*>(r)[i] = rv;
     }
@@ -391,10 +387,62 @@ static __global__ void __launch_bounds__(kVecThreads)
         x[i] += alpha * p[i];
         const double ri = r[i] - alpha * qi;
         r[i] = ri;
-        rr_new += ri * ri;
+        red[0] += ri * ri;
     }
-    double red[1] = {rr_new};
-    grid_reduce_finish<1, kVecThreads>(FinCgUpdateSlabs{st, pq, alpha}, red, s, 0);
+    {
+        __shared__ double sh[32];
+        double tot[1];
+        block_sum<1, kVecThreads>(red, tot, sh);
+        if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot[0];
+    }
+    bool skip = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        skip = atomicCAS(status + 1, DEV_INJECT_SKIP_BARRIER, DEV_INJECT_NONE) == DEV_INJECT_SKIP_BARRIER;
+    if (!grid_barrier_bounded(bar, status, skip)) return;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = (int)threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(rr_parts + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sh_v = v;
+    }
+    __syncthreads();
+    const double rr_new = sh_v;
+    bool done = true;
+    int code = LILAC_ERR_BREAKDOWN;
+    if (ok) {
+        if (rr_new == 0.0 || (tol2 >= 0.0 && rr_new <= tol2)) {
+            code = LILAC_OK;
+        } else if (it >= max_iter) {
+            code = tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+        } else {
+            done = false;
+        }
+    }
+    const double beta = rr_new / rr;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        st->pq = pq;
+        if (ok) {
+            st->alpha = alpha;
+            st->iters = it;
+            st->beta = beta;
+            st->rr = rr_new;
+        }
+        if (done) {
+            st->status = code;
+            st->done = 1;
+        }
+    }
+    if (done) return;
+    const int nv2 = vec ? n / 2 : 0;
+    for (int i = g0; i < nv2; i += gs) {
+        const double2 rv = reinterpret_cast<const double2*>(r)[i];
+        double2 pv = reinterpret_cast<const double2*>(p)[i];
+        pv.x = rv.x + beta * pv.x;
+        pv.y = rv.y + beta * pv.y;
+        reinterpret_cast<double2*>(p)[i] = pv;
+    }
+    for (int i = nv2 * 2 + g0; i < n; i += gs) p[i] = r[i] + beta * p[i];
 }
 
 // p = r + beta p.

@@ -52,7 +52,7 @@ EXPORTS = (
     "lilac_csr_tune_table",
 )
 
-LILAC_INJECT_ALLOC_FAIL, LILAC_INJECT_SKIP_COPY = 1, 2
+LILAC_INJECT_ALLOC_FAIL, LILAC_INJECT_SKIP_COPY, LILAC_INJECT_SKIP_BARRIER = 1, 2, 3
 
 LILAC_LAYOUT_ROWS, LILAC_LAYOUT_VECTORS = 0, 1
 

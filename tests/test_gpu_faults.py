@@ -1,13 +1,14 @@
 """Failure paths, exercised without faulting the GPU: an injected allocation
-failure, and a bounded device wait made to expire by a host-set test hook
-(the STAGED kernel's first bulk copy left unissued); the handle reports the
-timeout, stays sticky, and works again after lilac_csr_reset_error."""
+failure, and bounded device waits made to expire by host-set test hooks (the
+STAGED kernel's first bulk copy left unissued; a CTA that skips the fused CG
+step's grid barrier); the handle reports the timeout, stays sticky, and works
+again after lilac_csr_reset_error."""
 import numpy as np
 import pytest
 
 from paper_2001_07938_gb300 import inputs
 from paper_2001_07938_gb300 import lilac as L
-from lilac_testutil import assert_spmv_close, torch_cuda
+from lilac_testutil import assert_spmv_close, dev, host, torch_cuda, true_rel_residual
 
 pytestmark = pytest.mark.gpu
 
@@ -53,4 +54,32 @@ def test_bounded_wait_timeout_is_reported_sticky_and_reset():
     y[:] = 0.0
     M.spmv(x, y)
     assert_spmv_close(A, x, y, False, "after reset")
+    M.close()
+
+
+def test_cg_step_barrier_timeout_is_reported_sticky_and_reset():
+    """FP64 CG on a SLAB handle runs each step's update and direction in one
+    launch with a bounded grid barrier.  With CTA 0 kept from arriving, the
+    other CTAs give up after ~2 s and the solve reports LILAC_ERR_TIMEOUT
+    (sticky); after the reset the same solve converges."""
+    torch = torch_cuda()
+    A = inputs.spd_random(30000, 40, 20.0, 4)
+    b = inputs.uniform(3, A.n)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_SLAB, 4)
+    assert M.info()["active_variant"] == L.LILAC_VARIANT_SLAB
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    L.lilac_debug_inject(M.handle, L.LILAC_INJECT_SKIP_BARRIER)
+    with pytest.raises(L.LilacError) as e:
+        M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+    assert e.value.status == L.LILAC_ERR_TIMEOUT
+    with pytest.raises(L.LilacError) as e:
+        M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+    assert e.value.status == L.LILAC_ERR_TIMEOUT
+    L.lilac_csr_reset_error(M.handle)
+    x.zero_()
+    st, info = M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+    torch.cuda.synchronize()
+    assert st == L.LILAC_OK
+    assert true_rel_residual(A, b, host(x)) <= 1e-10
     M.close()
