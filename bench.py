@@ -64,7 +64,8 @@ FP64_PEAK_TFLOPS = 1.25
 # then created without the timed tuning, so that a run under a profiler uses
 # the same kernel as the plain run)
 FORCED_VARIANT = None
-VARIANT_CODES = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6, "sell": 7}
+VARIANT_CODES = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "jds": 6, "sell": 7,
+                 "hub": 8}
 
 
 def _kernel_src_hash():
@@ -151,7 +152,9 @@ def _kernel_name(M):
     return {1: "spmv_rows_kernel (scalar)", 2: f"spmv_rows_kernel (vector, {w} lanes/row)",
             3: f"spmv_staged_kernel ({w} lanes/row)", 4: "spmv_merge_kernel",
             5: "spmv_slab_kernel (sliced ELL over x slabs in shared memory, slabs combined per row group)",
-            6: "spmv_jds_kernel", 7: "spmv_sell_kernel (sliced ELL, one lane per row)"
+            6: "spmv_jds_kernel", 7: "spmv_sell_kernel (sliced ELL, one lane per row)",
+            8: "hub_pieces_kernel + spmv_sell_kernel (hub columns' x in shared memory, "
+               "cold columns as sliced ELL adding the slab sums)"
             }.get(info["variant"], "spmv")
 
 

@@ -94,13 +94,21 @@ typedef enum {
                                  rows sorted by length, one thread per row, nonzero d of all
                                  rows stored together; on another value array (an FP32 copy)
                                  STAGED runs */
-    LILAC_VARIANT_SELL = 7    /* sliced ELL (chunks of 32 rows, element k of the chunk's 32
+    LILAC_VARIANT_SELL = 7,   /* sliced ELL (chunks of 32 rows, element k of the chunk's 32
                                  rows stored together), built once per matrix: one lane per row
                                  with one fused multiply-add per nonzero; rows longer than a
                                  piece cap are cut into pieces finished in piece order; rows
                                  sorted by length when row order would pad much.  On another
                                  value array (an FP32 copy), or where the copy would pad by more
                                  than half, STAGED runs */
+    LILAC_VARIANT_HUB = 8     /* hub columns, built once per matrix, for power-law matrices whose x
+                                 exceeds 1 MB: the most frequent columns (up to 4 slabs of 192 KB
+                                 of x, while a slab adds 5% of the nonzeros) are gathered once
+                                 per call and held in shared memory, one CTA per SM summing each
+                                 row's piece of its slab; the other nonzeros run as a sliced ELL
+                                 copy whose lanes add the slab sums before the epilogue.  Where
+                                 the hub columns hold under 40% of the nonzeros, or on another
+                                 value array, STAGED runs */
 } lilac_variant;
 
 /* lilac_csr_create flags.  By default create times the candidate SpMV

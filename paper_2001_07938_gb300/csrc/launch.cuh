@@ -322,8 +322,83 @@ lilac_status launch_sell(lilac_csr_s* A, const typename Op::ValT* val, const typ
     return LILAC_OK;
 }
 
-#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, FN_JDS, FN_SELL, ...) \
+// HUB: the hub columns' x gathered, their pieces summed per slab from shared
+// memory (hub_pieces_kernel), the cold part through the SELL kernel, which
+// adds the slab partials (lilac_hub.cu builds the copies).  Another value
+// array (an FP32 copy) goes to STAGED, as does a handle without the copies.
+template <int V, class Op>
+lilac_status prepare_hub(lilac_csr_s* A) {
+    int& bps = bps_slot<V + 512, Op, true>(A->device);
+    if (bps == 0) {
+        auto kern = hub_pieces_kernel<kSlabThreads, kSlabUnroll, Op>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            kSlabMaxBytes + 64));
+        bps = 1;
+    }
+    LILAC_TRY(prepare_sell<V, Op>(A));
+    return prepare_staged_any<Op>(A);
+}
+
+template <class Op>
+bool hub_split_epilogue(const lilac_csr_s* A) {
+    return Op::kTwoPhase && Op::NR > 0 && A->hub_two_pass;
+}
+
+template <int V, class Op>
+lilac_status launch_hub(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
+                        const Op& op, cudaStream_t stream) {
+    if (!A->hub_built || (const void*)val != A->val.p) return launch_staged_any<Op>(A, val, x, op, stream);
+    LILAC_TRY(prepare_hub<V, Op>(A));
+    using VecT = typename Op::VecT;
+    using AccT = typename Op::AccT;
+    const int H = A->hub_H;
+    VecT* xhot = A->hub_xhot.as<VecT>();
+    hub_gather_kernel<VecT><<<(H + 255) / 256, 256, 0, stream>>>(H, A->hub_cols.as<int>(), x, xhot);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    // rows: the stride of the slab partials P
+    SlabView hv{A->hub_cptr.as<int>(), A->hub_crow.as<int>(), A->hub_col.as<uint16_t>(), nullptr,
+                nullptr, nullptr, A->hub_pstride, H, A->hub_W, A->hub_S, 0};
+    const size_t smem = (sizeof(VecT) * ((size_t)A->hub_W + 1) + 15) & ~size_t(15);
+    const HubSplits hs{A->hub_splits.as<int4>(), A->hub_sub_split.as<int>(), A->hub_part.as<double>(),
+                       A->hub_cnt.as<unsigned>()};
+    hub_pieces_kernel<kSlabThreads, kSlabUnroll, Op><<<(unsigned)A->hub_grid, kSlabThreads, smem, stream>>>(
+        hv, A->hub_ranges.as<int4>(), A->hub_val.as<typename Op::ValT>(), xhot, H,
+        A->hub_P.as<AccT>(), hs, op);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    const int bps = bps_slot<V + 256, Op, false>(A->device);
+    constexpr int kWarps = kSellThreads / 32;
+    int64_t grid = (int64_t)A->sm_count * bps;
+    const int64_t need = ((int64_t)A->hubc_nchunks + kWarps - 1) / kWarps;
+    grid = std::max<int64_t>(1, std::min<int64_t>(std::min<int64_t>(grid, need), kMaxCtas));
+    SellView cv{A->hubc_cptr.as<int>(), A->hubc_crow.as<int>(), A->hubc_col.as<int>(),
+                A->hubc_splits.as<int4>(), A->hubc_piece_split.as<int>(), A->hubc_nchunks,
+                A->hubc_nsplit, A->hub_P.p, A->hubc_mask.as<uint8_t>(), A->hub_pstride,
+                32 * A->hubc_nchunks};
+    Scratch sc = A->scratch();
+    sc.long_part = A->hubc_part.as<double>();
+    sc.long_red = A->hubc_red.as<double>();
+    sc.long_cnt = A->hubc_cnt.as<unsigned>();
+    if constexpr (Op::kTwoPhase && Op::NR > 0) {
+        if (hub_split_epilogue<Op>(A)) {
+            spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op><<<(unsigned)grid, kSellThreads, 0, stream>>>(
+                cv, A->hubc_val.as<typename Op::ValT>(), x, op, sc);
+            LILAC_CUDA_TRY(cudaGetLastError());
+            rows_reduce_kernel<kVecThreads, Op><<<vec_grid(A, A->rows), kVecThreads, 0, stream>>>(
+                A->rows, op, A->scratch());
+            LILAC_CUDA_TRY(cudaGetLastError());
+            return LILAC_OK;
+        }
+    }
+    spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op><<<(unsigned)grid, kSellThreads, 0, stream>>>(
+        cv, A->hubc_val.as<typename Op::ValT>(), x, op, sc);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+#define LILAC_DISPATCH_SPMV(FN_ROWS, FN_STAGED, FN_SLAB, FN_MERGE, FN_JDS, FN_SELL, FN_HUB, ...) \
     switch (A->variant) {                                                   \
+        case LILAC_VARIANT_HUB: /* hub slabs + cold sliced ELL */           \
+            return FN_HUB<1, Op>(__VA_ARGS__);                              \
         case LILAC_VARIANT_SELL: /* one lane per row piece */               \
             return FN_SELL<1, Op>(__VA_ARGS__);                             \
         case LILAC_VARIANT_MERGE: /* thread-sequential: no lanes per row */ \
@@ -368,20 +443,21 @@ template <class Op>
 int spmv_launch_count(const lilac_csr_s* A, const void* val) {
     if (val != A->val.p) return 1;
     if (A->variant == LILAC_VARIANT_SELL && A->sell_built && sell_split_epilogue<Op>(A)) return 2;
+    if (A->variant == LILAC_VARIANT_HUB && A->hub_built) return hub_split_epilogue<Op>(A) ? 4 : 3;
     return 1;
 }
 
 template <class Op>
 lilac_status prepare_spmv(lilac_csr_s* A) {
     LILAC_DISPATCH_SPMV(prepare_rows, prepare_staged, prepare_slab_and_staged, prepare_merge,
-                        prepare_jds, prepare_sell, A)
+                        prepare_jds, prepare_sell, prepare_hub, A)
 }
 
 template <class Op>
 lilac_status launch_spmv(lilac_csr_s* A, const typename Op::ValT* val, const typename Op::VecT* x,
                          const Op& op, cudaStream_t stream) {
     LILAC_DISPATCH_SPMV(launch_rows, launch_staged, launch_slab, launch_merge, launch_jds,
-                        launch_sell, A, val, x, op, stream)
+                        launch_sell, launch_hub, A, val, x, op, stream)
 }
 
 // Replay `body` (which enqueues work on the stream it is given) as a CUDA

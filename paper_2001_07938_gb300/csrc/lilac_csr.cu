@@ -273,7 +273,12 @@ int64_t lilac_csr_s::device_bytes() const {
                                   &cg32.p, &cg32.q, &cg32.state, &cg_outer_state, &cg_outer_r,
                                   &ir_x, &ir_b, &pr_y, &pr_state, &pr_l1, &pr_has_out,
                                   &jds_slot_row, &jds_row_slot, &jds_len, &jds_ptr, &jds_col,
-                                  &jds_val, &bfs_row, &bfs_state, &bfs_level, &spmm_buf};
+                                  &jds_val, &bfs_row, &bfs_state, &bfs_level, &spmm_buf,
+                                  &hub_cols, &hub_xhot, &hub_cptr, &hub_crow, &hub_col, &hub_val,
+                                  &hub_perm, &hub_ranges, &hub_P, &hubc_cptr, &hubc_crow,
+                                  &hubc_col, &hubc_val, &hubc_perm, &hubc_splits,
+                                  &hubc_piece_split, &hubc_part, &hubc_red, &hubc_cnt, &hubc_mask,
+                                  &hub_splits, &hub_sub_split, &hub_part, &hub_cnt};
     int64_t t = 0;
     for (auto* b : all) t += (int64_t)b->bytes;
     return t;
@@ -284,6 +289,7 @@ static lilac_status zero_scratch(lilac_csr A, cudaStream_t stream) {
                              &A->status, &A->slab_gcnt, &A->cg_step};
     for (auto* b : bufs)
         if (b->p) LILAC_CUDA_TRY(cudaMemsetAsync(b->p, 0, b->bytes, stream));
+    LILAC_TRY(hub_zero_counters(A, stream));
     return sell_zero_counters(A, stream);
 }
 
@@ -459,6 +465,15 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
             sell_release(A);
         }
     }
+    bool hub_trial = false;
+    if (!A->hub_built && hub_worthwhile(A)) {
+        if (ensure_hub(A, stream) == LILAC_OK && A->hub_built) {
+            hub_trial = true;
+            cands.push_back({LILAC_VARIANT_HUB, staged_w});
+        } else {
+            hub_release(A);
+        }
+    }
     bool jds_trial = false;
     if (A->max_row_len <= 1024 && !A->jds_built) {
         if (ensure_jds(A, stream) == LILAC_OK) {
@@ -509,11 +524,13 @@ static lilac_status tune_timed(lilac_csr A, cudaStream_t stream) {
     A->vwidth = bestc.width;
     if ((jds_trial && bestc.variant != LILAC_VARIANT_JDS) ||
         (slab_trial && bestc.variant != LILAC_VARIANT_SLAB) ||
-        (sell_trial && bestc.variant != LILAC_VARIANT_SELL))
+        (sell_trial && bestc.variant != LILAC_VARIANT_SELL) ||
+        (hub_trial && bestc.variant != LILAC_VARIANT_HUB))
         LILAC_CUDA_TRY(cudaStreamSynchronize(stream));
     if (jds_trial && bestc.variant != LILAC_VARIANT_JDS) jds_release(A);
     if (slab_trial && bestc.variant != LILAC_VARIANT_SLAB) slab_release(A);
     if (sell_trial && bestc.variant != LILAC_VARIANT_SELL) sell_release(A);
+    if (hub_trial && bestc.variant != LILAC_VARIANT_HUB) hub_release(A);
     return LILAC_OK;
 }
 
@@ -535,6 +552,7 @@ static void free_handle(lilac_csr A) {
     jds_release(A);
     slab_release(A);
     sell_release(A);
+    hub_release(A);
     delete A;
 }
 
@@ -600,6 +618,7 @@ lilac_status lilac_csr_update_values(lilac_csr A, const void* vals, lilac_mem wh
     A->val32_valid = false;  // derived FP32 copy is stale
     LILAC_TRY(slab_refresh_values(A, s));
     LILAC_TRY(sell_refresh_values(A, s));
+    LILAC_TRY(hub_refresh_values(A, s));
     LILAC_TRY(jds_refresh_values(A, s));
     return LILAC_OK;
 } catch (...) {
@@ -641,12 +660,15 @@ lilac_status lilac_csr_info(lilac_csr A, lilac_csr_info_t* info) try {
     int active = A->variant;
     if ((active == LILAC_VARIANT_SLAB && !A->slab_built) ||
         (active == LILAC_VARIANT_SELL && !A->sell_built) ||
+        (active == LILAC_VARIANT_HUB && !A->hub_built) ||
         (active == LILAC_VARIANT_JDS && !A->jds_built))
         active = LILAC_VARIANT_STAGED;
     info->active_variant = active;
     info->sell_split_rows = A->sell_built ? A->sell_nsplit : 0;
     info->sell_padded_nnz = A->sell_built ? A->sell_elems : 0;
-    info->spmv_kernels = active == LILAC_VARIANT_SELL && A->sell_two_pass ? 2 : 1;
+    info->spmv_kernels = active == LILAC_VARIANT_SELL && A->sell_two_pass ? 2
+                         : active == LILAC_VARIANT_HUB ? (A->hub_two_pass ? 4 : 3)
+                                                       : 1;
     return LILAC_OK;
 } catch (...) {
     return lilac::api_failure();
@@ -675,7 +697,7 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
         set_last_error("NULL handle");
         return LILAC_ERR_INVALID_ARG;
     }
-    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_SELL ||
+    if (variant < LILAC_VARIANT_SCALAR || variant > LILAC_VARIANT_HUB ||
         (vector_width != 0 && (vector_width < 1 || vector_width > 32 ||
                                (vector_width & (vector_width - 1)) != 0))) {
         set_last_error("unsupported variant / width");
@@ -692,6 +714,10 @@ lilac_status lilac_csr_set_variant(lilac_csr A, int32_t variant, int32_t vector_
     if (variant == LILAC_VARIANT_SELL) {
         DeviceGuard g(A->device);
         LILAC_TRY(ensure_sell(A, nullptr));
+    }
+    if (variant == LILAC_VARIANT_HUB) {
+        DeviceGuard g(A->device);
+        LILAC_TRY(ensure_hub(A, nullptr));
     }
     A->variant = variant;
     if (vector_width) A->vwidth = vector_width;

@@ -147,6 +147,23 @@ struct lilac_csr_s {
     int64_t sell_elems = 0;
     bool sell_built = false;
     bool sell_two_pass = false;  // sorted rows, many of them: reductions in a row-order pass
+    // HUB copies (built on first use; lilac_hub.cu): the hub columns and their
+    // gathered x, the hot part (chunk offsets, lane rows / sub-pieces, 16-bit
+    // slab-local columns, values, CSR index per element, CTA runs, slab
+    // partials P, long pieces' splits with their sums and counters), and
+    // the cold part as a sliced ELL copy (chunk offsets, lane rows / pieces,
+    // columns, values, CSR index per element, split rows and their scratch,
+    // per lane the mask of slabs in which its row has a piece)
+    lilac::DevBuf hub_cols, hub_xhot, hub_cptr, hub_crow, hub_col, hub_val, hub_perm, hub_ranges,
+        hub_P, hub_splits, hub_sub_split, hub_part, hub_cnt;
+    lilac::DevBuf hubc_cptr, hubc_crow, hubc_col, hubc_val, hubc_perm, hubc_splits,
+        hubc_piece_split, hubc_part, hubc_red, hubc_cnt, hubc_mask;
+    int hub_H = 0, hub_S = 0, hub_W = 0, hub_grid = 0, hub_pstride = 0;
+    int hubc_nchunks = 0, hubc_nsplit = 0, hubc_npieces = 0;
+    int64_t hub_elems = 0, hubc_elems = 0;
+    double hub_share = 0.0;
+    bool hub_built = false;
+    bool hub_two_pass = false;  // many short rows: reductions in a row-order pass
     // JDS copy (built on first use): slot -> row, row -> slot, slot lengths,
     // jagged diagonal offsets, columns and values in JDS order
     lilac::DevBuf jds_slot_row, jds_row_slot, jds_len, jds_ptr, jds_col, jds_val;
@@ -214,6 +231,11 @@ lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
 void slab_release(lilac_csr A);
 bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status ensure_sell(lilac_csr A, cudaStream_t stream);
+bool hub_worthwhile(const lilac_csr_s* A);
+lilac_status ensure_hub(lilac_csr A, cudaStream_t stream);
+lilac_status hub_refresh_values(lilac_csr A, cudaStream_t stream);
+lilac_status hub_zero_counters(lilac_csr A, cudaStream_t stream);
+void hub_release(lilac_csr A);
 lilac_status sell_refresh_values(lilac_csr A, cudaStream_t stream);
 void sell_release(lilac_csr A);
 lilac_status sell_zero_counters(lilac_csr A, cudaStream_t stream);

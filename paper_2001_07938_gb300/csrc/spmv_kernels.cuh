@@ -403,7 +403,25 @@ struct SellView {
     const int* __restrict__ piece_split;  // piece -> split row
     int nchunks;
     int nsplit;
+    // HUB: the copy holds a row's other (cold) columns only; the slab partials
+    // of the slabs q in the row's mask (add_mask per lane, splits[].w for a
+    // split row) are added, in slab order, before the epilogue (addP null:
+    // none).  They are laid out by lane: addP[q * add_stride + i] for the row
+    // of lane i = 32 * chunk + lane, addP[q * add_stride + add_split_base +
+    // s] for split row s, so a warp's reads are coalesced.
+    const void* addP;
+    const uint8_t* add_mask;
+    int add_stride;
+    int add_split_base;
 };
+
+template <class AccT>
+__device__ __forceinline__ AccT sell_add_slabs(const SellView& S, int idx, unsigned mask, AccT acc) {
+    const AccT* __restrict__ P = static_cast<const AccT*>(S.addP);
+    for (int q = 0; mask != 0u; ++q, mask >>= 1)
+        if (mask & 1u) acc += __ldg(P + (size_t)q * S.add_stride + idx);
+    return acc;
+}
 
 template <bool kStoreOnly, class AccT, class Op>
 __device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& op, const Scratch& s,
@@ -418,6 +436,7 @@ __device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& o
         __threadfence();
         AccT rs = AccT(0);
         for (int j = 0; j < sp.z; ++j) rs += AccT(__ldcg(&s.long_part[sp.y + j]));
+        if (S.addP) rs = sell_add_slabs(S, S.add_split_base + lid, (unsigned)sp.w, rs);
         if constexpr (kStoreOnly) {
             op.store(sp.x, rs);
         } else {
@@ -447,10 +466,24 @@ __global__ void __launch_bounds__(THREADS)
     typename Op::RedT red[NR > 0 ? NR : 1] = {};
     const int lane = threadIdx.x & 31;
     const int nwarps = (int)(gridDim.x * (THREADS / 32));
-    for (int ch = (int)((blockIdx.x * THREADS + threadIdx.x) >> 5); ch < S.nchunks; ch += nwarps) {
-        const int base = __ldg(S.cptr + ch);
-        const int width = (__ldg(S.cptr + ch + 1) - base) >> 5;
-        const int who = __ldg(S.crow + (size_t)ch * 32 + lane);
+    // the next chunk's offsets and lane row are loaded while this chunk runs:
+    // short chunks (many on power-law matrices) then cost no extra round trip
+    int ch = (int)((blockIdx.x * THREADS + threadIdx.x) >> 5);
+    int nbase = 0, nend = 0, nwho = -1;
+    if (ch < S.nchunks) {
+        nbase = __ldg(S.cptr + ch);
+        nend = __ldg(S.cptr + ch + 1);
+        nwho = __ldg(S.crow + (size_t)ch * 32 + lane);
+    }
+    for (; ch < S.nchunks; ch += nwarps) {
+        const int base = nbase;
+        const int width = (nend - base) >> 5;
+        const int who = nwho;
+        if (ch + nwarps < S.nchunks) {
+            nbase = __ldg(S.cptr + ch + nwarps);
+            nend = __ldg(S.cptr + ch + nwarps + 1);
+            nwho = __ldg(S.crow + (size_t)(ch + nwarps) * 32 + lane);
+        }
         const ValT* __restrict__ vp = val + base + lane;
         const int* __restrict__ cp = S.col + base + lane;
         AccT acc = AccT(0);
@@ -488,6 +521,8 @@ __global__ void __launch_bounds__(THREADS)
                 if (k + u < width) acc += AccT(vv[u]) * AccT(xx[u]);
         }
         if (who >= 0) {
+            if (S.addP)
+                acc = sell_add_slabs(S, ch * 32 + lane, __ldg(S.add_mask + (size_t)ch * 32 + lane), acc);
             if constexpr (kStoreOnly)
                 op.store(who, acc);
             else
@@ -558,10 +593,21 @@ struct SlabView {
 // current ones, so a warp keeps loads in flight while it waits for the FP64
 // pipe.
 template <int UNR, bool PIPE, class AccT, class ValT, class VecT>
+__device__ __forceinline__ AccT slab_lane_sum(const SlabView& V, const ValT* __restrict__ sval,
+                                              const VecT* xs, int base, int width, int lane);
+
+template <int UNR, bool PIPE, class AccT, class ValT, class VecT>
 __device__ __forceinline__ AccT slab_chunk_sum(const SlabView& V, const ValT* __restrict__ sval,
                                                const VecT* xs, int ch, int lane) {
     const int base = __ldg(V.cptr + ch);
     const int width = (__ldg(V.cptr + ch + 1) - base) >> 5;
+    return slab_lane_sum<UNR, PIPE, AccT>(V, sval, xs, base, width, lane);
+}
+
+// The same with the chunk's element offset and width given (loaded ahead).
+template <int UNR, bool PIPE, class AccT, class ValT, class VecT>
+__device__ __forceinline__ AccT slab_lane_sum(const SlabView& V, const ValT* __restrict__ sval,
+                                              const VecT* xs, int base, int width, int lane) {
     const ValT* __restrict__ vp = sval + base + lane;
     const uint16_t* __restrict__ cp = V.col + base + lane;
     AccT acc = AccT(0);
@@ -684,6 +730,103 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int q = 0; q < NR; ++q) r2[q] = red_value(red[q]);
         grid_reduce_slots<NR, THREADS>(op, r2, s, last ? c.w : -1, V.G);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// HUB kernels (lilac_hub.cu builds the copies).  A power-law matrix whose x
+// is far larger than L1 spends its time on random x gathers that each move a
+// 32-byte sector from L2 for a 4- or 8-byte value.  The hub columns, the most
+// frequent ones, hold most of the nonzeros: their x is gathered once per
+// SpMV (hub_gather_kernel), cut into S slabs of W values, and held in shared
+// memory by one CTA per SM (hub_pieces_kernel), which sums every row's piece
+// of that slab with 16-bit slab-local columns into P[s][row] (rows without a
+// piece in the slab are no lane of it), laid out by the row's lane in the
+// cold copy.  The other (cold) nonzeros form a sliced ELL copy run by
+// spmv_sell_kernel, which adds the partials of the slabs in the row's mask to
+// its sum before the epilogue.  Each element issues one load, from shared
+// memory or through L1/L2, never both.
+
+// x of the hub columns (hot[h], h < H) into xhot, ahead of the pieces kernel.
+template <class VecT>
+__global__ void hub_gather_kernel(int H, const int* __restrict__ hot, const VecT* __restrict__ x,
+                                  VecT* __restrict__ xhot) {
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < H; h += gridDim.x * blockDim.x)
+        xhot[h] = __ldg(x + __ldg(hot + h));
+}
+
+// Hot pieces longer than the copy's cap are cut into sub-pieces of at most
+// the cap, one lane each (lane row -(2 + sub-piece)): sub-piece p's sum goes
+// to part[p], and the last of a split's sub-pieces to arrive (counter) adds
+// them in order into P[slab][row].
+struct HubSplits {
+    const int4* __restrict__ splits;  // {row, first sub-piece, sub-pieces, slab}
+    const int* __restrict__ sub_split;  // sub-piece -> split
+    double* part;
+    unsigned* cnt;
+};
+
+// One CTA per {slab, first chunk, end chunk} run: slab s of xhot in shared
+// memory (plus a zero at W for padding), warps take the run's chunks from a
+// shared counter, lane l of a chunk stores its piece sum to P[s][pos], pos
+// (the lane's crow entry, V.rows the stride of P) the row's place in the
+// cold copy.
+template <int THREADS, int UNR, class Op>
+__global__ void __launch_bounds__(THREADS, 1)
+    hub_pieces_kernel(SlabView V, const int4* __restrict__ ranges,
+                      const typename Op::ValT* __restrict__ hval,
+                      const typename Op::VecT* __restrict__ xhot, int H,
+                      typename Op::AccT* __restrict__ P, HubSplits hs, Op op) {
+    if (op.skip()) return;
+    using VecT = typename Op::VecT;
+    using AccT = typename Op::AccT;
+    extern __shared__ __align__(16) unsigned char hub_smem[];
+    __shared__ int next_chunk;
+    VecT* xs = reinterpret_cast<VecT*>(hub_smem);
+    const int4 c = ranges[blockIdx.x];  // {slab, first chunk, end chunk, -}
+    const int c0 = c.x * V.W;
+    slab_load_x<THREADS>(xs, xhot, c0, min(V.W, H - c0), V.W);
+    if (threadIdx.x == 0) next_chunk = c.y + THREADS / 32;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    AccT* __restrict__ Ps = P + (size_t)c.x * V.rows;
+    // the next chunk is taken, and its offsets and lane rows loaded, while
+    // this one runs: short chunks then cost no extra round trip
+    int ch = c.y + (int)(threadIdx.x >> 5);
+    int nbase = 0, nend = 0, nrow = -1;
+    if (ch < c.z) {
+        nbase = __ldg(V.cptr + ch);
+        nend = __ldg(V.cptr + ch + 1);
+        nrow = __ldg(V.crow + (size_t)ch * 32 + lane);
+    }
+    while (ch < c.z) {
+        const int row = nrow, base = nbase, width = (nend - nbase) >> 5;
+        int nx = 0;
+        if (lane == 0) nx = atomicAdd(&next_chunk, 1);
+        const int nch = __shfl_sync(0xffffffffu, nx, 0);
+        if (nch < c.z) {
+            nbase = __ldg(V.cptr + nch);
+            nend = __ldg(V.cptr + nch + 1);
+            nrow = __ldg(V.crow + (size_t)nch * 32 + lane);
+        }
+        const AccT acc = slab_lane_sum<UNR, false, AccT>(V, hval, xs, base, width, lane);
+        if (row >= 0) {
+            Ps[row] = acc;
+        } else if (row < -1) {
+            const int sp = -row - 2;
+            hs.part[sp] = (double)acc;
+            __threadfence();
+            const int lid = __ldg(hs.sub_split + sp);
+            const int4 q = hs.splits[lid];
+            if (atomicAdd(&hs.cnt[lid], 1u) == (unsigned)q.z - 1u) {
+                __threadfence();
+                AccT sum = AccT(0);
+                for (int j = 0; j < q.z; ++j) sum += AccT(__ldcg(&hs.part[q.y + j]));
+                P[(size_t)q.w * V.rows + q.x] = sum;
+                hs.cnt[lid] = 0u;
+            }
+        }
+        ch = nch;
     }
 }
 

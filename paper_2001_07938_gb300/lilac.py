@@ -31,12 +31,12 @@ LILAC_ERR_UNSUPPORTED = 10
 LILAC_F64, LILAC_F32 = 0, 1
 LILAC_MEM_HOST, LILAC_MEM_DEVICE = 0, 1
 LILAC_VARIANT_AUTO, LILAC_VARIANT_SCALAR, LILAC_VARIANT_VECTOR, LILAC_VARIANT_STAGED, \
-    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB, LILAC_VARIANT_JDS, LILAC_VARIANT_SELL = \
-    0, 1, 2, 3, 4, 5, 6, 7
+    LILAC_VARIANT_MERGE, LILAC_VARIANT_SLAB, LILAC_VARIANT_JDS, LILAC_VARIANT_SELL, \
+    LILAC_VARIANT_HUB = 0, 1, 2, 3, 4, 5, 6, 7, 8
 LILAC_CREATE_NO_TUNE = 0x1
 
 VARIANT_NAMES = {1: "scalar", 2: "vector", 3: "staged", 4: "merge", 5: "slab", 6: "jds",
-                 7: "sell"}
+                 7: "sell", 8: "hub"}
 
 # every symbol include/lilac.h declares (checked by the tests)
 EXPORTS = (

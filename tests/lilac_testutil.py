@@ -61,4 +61,4 @@ def true_rel_residual(A, b, x):
 # (variant, lanes per row); for SLAB and SELL the width is the STAGED width
 # they fall back to where their copy is not built
 ALL_VARIANTS = ([(1, 1)] + [(2, w) for w in (2, 4, 8, 16, 32)] + [(3, w) for w in (1, 2, 4, 8, 16, 32)]
-                + [(4, 1)] + [(5, 1), (5, 4)] + [(6, 1)] + [(7, 1), (7, 8)])
+                + [(4, 1)] + [(5, 1), (5, 4)] + [(6, 1)] + [(7, 1), (7, 8)] + [(8, 1)])

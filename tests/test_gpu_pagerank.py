@@ -58,6 +58,29 @@ def test_sell_split_epilogue_on_many_sorted_rows():
     np.testing.assert_allclose(l1, l1r, rtol=1e-4, atol=1e-6)
 
 
+@pytest.mark.parametrize("permute", [True, False])
+def test_hub_pagerank_matches_oracle_and_repeats(permute):
+    """PageRank on the HUB copies (hub gather, slab pieces, cold sliced ELL
+    adding the slab sums, row-order reduction), relabelled and unpermuted
+    R-MAT: within the FP32 tolerance of the oracle, bitwise run to run."""
+    torch = torch_cuda()
+    A = inputs.rmat_transposed(19, 8, seed=6, permute=permute)
+    xr, l1r = oracle.pagerank(A.row_ptr, A.col_ind, A.vals, iters=20)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_HUB, 1)
+    assert M.info()["active_variant"] == L.LILAC_VARIANT_HUB
+    xs = []
+    for _ in range(2):
+        x = torch.empty(A.n, dtype=torch.float32, device="cuda")
+        l1 = M.pagerank(x, iters=20)
+        torch.cuda.synchronize()
+        xs.append(host(x))
+    M.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    assert np.abs(xs[0].astype(np.float64) - xr).sum() <= 1e-5
+    np.testing.assert_allclose(l1, l1r, rtol=1e-4, atol=1e-6)
+
+
 def test_fp64_pagerank_matches_oracle_tightly():
     A = inputs.rmat_transposed(12, 8, seed=4)
     xr, l1r = oracle.pagerank(A.row_ptr, A.col_ind, A.vals.astype(np.float64), iters=30)

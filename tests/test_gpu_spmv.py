@@ -12,7 +12,7 @@ import pytest
 import oracle
 from paper_2001_07938_gb300 import inputs
 from paper_2001_07938_gb300 import lilac as L
-from lilac_testutil import ALL_VARIANTS, assert_spmv_close, dev, host, torch_cuda
+from lilac_testutil import ALL_VARIANTS, assert_spmv_close, dev, host, torch_cuda, true_rel_residual
 from conftest import load_golden
 
 pytestmark = pytest.mark.gpu
@@ -185,6 +185,82 @@ def test_slab_and_sell_padding_ignore_nonfinite_x_and_follow_updates(variant):
     assert M.info()["active_variant"] == variant
     assert_spmv_close(A2, x, _run(M, x, np.float64), False, f"variant {variant} after update")
     M.close()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_hub_variant_on_a_power_law_graph(dtype):
+    """HUB (the hub columns' x gathered per call and held in shared memory, in
+    slabs; the cold nonzeros as a sliced ELL copy that adds the slab sums) on
+    an R-MAT graph whose x exceeds 1 MB: built, within the oracle's bound,
+    bitwise the same on repeat, ignoring an inf in x where no nonzero reads
+    it, and following value updates.  A matrix with uniform random columns
+    gets no hub copy and runs STAGED."""
+    fp32 = dtype == np.float32
+    torch = torch_cuda()
+    A = inputs.rmat_transposed(19 if fp32 else 18, 8, seed=21).astype(dtype)
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_HUB, 1)
+    info = M.info()
+    assert info["active_variant"] == L.LILAC_VARIANT_HUB
+    assert info["spmv_kernels"] in (3, 4)
+    x = inputs.uniform(22, A.ncols, dtype=dtype)
+    y = _run(M, x, dtype)
+    assert_spmv_close(A, x.astype(np.float64), y, fp32, "hub")
+    np.testing.assert_array_equal(y, _run(M, x, dtype))
+    counts = np.bincount(A.col_ind, minlength=A.ncols)
+    empty = np.nonzero(counts == 0)[0]
+    if empty.size:
+        xi = x.copy()
+        xi[empty[:1000]] = np.inf
+        np.testing.assert_array_equal(_run(M, xi, dtype), y)
+    v2 = inputs.uniform(23, A.nnz, 0.0, 1.0, dtype=dtype)
+    L.lilac_csr_update_values(M.handle, v2.ctypes.data, L.LILAC_MEM_HOST)
+    torch.cuda.synchronize()
+    A2 = inputs.CSR(A.n, A.ncols, A.row_ptr, A.col_ind, v2)
+    assert_spmv_close(A2, x.astype(np.float64), _run(M, x, dtype), fp32, "hub after update")
+    M.close()
+    U = inputs.spd_random(200000, 4, 20.0, 5)
+    MU = L.CsrMatrix.from_csr(U, flags=L.LILAC_CREATE_NO_TUNE)
+    MU.set_variant(L.LILAC_VARIANT_HUB, 1)
+    assert MU.info()["active_variant"] == L.LILAC_VARIANT_STAGED
+    xu = inputs.uniform(24, U.ncols)
+    assert_spmv_close(U, xu, _run(MU, xu, np.float64), False, "hub not built")
+    MU.close()
+
+
+def test_hub_cg_on_a_symmetrised_power_law_matrix():
+    """FP64 CG on a HUB handle (the SpMV with the CG epilogue through the hub
+    slabs and the cold copy): converges like the oracle, bitwise run to run."""
+    import scipy.sparse as sp
+    G = inputs.rmat_transposed(18, 8, seed=31)
+    B = sp.csr_matrix((np.ones(G.nnz), G.col_ind, G.row_ptr), shape=(G.n, G.n))
+    S = (B + B.T).tocsr()
+    S.sum_duplicates()
+    S.setdiag(0)
+    S.eliminate_zeros()
+    d = np.asarray(abs(S).sum(axis=1)).ravel() + 1.0
+    S = (S + sp.diags(d)).tocsr()
+    S.sort_indices()
+    A = inputs.CSR(S.shape[0], S.shape[1], S.indptr.astype(np.int32), S.indices.astype(np.int32),
+                   S.data.astype(np.float64))
+    b = inputs.uniform(32, A.n)
+    torch = torch_cuda()
+    M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
+    M.set_variant(L.LILAC_VARIANT_HUB, 1)
+    assert M.info()["active_variant"] == L.LILAC_VARIANT_HUB
+    xs = []
+    for _ in range(2):
+        x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        st, info = M.cg(dev(b), x, rtol=1e-10, max_iter=3000)
+        torch.cuda.synchronize()
+        assert st == L.LILAC_OK
+        xs.append(host(x))
+    M.close()
+    np.testing.assert_array_equal(xs[0], xs[1])
+    _, itr, _ = oracle.cg(A.row_ptr, A.col_ind, A.vals, b, max_iter=3000, rtol=1e-10)
+    # ~600 iterations: rounding in another summation order moves the count a little
+    assert abs(info.iters - itr) <= max(2, itr // 50)
+    assert true_rel_residual(A, b, xs[0]) <= 1e-10
 
 
 def test_slab_fp32_values_and_vectors():
