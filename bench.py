@@ -660,6 +660,10 @@ class SpMM8(Workload):
         return {"max_rel_diff_vs_spmv_column": d,
                 "k_single_spmv_ms": e0.elapsed_time(e1) / 5}
 
+    def roofline_alu(self):
+        # one FP64 FMA per nonzero and vector: the FP64 pipe, not DRAM, bounds it
+        return 2.0 * self.A.nnz * self.k, f"FP64 FMA per nonzero and vector ({self.k} vectors)"
+
     def roofline_sample(self, k):
         torch = self.torch
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -872,18 +876,27 @@ def run_marshal(args):
 
 
 def run_served(args):
+    """The served stream against the plain system (one request at a time,
+    lilac_spmv / FP64 lilac_cg, matrices resident), both with the same
+    tuning policy.  The server is created once; a first pass at saturation
+    uploads the pool (as the plain system's handles are created before it is
+    timed), then one saturated pass and one Poisson pass per load point are
+    timed.  Plain latencies under the same arrivals follow exactly from its
+    measured service times (FIFO, one server)."""
     import torch
     from paper_2001_07938_gb300 import build as lbuild
     from paper_2001_07938_gb300 import lilac as L
     torch.cuda.set_device(0)
     lbuild.build()
     L.load()
-    pool, reqs = served_stream(n_req=args.served_requests)
+    pool, reqs = served_stream(n_req=args.served_requests, n_mats=args.served_mats,
+                               n_hi=args.served_nmax, kmax=args.served_kmax)
     N = len(reqs)
     n_cg = sum(1 for r in reqs if r[0] == "cg")
     n_mixed = sum(1 for r in reqs if r[0] == "cg" and r[4] == 2)
-    # plain: one request at a time through lilac_spmv / lilac_cg (FP64), matrices resident
-    Ms = [L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE) for A in pool]
+    pool_bytes = sum(A.nnz * 12 + (A.n + 1) * 4 for A in pool)
+    flags = 0 if args.served_tune else L.LILAC_CREATE_NO_TUNE
+    Ms = [L.CsrMatrix.from_csr(A, flags=flags) for A in pool]
     outs_plain = []
 
     def plain_one(r):
@@ -910,24 +923,23 @@ def run_served(args):
     for M in Ms:
         M.close()
     cap = N / plain_makespan
-    lam = args.served_load * cap
-    rng = np.random.default_rng(1)
-    arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
-    fin, lat_plain = 0.0, []
-    for a, sv in zip(arrivals, service):  # FIFO single server, exact from service times
-        fin = max(fin, a) + sv
-        lat_plain.append(fin - a)
+
+    S = L.Server(hbm_budget_bytes=int(args.served_budget_gb * 2 ** 30),
+                 iters_per_round=args.served_round, tune=args.served_tune)
+    ids = [S.add_matrix(A) for A in pool]
 
     def serve(timed_arrivals):
-        S = L.Server(iters_per_round=args.served_round)
-        ids = [S.add_matrix(A) for A in pool]
         outs = [None] * N
-        lat = [0.0] * N
+        lat, wait, svc, rounds = [0.0] * N, [0.0] * N, [0.0] * N, [0] * N
         got = 0
         t0 = L.Server.now()
+        st0 = S.stats()
         i = 0
+        last_progress = L.Server.now()
         while got < N:
             now = L.Server.now() - t0
+            if L.Server.now() - last_progress > 300.0:
+                raise RuntimeError(f"served stream stalled: {S.stats()}")
             while i < N and (timed_arrivals is None or timed_arrivals[i] <= now):
                 kind, mi, inp, k, prec = reqs[i]
                 A = pool[mi]
@@ -942,23 +954,66 @@ def run_served(args):
             pending = S.step()
             for c in S.poll():
                 # latency from the scheduled arrival when arrivals are timed
-                a = c["arrival"] if timed_arrivals is None else t0 + timed_arrivals[c["tag"]]
-                lat[c["tag"]] = c["finish"] - a
+                tag = c["tag"]
+                a = c["arrival"] if timed_arrivals is None else t0 + timed_arrivals[tag]
+                lat[tag] = c["finish"] - a
+                wait[tag] = c["admitted"] - a
+                svc[tag] = c["finish"] - c["admitted"]
+                rounds[tag] = c["rounds"]
+                if c["status"] != L.LILAC_OK:
+                    raise RuntimeError(f"request {tag} failed: {c}")
                 got += 1
+                last_progress = L.Server.now()
             if pending == 0 and i < N and timed_arrivals is not None:
                 time.sleep(max(0.0, min(0.01, timed_arrivals[i] - (L.Server.now() - t0))))
         makespan = L.Server.now() - t0
-        st = S.stats()
-        S.close()
-        return outs, lat, makespan, st
+        st1 = S.stats()
+        delta = {k: st1[k] - st0[k] for k in ("rounds", "uploads", "evictions", "budget_waits")}
+        return outs, lat, wait, svc, rounds, makespan, delta
 
-    serve(None)  # warm-up: graph capture, pool blocks
-    outs_s, _, served_makespan, st_sat = serve(None)
-    _, lat_served, _, st_poisson = serve(arrivals)
-    # agreement of the two systems (library only): relative max difference
+    def pct(v, q):
+        return 1000.0 * float(np.percentile(v, q))
+
+    def breakdown(lat, wait, svc, rounds):
+        """Mean queue wait / service / rounds of the requests at or above the
+        99th latency percentile, by kind."""
+        p99 = np.percentile(lat, 99)
+        top = [t for t in range(N) if lat[t] >= p99]
+        kinds = {}
+        for name in ("spmv", "cg"):
+            ts = [t for t in top if reqs[t][0] == name]
+            if ts:
+                kinds[name] = {"count": len(ts),
+                               "queue_wait_ms": 1000 * float(np.mean([wait[t] for t in ts])),
+                               "service_ms": 1000 * float(np.mean([svc[t] for t in ts])),
+                               "rounds": float(np.mean([rounds[t] for t in ts])),
+                               "n": float(np.mean([pool[reqs[t][1]].n for t in ts]))}
+        return kinds
+
+    serve(None)  # warm-up: uploads, graph capture, pool blocks
+    outs_s, _, _, _, _, served_makespan, sat_delta = serve(None)
     diff = max(float(np.max(np.abs(a - b)) / max(1e-300, float(np.max(np.abs(b)))))
                for a, b in zip(outs_s, outs_plain))
     value = N / served_makespan
+    loads = []
+    for load in [float(v) for v in args.served_loads.split(",")]:
+        lam = load * cap
+        rng = np.random.default_rng(1)
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+        fin, lat_plain = 0.0, []
+        for a, sv in zip(arrivals, service):  # FIFO single server, exact from service times
+            fin = max(fin, a) + sv
+            lat_plain.append(fin - a)
+        _, lat, wait, svc, rounds, mk, delta = serve(arrivals)
+        loads.append({"load": load, "arrival_rate_per_s": lam,
+                      "served": {"latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                                 "queue_wait_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)},
+                                 "p99_breakdown": breakdown(lat, wait, svc, rounds),
+                                 "makespan_s": mk, **delta},
+                      "plain": {"latency_ms": {"p50": pct(lat_plain, 50),
+                                               "p99": pct(lat_plain, 99)}}})
+    st = S.stats()
+    S.close()
     line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": served_makespan * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -966,20 +1021,17 @@ def run_served(args):
             "config": {"workload": "served_stream", "requests": N, "cg_requests": n_cg,
                        "cg_mixed_precision_requests": n_mixed,
                        "plain": "one request at a time, lilac_spmv / FP64 lilac_cg",
-                       "matrices": len(pool), "n_range": [1e3, 2e5], "zipf": 1.1,
-                       "spmv_vectors": "1..8", "rtol": 1e-10,
-                       "arrivals": f"Poisson at {args.served_load} x plain capacity",
-                       "iters_per_round": args.served_round,
-                       "note": "scaled-down stream (10,000 requests, n up to 2e6 in the full recipe)"},
+                       "matrices": len(pool), "pool_matrix_bytes": pool_bytes,
+                       "n_range": [1e3, args.served_nmax], "zipf": 1.1,
+                       "spmv_vectors": f"1..{args.served_kmax}", "rtol": 1e-10,
+                       "hbm_budget_gb": args.served_budget_gb, "tuned": bool(args.served_tune),
+                       "iters_per_round": args.served_round},
             "served": {"requests_per_s": value, "cg_solves_per_s": n_cg / served_makespan,
-                       "latency_ms": {"p50": 1000 * float(np.percentile(lat_served, 50)),
-                                      "p99": 1000 * float(np.percentile(lat_served, 99))},
-                       "rounds": st_sat["rounds"], "uploads": st_sat["uploads"]},
-            "plain": {"requests_per_s": cap, "cg_solves_per_s": n_cg / plain_makespan,
-                      "latency_ms": {"p50": 1000 * float(np.percentile(lat_plain, 50)),
-                                     "p99": 1000 * float(np.percentile(lat_plain, 99))}},
+                       "saturated": sat_delta, "resident_bytes_end": st["resident_bytes"]},
+            "plain": {"requests_per_s": cap, "cg_solves_per_s": n_cg / plain_makespan},
             "served_vs_plain_throughput": value / cap,
             "max_rel_diff_served_vs_plain": diff,
+            "loads": loads,
             "roofline": None, "cpu_baseline": None,
             "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0, "note": "requests carry host buffers end to end"}}
@@ -1254,8 +1306,15 @@ def main():
                     help="R-MAT scale of the pagerank22 workload (22 is the benchmark size)")
     ap.add_argument("--ir-precision", type=int, choices=[1, 2], default=2,
                     help="mixed-precision CG of the ir192 workload")
-    ap.add_argument("--served-requests", type=int, default=2000)
-    ap.add_argument("--served-load", type=float, default=0.8)
+    ap.add_argument("--served-requests", type=int, default=2000,
+                    help="served stream: requests (the full recipe: 10000)")
+    ap.add_argument("--served-mats", type=int, default=32, help="matrices in the pool (full: 256)")
+    ap.add_argument("--served-nmax", type=float, default=2e5, help="largest n (full: 2e6)")
+    ap.add_argument("--served-kmax", type=int, default=8, help="vectors per SpMV (full: 32)")
+    ap.add_argument("--served-loads", default="0.8",
+                    help="arrival rates as fractions of the plain capacity (full: 0.5,0.8,0.95)")
+    ap.add_argument("--served-budget-gb", type=float, default=120.0)
+    ap.add_argument("--served-tune", type=int, default=0, help="1: timed tuning at upload")
     ap.add_argument("--served-round", type=int, default=16)
     ap.add_argument("--variant", default="",
                     help="force the SpMV kernel instead of the tuner's choice, e.g. slab:4")

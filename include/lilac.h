@@ -484,8 +484,10 @@ lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
  * loop.  Each step admits queued requests in arrival order while the budget
  * and the active limit allow (uploading a matrix on first use and evicting
  * the least recently used idle matrix when memory is needed), runs every
- * admitted SpMV request in one batched launch, advances every active CG solve
- * by iters_per_round iterations in one captured graph, and retires finished
+ * admitted single-vector SpMV request in one batched launch and every SpMV
+ * request of 2 to 32 vectors through the multi-vector kernel (each nonzero
+ * streamed once for all its vectors), advances every active CG solve by
+ * iters_per_round iterations in one captured graph, and retires finished
  * requests (result copied to the caller's host buffer).  A request's result
  * is bitwise the same whatever else is in flight.
  */
@@ -495,7 +497,8 @@ typedef struct {
     int64_t hbm_budget_bytes; /* resident matrices + request workspaces (default 120 GiB) */
     int32_t max_active;       /* requests in flight at most (default 256) */
     int32_t iters_per_round;  /* CG iterations per step (default 16) */
-    int32_t pad;
+    int32_t tune;             /* 1: time the SpMV variants of a matrix at its first upload (the
+                                 autotuner of lilac_csr_create); 0 (default): row statistics */
 } lilac_server_opts;
 
 typedef enum { LILAC_REQ_SPMV = 0, LILAC_REQ_CG = 1 } lilac_req_kind;
@@ -521,6 +524,9 @@ typedef struct {
     double rel_res;    /* CG recursive ||r|| / ||b|| */
     double arrival;    /* lilac_server_now() at submit */
     double finish;     /* lilac_server_now() at retirement */
+    double admitted;   /* lilac_server_now() when it left the queue (workspace granted) */
+    int32_t rounds;    /* server steps it took part in */
+    int32_t pad;
 } lilac_completion;
 
 typedef struct {

@@ -40,7 +40,9 @@ struct BatchEngine {
     lilac_status ensure(int nprobs, int64_t nspmv, int64_t nvec);
     // Set the active problems (descriptors and work lists); synchronizes s.
     lilac_status upload(const std::vector<BatchProb>& probs, cudaStream_t s);
-    int grid_for(int64_t items) const;
+    int g_spmv = 0, g_vec = 0;  // resident CTAs of the two kernels (0: not yet queried)
+    void resident_grids();
+    int grid_for(int64_t items, bool spmv);
     lilac_status spmv_phase(cudaStream_t s);
     lilac_status cg_start(cudaStream_t s);
     lilac_status enqueue_rounds(int R, cudaStream_t s, int g1, int g2);

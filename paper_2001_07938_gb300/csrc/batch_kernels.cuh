@@ -29,7 +29,11 @@ enum BatchLayout : int { BL_TILES = 0, BL_SELL = 1 };
 constexpr int kBatchThreads = 256;
 constexpr int kBatchItems = 2048;   // nonzeros per tile: matches the STAGED tile list
 constexpr int kBatchRows = 1024;    // rows per tile: matches the STAGED tile list
-constexpr int kBatchChunk = 4096;   // vector elements per chunk item
+#ifndef LILAC_BATCH_SPMV_CTAS
+#define LILAC_BATCH_SPMV_CTAS 4
+#endif
+constexpr int kBatchSpmvCtasPerSm = LILAC_BATCH_SPMV_CTAS;  // register bound of the SpMV-phase kernel
+constexpr int kBatchChunk = 1024;   // vector elements per chunk item (4 per thread)
 constexpr int kBatchSellChunks = kBatchThreads / 32;  // SELL chunks per item (one per warp)
 
 struct BatchProb {
@@ -91,13 +95,28 @@ struct BatchItem {
     int idx;
 };
 
-// Item-order sum of a problem's partials (stride apart) + split-row sums.
-__device__ __forceinline__ double batch_sum_parts(const double* part, int n, int stride,
-                                                  const double* extra, int nextra) {
-    double s = 0.0;
-    for (int i = 0; i < n; ++i) s += __ldcg(part + (size_t)i * stride);
-    for (int i = 0; i < nextra; ++i) s += __ldcg(extra + (size_t)i * kMaxRed);
-    return s;
+// Sum of a problem's NR-wide partials (item i at part + i * stride) and its
+// split-row sums (extra + i * kMaxRed), by the whole block of the item that
+// arrived last: thread t adds items t, t + THREADS, ... in order, then the
+// block's fixed tree -- an order set by the problem's item count alone, so a
+// problem's sums do not depend on the other problems of the batch.  The
+// result is valid in thread 0.
+template <int NR, int THREADS>
+__device__ __forceinline__ void batch_sum_parts(const double* part, int n, int stride,
+                                                const double* extra, int nextra,
+                                                double (&out)[NR], double* sh) {
+    double acc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) acc[q] = 0.0;
+    for (int i = threadIdx.x; i < n; i += THREADS) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += __ldcg(part + (size_t)i * stride + q);
+    }
+    for (int i = threadIdx.x; i < nextra; i += THREADS) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) acc[q] += __ldcg(extra + (size_t)i * kMaxRed + q);
+    }
+    block_sum<NR, THREADS>(acc, out, sh);
 }
 
 __device__ __forceinline__ bool batch_ru_due(const CgState* st) {
@@ -131,9 +150,31 @@ struct BEpiResid {  // r32 = float(b - A x), ||b - A x||^2, float(r).float(r)
     }
 };
 
-// One tile of one problem: products to shared memory, rows by groups of V
-// lanes; a chunk of a split row is summed by the block and finished by the
-// chunk that arrives last.  Returns the tile's FP64 sums in red[0..1].
+// Rows of a staged tile by groups of V lanes: lane l of a group adds
+// elements l, l + V, ... of its row (one FMA each), then the group's tree.
+template <int V, class AccT, class Epi>
+__device__ __forceinline__ void batch_tile_rows(const TileDesc& t, int nrows, const AccT* vs,
+                                                const AccT* xs, const int* rp_s, const Epi& epi,
+                                                double* red) {
+    constexpr int NGROUPS = kBatchThreads / V;
+    const int tid = threadIdx.x;
+    const int lane = tid & (V - 1), group = tid / V;
+    const unsigned mask = group_mask<V>(tid);
+    for (int rr = group; rr < nrows; rr += NGROUPS) {
+        const int kb = rp_s[rr] - t.k0, ke = rp_s[rr + 1] - t.k0;
+        AccT sum = AccT(0);
+        for (int k = kb + lane; k < ke; k += V) sum = fma(vs[k], xs[k], sum);
+        sum = group_sum<V>(sum, mask);
+        if (lane == 0) epi.row(t.r0 + rr, sum, red);
+    }
+}
+
+// One tile of one problem: its values and gathered x to shared memory (one
+// coalesced pass), then rows by groups of V lanes -- 4 for short rows, 16
+// when the tile's rows average 48 elements or more, so that every lane has
+// a few elements of a row -- with one FMA per element; a chunk of a split
+// row is summed by the block and finished by the chunk that arrives last.
+// Returns the tile's FP64 sums in red[0..1].
 template <class ValT, class VecT, class AccT, class Epi>
 __device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t,
                                            const ValT* __restrict__ val,
@@ -142,12 +183,9 @@ __device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t
                                            AccT* sh) {
     constexpr int THREADS = kBatchThreads;
     constexpr int IPT = kBatchItems / THREADS;
-    constexpr int V = 4;
-    constexpr int NGROUPS = THREADS / V;
-    AccT* prod = reinterpret_cast<AccT*>(smem);
+    AccT* vs = reinterpret_cast<AccT*>(smem);
+    AccT* xs = vs + kBatchItems;
     const int tid = threadIdx.x;
-    const int lane = tid & (V - 1), group = tid / V;
-    const unsigned mask = group_mask<V>(tid);
     int cj[IPT];
     ValT vj[IPT];
 #pragma unroll
@@ -159,23 +197,23 @@ __device__ __forceinline__ void batch_tile(const BatchProb& P, const TileDesc& t
 #pragma unroll
     for (int j = 0; j < IPT; ++j) {
         const int k = t.k0 + j * THREADS + tid;
-        if (k < t.k1) prod[j * THREADS + tid] = AccT(vj[j]) * AccT(__ldg(xin + cj[j]));
+        if (k < t.k1) {
+            vs[j * THREADS + tid] = AccT(vj[j]);
+            xs[j * THREADS + tid] = AccT(__ldg(xin + cj[j]));
+        }
     }
     if (t.r1 >= 0) {
         const int nrows = t.r1 - t.r0;
         for (int q = tid; q <= nrows; q += THREADS) rp_s[q] = __ldg(P.row_ptr + t.r0 + q);
         __syncthreads();
-        for (int rr = group; rr < nrows; rr += NGROUPS) {
-            const int kb = rp_s[rr] - t.k0, ke = rp_s[rr + 1] - t.k0;
-            AccT sum = AccT(0);
-            for (int k = kb + lane; k < ke; k += V) sum += prod[k];
-            sum = group_sum<V>(sum, mask);
-            if (lane == 0) epi.row(t.r0 + rr, sum, red);
-        }
+        if (t.k1 - t.k0 >= 48 * nrows)  // uniform over the block
+            batch_tile_rows<16>(t, nrows, vs, xs, rp_s, epi, red);
+        else
+            batch_tile_rows<4>(t, nrows, vs, xs, rp_s, epi, red);
     } else {
         __syncthreads();
         AccT sum = AccT(0);
-        for (int k = tid; k < t.k1 - t.k0; k += THREADS) sum += prod[k];
+        for (int k = tid; k < t.k1 - t.k0; k += THREADS) sum = fma(vs[k], xs[k], sum);
         sum = block_sum_lead<THREADS, AccT>(sum, sh);
         if (tid == 0) {
             const int lid = t.r0, slot = -t.r1 - 1;
@@ -273,9 +311,9 @@ __device__ __forceinline__ void batch_item(const BatchProb& P, int idx, const Va
         batch_tile<ValT, VecT, AccT>(P, P.tiles[idx], val, xin, epi, red, smem, rp_s, sh);
 }
 
-// Problem-level ends of the SpMV phases (last tile of the problem, thread 0).
-__device__ __forceinline__ void batch_finish_pq(const BatchProb& P) {
-    const double pq = batch_sum_parts(P.part, P.ntiles, 2, P.long_red, P.nlong);
+// Problem-level ends of the SpMV phases (last tile of the problem, thread 0,
+// given the problem's sums).
+__device__ __forceinline__ void batch_finish_pq(const BatchProb& P, double pq) {
     CgState* st = P.st;
     st->pq = pq;
     if (!(pq > 0.0) || !isfinite(pq)) {
@@ -286,9 +324,7 @@ __device__ __forceinline__ void batch_finish_pq(const BatchProb& P) {
     }
 }
 
-__device__ __forceinline__ void batch_finish_resid(const BatchProb& P) {
-    const double rr_true = batch_sum_parts(P.part, P.ntiles, 2, P.long_red, P.nlong);
-    const double rr32 = batch_sum_parts(P.part + 1, P.ntiles, 2, P.long_red + 1, P.nlong);
+__device__ __forceinline__ void batch_finish_resid(const BatchProb& P, double rr_true, double rr32) {
     CgState* st = P.st;
     st->true_rr = rr_true;
     st->updates += 1;
@@ -310,15 +346,16 @@ __device__ __forceinline__ void batch_finish_resid(const BatchProb& P) {
 // in the problem's precision).  MODE 1: the FP64 residual of BP_F32_RU
 // problems whose replacement is due (other items return at once).
 template <int MODE>
-static __global__ void __launch_bounds__(kBatchThreads)
+static __global__ void __launch_bounds__(kBatchThreads, kBatchSpmvCtasPerSm)
     batch_spmv_kernel(const BatchProb* __restrict__ probs, const BatchItem* __restrict__ items,
                       const int* __restrict__ nitems_dev) {
     constexpr int THREADS = kBatchThreads;
-    __shared__ __align__(16) unsigned char smem[kBatchItems * sizeof(double)];
+    __shared__ __align__(16) unsigned char smem[2 * kBatchItems * sizeof(double)];
     __shared__ int rp_s[kBatchRows + 2];
     __shared__ double sh[32];
     __shared__ float shf[32];
     __shared__ double shr[kMaxRed * 32];
+    __shared__ int last;
     const int tid = threadIdx.x;
     const int nitems = *nitems_dev;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -365,12 +402,18 @@ static __global__ void __launch_bounds__(kBatchThreads)
                 P.part[2 * item.idx] = tot[0];
                 P.part[2 * item.idx + 1] = tot[1];
                 __threadfence();
-                if (atomicAdd(&P.cnt[0], 1u) == (unsigned)P.ntiles - 1u) {
-                    __threadfence();
+                last = atomicAdd(&P.cnt[0], 1u) == (unsigned)P.ntiles - 1u;
+            }
+            __syncthreads();
+            if (last) {  // uniform over the block
+                __threadfence();
+                double sums[2];
+                batch_sum_parts<2, THREADS>(P.part, P.ntiles, 2, P.long_red, P.nlong, sums, shr);
+                if (tid == 0) {
                     if (MODE == 0)
-                        batch_finish_pq(P);
+                        batch_finish_pq(P, sums[0]);
                     else
-                        batch_finish_resid(P);
+                        batch_finish_resid(P, sums[0], sums[1]);
                     P.cnt[0] = 0u;
                 }
             }
@@ -391,6 +434,7 @@ static __global__ void __launch_bounds__(kBatchThreads)
                      const int* __restrict__ nitems_dev) {
     constexpr int THREADS = kBatchThreads;
     __shared__ double shr[kMaxRed * 32];
+    __shared__ int last;
     const int tid = threadIdx.x;
     const int nitems = *nitems_dev;
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
@@ -455,13 +499,19 @@ static __global__ void __launch_bounds__(kBatchThreads)
         }
         double r1[1] = {red}, tot[1];
         block_sum<1, THREADS>(r1, tot, shr);
+        double* vpart = P.part + 2 * (size_t)P.ntiles;
         if (tid == 0) {
-            double* vpart = P.part + 2 * (size_t)P.ntiles;
             vpart[item.idx] = tot[0];
             __threadfence();
-            if (atomicAdd(&P.cnt[1], 1u) == (unsigned)P.nchunks - 1u) {
-                __threadfence();
-                const double s = batch_sum_parts(vpart, P.nchunks, 1, nullptr, 0);
+            last = atomicAdd(&P.cnt[1], 1u) == (unsigned)P.nchunks - 1u;
+        }
+        __syncthreads();
+        if (last) {  // uniform over the block
+            __threadfence();
+            double sum[1];
+            batch_sum_parts<1, THREADS>(vpart, P.nchunks, 1, nullptr, 0, sum, shr);
+            if (tid == 0) {
+                const double s = sum[0];
                 if (PHASE == 0) {
                     st->rr = s;
                     st->bb = s;

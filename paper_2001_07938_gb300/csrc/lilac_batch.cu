@@ -183,13 +183,30 @@ lilac_status BatchEngine::upload(const std::vector<BatchProb>& probs, cudaStream
     return LILAC_OK;
 }
 
-int BatchEngine::grid_for(int64_t items) const {
-    return (int)std::max<int64_t>(1, std::min<int64_t>(items, (int64_t)sm_count * 8));
+// Resident CTAs of the SpMV-phase and vector-phase kernels on the device:
+// the grids of their grid-stride loops.
+void BatchEngine::resident_grids() {
+    if (g_spmv > 0) return;
+    int a = 0, b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batch_spmv_kernel<0>, kBatchThreads, 0) !=
+            cudaSuccess || a < 1)
+        a = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batch_vec_kernel<1>, kBatchThreads, 0) !=
+            cudaSuccess || b < 1)
+        b = 1;
+    (void)cudaGetLastError();
+    g_spmv = sm_count * a;
+    g_vec = sm_count * b;
+}
+
+int BatchEngine::grid_for(int64_t items, bool spmv) {
+    resident_grids();
+    return (int)std::max<int64_t>(1, std::min<int64_t>(items, spmv ? g_spmv : g_vec));
 }
 
 lilac_status BatchEngine::spmv_phase(cudaStream_t s) {
     if (host_counts[0] == 0) return LILAC_OK;
-    batch_spmv_kernel<0><<<grid_for(host_counts[0]), kBatchThreads, 0, s>>>(
+    batch_spmv_kernel<0><<<grid_for(host_counts[0], true), kBatchThreads, 0, s>>>(
         probs_d.as<BatchProb>(), items_spmv_d.as<BatchItem>(), counts_d.as<int>());
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -197,7 +214,7 @@ lilac_status BatchEngine::spmv_phase(cudaStream_t s) {
 
 lilac_status BatchEngine::cg_start(cudaStream_t s) {
     if (host_counts[1] == 0) return LILAC_OK;
-    batch_vec_kernel<0><<<grid_for(host_counts[1]), kBatchThreads, 0, s>>>(
+    batch_vec_kernel<0><<<grid_for(host_counts[1], false), kBatchThreads, 0, s>>>(
         probs_d.as<BatchProb>(), items_vec_d.as<BatchItem>(), counts_d.as<int>() + 1);
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -230,15 +247,15 @@ lilac_status BatchEngine::enqueue_rounds(int R, cudaStream_t s, int g1, int g2) 
 
 lilac_status BatchEngine::cg_rounds(int R, cudaStream_t s) {
     if (host_counts[1] == 0) return LILAC_OK;
-    // persistent grids: the full machine, independent of the current counts
-    const int g = sm_count * 8;
+    // persistent grids: the resident CTAs, independent of the current counts
+    resident_grids();
     const uint64_t key = ((uint64_t)R << 33) ^ ((uint64_t)mixed << 32) ^ gen;
     auto it = graphs.find(key);
     if (it == graphs.end()) {
         if (!capture_stream)
             LILAC_CUDA_TRY(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
         LILAC_CUDA_TRY(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
-        lilac_status st = enqueue_rounds(R, capture_stream, g, g);
+        lilac_status st = enqueue_rounds(R, capture_stream, g_spmv, g_vec);
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(capture_stream, &graph);
         if (st != LILAC_OK) {
@@ -408,7 +425,8 @@ extern "C" lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac
         if (r == R)
             LILAC_TRY(B->eng.cg_rounds(R, s));
         else
-            LILAC_TRY(B->eng.enqueue_rounds(r, s, B->eng.sm_count * 8, B->eng.sm_count * 8));
+            LILAC_TRY(B->eng.enqueue_rounds(r, s, B->eng.grid_for(B->eng.host_counts[0], true),
+                                            B->eng.grid_for(B->eng.host_counts[1], false)));
         done_iters += r;
         all_done = true;
         for (int i = 0; i < count; ++i)

@@ -47,7 +47,14 @@ static lilac_status ensure_cg_work(lilac_csr A, CgWork& W, bool f32) {
     return LILAC_OK;
 }
 
-enum GraphKind { G_CG64_FIXED = 1, G_CG64_CHUNK = 2, G_CG32_CHUNK = 3, G_CGRU_CHUNK = 4 };
+enum GraphKind {
+    G_CG64_FIXED = 1,
+    G_CG64_CHUNK = 2,
+    G_CG32_CHUNK = 3,
+    G_CGRU_CHUNK = 4,
+    G_SOLO64 = 5,  // a solve on caller-held memory (the server's lane for large matrices)
+    G_SOLORU = 6
+};
 
 // Profiling of the SpMV launches (opts->profile): event pairs recorded on the
 // launching stream around every SpMV, also inside captured graphs.
@@ -121,6 +128,22 @@ static int iter_kernels(lilac_csr A, const V* val) {
     return 2 + spmv_launch_count<OpCgPq<V, T>>(A, val);
 }
 
+// What FP64 CG on the handle's values needs before its first (captured)
+// iteration: the SpMV's scratch and, for the SLAB CG form, the step kernel's
+// barrier counters and r.r partials.
+static lilac_status prepare_cg64(lilac_csr A, cudaStream_t s) {
+    LILAC_TRY(prepare_spmv<OpCgPq<double, double>>(A));
+    if (slab_cg_active(A, A->val.as<double>())) {
+        LILAC_TRY(prepare_slab_cg(A));
+        const size_t need = 4 * sizeof(unsigned) + sizeof(double) * (size_t)A->sm_count;
+        if (!A->cg_step.p || A->cg_step.bytes < need) {
+            LILAC_TRY(A->ws_alloc(A->cg_step, need));
+            LILAC_CUDA_TRY(cudaMemsetAsync(A->cg_step.p, 0, A->cg_step.bytes, s));
+        }
+    }
+    return LILAC_OK;
+}
+
 // Run CG iterations until the device says done: either one graph of
 // max_iter iterations (no tolerance) or graphs of `chunk` iterations with a
 // host check in between.  `start` enqueues the start of the solve.
@@ -130,16 +153,8 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
                                 int kind_chunk, const void* key_b, Start&& start, cudaStream_t s,
                                 CgState* host_state, Prof& prof) {
     LILAC_TRY(prepare_spmv<OpCgPq<V, T>>(A));
-    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value) {
-        if (slab_cg_active(A, val)) {
-            LILAC_TRY(prepare_slab_cg(A));
-            const size_t need = 4 * sizeof(unsigned) + sizeof(double) * (size_t)A->sm_count;
-            if (!A->cg_step.p || A->cg_step.bytes < need) {
-                LILAC_TRY(A->ws_alloc(A->cg_step, need));
-                LILAC_CUDA_TRY(cudaMemsetAsync(A->cg_step.p, 0, A->cg_step.bytes, s));
-            }
-        }
-    }
+    if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
+        if (val == A->val.as<double>()) LILAC_TRY(prepare_cg64(A, s));
     const uint64_t pflag = prof.on ? 1 : 0;
     if (!has_tol) {
         if (prof.on) LILAC_TRY(ensure_prof_events(A, max_iter));
@@ -400,6 +415,93 @@ static lilac_status cg_mixed_ru(lilac_csr A, const double* b, double* x, const l
     if (A->dtype == LILAC_F64)
         return cg_mixed_ru_impl<double>(A, A->val.as<double>(), b, x, o, s, hs, info, prof);
     return cg_mixed_ru_impl<float>(A, A->val.as<float>(), b, x, o, s, hs, info, prof);
+}
+
+// --- one solve on caller-held memory ----------------------------------------
+// The request server's lane for large matrices: the iterations of lilac_cg
+// (FP64, or FP32 CG with FP64 reliable updates) with the handle's tuned
+// kernels, R at a time, on vectors and state the caller owns, so that several
+// solves may share one handle (run them on one stream: they share its SpMV
+// scratch).
+
+static size_t al256(size_t b) { return (b + 255) & ~size_t(255); }
+
+size_t solo_cg_bytes(const lilac_csr_s* A, int prec) {
+    const size_t n = (size_t)std::max(1, A->rows);
+    if (prec == 0) return 3 * al256(8 * n) + al256(sizeof(CgState));
+    // FP32 r, p, q and correction d; the FP64 residual
+    return 4 * al256(4 * n) + al256(sizeof(CgState)) + al256(8 * n);
+}
+
+void solo_cg_bind(const lilac_csr_s* A, int prec, void* ws, SoloCg& c) {
+    const size_t n = (size_t)std::max(1, A->rows);
+    const size_t vb = al256((prec == 0 ? 8 : 4) * n);
+    unsigned char* w = static_cast<unsigned char*>(ws);
+    c.prec = prec;
+    c.W.n = A->rows;
+    c.W.f32 = prec != 0;
+    c.W.r = DevBuf{w, vb};
+    c.W.p = DevBuf{w + vb, vb};
+    c.W.q = DevBuf{w + 2 * vb, vb};
+    c.W.state = DevBuf{w + 3 * vb, sizeof(CgState)};
+    w += 3 * vb + al256(sizeof(CgState));
+    c.d = nullptr;
+    c.r64 = nullptr;
+    if (prec != 0) {
+        c.d = reinterpret_cast<float*>(w);
+        c.r64 = reinterpret_cast<double*>(w + vb);
+    }
+}
+
+lilac_status solo_cg_prepare(lilac_csr A, int prec, cudaStream_t s) {
+    if (A->dtype != LILAC_F64 || A->rows != A->ncols) {
+        set_last_error("solve lane: square FP64 matrices only");
+        return LILAC_ERR_INVALID_ARG;
+    }
+    if (prec == 0) return prepare_cg64(A, s);
+    LILAC_TRY(make_val32(A, s));
+    LILAC_TRY(prepare_spmv<OpResidual<double, RES_OUTER>>(A));
+    LILAC_TRY(prepare_spmv<OpResidualRU<double>>(A));
+    LILAC_TRY(prepare_spmv<OpCgPq<float, float>>(A));
+    return LILAC_OK;
+}
+
+lilac_status solo_cg_start(lilac_csr A, SoloCg& c, const double* b, double* x, double rtol,
+                           int max_iter, double delta, cudaStream_t s) {
+    const int n = A->rows;
+    CgState* st = c.W.state.as<CgState>();
+    cg_state_reset_kernel<<<1, 1, 0, s>>>(st, max_iter);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    if (c.prec == 0) {
+        cg_start_zero_kernel<double, double><<<vec_grid(A, n), kVecThreads, 0, s>>>(
+            n, b, 1.0, x, c.W.r.as<double>(), c.W.p.as<double>(), FinCgStart<double>{st, rtol},
+            A->scratch());
+    } else {
+        LILAC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
+        OpResidual<double, RES_OUTER> op{c.r64, nullptr, b, st, rtol};
+        LILAC_TRY(launch_spmv(A, A->val.as<double>(), x, op, s));
+        ru_start_kernel<<<vec_grid(A, n), kVecThreads, 0, s>>>(
+            n, c.r64, c.W.r.as<float>(), c.W.p.as<float>(), c.d, FinRuStart{st, delta * delta},
+            A->scratch());
+    }
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
+lilac_status solo_cg_iters(lilac_csr A, SoloCg& c, const double* b, double* x, int nit,
+                           cudaStream_t s) {
+    const double* val = A->val.as<double>();
+    if (c.prec == 0) {
+        GraphKey key{G_SOLO64, c.W.state.p, x, nit, 0, A->variant, A->vwidth, A->ws_gen};
+        return run_maybe_graph(A, key, true, s, [&](cudaStream_t cs) {
+            return enqueue_iters<double, double>(A, val, x, c.W, nit, cs, false);
+        });
+    }
+    const float* val32 = A->val32.as<float>();
+    GraphKey key{G_SOLORU, c.W.state.p, x, nit, 0, A->variant, A->vwidth, A->ws_gen};
+    return run_maybe_graph(A, key, true, s, [&](cudaStream_t cs) {
+        return enqueue_iters_ru<double>(A, val32, val, b, x, c.d, c.W, nit, cs, false);
+    });
 }
 
 }  // namespace lilac

@@ -231,6 +231,26 @@ lilac_status slab_refresh_values(lilac_csr A, cudaStream_t stream);
 void slab_release(lilac_csr A);
 bool slab_worthwhile(const lilac_csr_s* A);
 lilac_status ensure_sell(lilac_csr A, cudaStream_t stream);
+// One CG solve on caller-held device memory with the handle's tuned kernels
+// (lilac_cg.cu; the request server's lane for large matrices).  prec 0: FP64
+// CG; prec 2: FP32 CG with FP64 reliable updates (delta: the replacement
+// threshold).  Bytes of the caller's workspace, its layout, preparation
+// (before any capture), the start (x = 0) and nit iterations as a cached graph.
+struct SoloCg {
+    CgWork W;  // views into the caller's workspace
+    float* d = nullptr;
+    double* r64 = nullptr;
+    int prec = 0;
+};
+size_t solo_cg_bytes(const lilac_csr_s* A, int prec);
+void solo_cg_bind(const lilac_csr_s* A, int prec, void* ws, SoloCg& c);
+lilac_status solo_cg_prepare(lilac_csr A, int prec, cudaStream_t s);
+lilac_status solo_cg_start(lilac_csr A, SoloCg& c, const double* b, double* x, double rtol,
+                           int max_iter, double delta, cudaStream_t s);
+lilac_status solo_cg_iters(lilac_csr A, SoloCg& c, const double* b, double* x, int nit,
+                           cudaStream_t s);
+lilac_status spmm_vectors_device(lilac_csr A, int k, const double* Xv, double* Yv, double* scratch,
+                                 cudaStream_t s);
 bool hub_worthwhile(const lilac_csr_s* A);
 lilac_status ensure_hub(lilac_csr A, cudaStream_t stream);
 lilac_status hub_refresh_values(lilac_csr A, cudaStream_t stream);

@@ -6,11 +6,19 @@
 // exceeded -- the paper's marshaling (construct on first use, destruct when
 // needed, Section 3.3 and Section 4.2) applied to a stream of requests.
 // Requests are admitted in arrival order while the budget and the active
-// limit allow; each round runs every admitted SpMV request in one batched
-// launch and advances every active CG solve by `iters_per_round` iterations
-// (one captured graph for all of them); finished requests are retired (result
-// copied to the caller's host buffer, latency recorded) and their slots and
-// memory go to the next requests in the queue.
+// limit allow; each round runs every admitted SpMV request and advances every
+// active CG solve by `iters_per_round` iterations; finished requests are
+// retired (result copied to the caller's host buffer, latency recorded) and
+// their slots and memory go to the next requests in the queue.
+//
+// Two lanes by size.  Requests on matrices of fewer than kServerLargeNnz
+// nonzeros run batched: all single-vector SpMVs in one launch, all CG
+// iterations of a round in one captured graph (many small problems, one
+// launch).  Requests on larger matrices, and SpMVs of 2..32 vectors, run on
+// the matrix's own tuned kernels (lilac_spmv's, lilac_spmm's and lilac_cg's
+// iterations, per request one cached graph of a round) on a second stream,
+// concurrently with the batched lane; the lane depends on the request alone,
+// so a request's result does not depend on the rest of the stream.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -92,11 +100,28 @@ struct SrvMatrix {
 struct SrvRequest {
     lilac_request r;
     double arrival = 0.0;
+    double admitted = 0.0;
+    int rounds = 0;
     void* ws = nullptr;  // workspace(s) + device vectors
     size_t ws_bytes = 0;
-    std::vector<BatchProb> probs;  // one per vector (SpMV) or one (CG)
+    std::vector<BatchProb> probs;  // one per vector (SpMV) or one (CG); none for multi-vector
     bool started = false;
+    bool multi = false;  // SpMV of 2..32 vectors: the multi-vector kernel
+    bool large = false;  // single-vector SpMV or CG on a large matrix: its own kernels
+    double* xv = nullptr;  // multi: X and Y vector-major, then row-major scratch
+    double* yv = nullptr;
+    double* scratch = nullptr;
+    SoloCg solo;              // large CG: vectors and state in ws
+    const double* sb = nullptr;  // large: b (CG) or x (SpMV) on the device
+    double* sx = nullptr;        // large: x (CG) or y (SpMV) on the device
+    int launched = 0;            // large CG: iterations launched
 };
+
+// SpMV requests of this many vectors run through the multi-vector kernel.
+constexpr int kServerMultiMin = 2, kServerMultiMax = 32;
+// Matrices of at least this many nonzeros run requests on their own kernels.
+constexpr int64_t kServerLargeNnz = (int64_t)1 << 19;
+constexpr double kServerRuDelta = 0.1;  // reliable-update threshold of precision 2
 
 }  // namespace lilac
 
@@ -107,6 +132,10 @@ struct lilac_server_s {
     int sm_count = 1;
     lilac_server_opts o{};
     cudaStream_t stream = nullptr;
+    cudaStream_t lane2 = nullptr;  // the large-matrix lane (created with the server)
+    cudaEvent_t round_start = nullptr;
+    CgState* solo_states = nullptr;  // pinned: the large CG solves' states after a round
+    int solo_cap = 0;
     std::vector<SrvMatrix> mats;
     std::deque<SrvRequest*> queue;
     std::vector<SrvRequest*> active;
@@ -144,29 +173,36 @@ static int64_t estimate_matrix_bytes(const SrvMatrix& m) {
            (int64_t)8192 * 16 + (1 << 20);
 }
 
+// Evict least recently used resident matrices that no active request uses
+// (never `keep`) until `need` more bytes fit the budget; false if they cannot.
+static bool evict_for(lilac_server_s* S, int64_t need, int keep) {
+    while (used_bytes(S) + need > S->o.hbm_budget_bytes) {
+        int victim = -1;
+        for (int i = 0; i < (int)S->mats.size(); ++i) {
+            const SrvMatrix& c = S->mats[i];
+            if (i != keep && c.h && c.users == 0 &&
+                (victim < 0 || c.last_use < S->mats[victim].last_use))
+                victim = i;
+        }
+        if (victim < 0) return false;
+        lilac_csr_destroy(S->mats[victim].h);
+        S->mats[victim].h = nullptr;
+        S->stats.evictions++;
+    }
+    return true;
+}
+
 // Make matrix `id` resident within the budget; false if it cannot fit now.
 static lilac_status make_resident(lilac_server_s* S, int id, bool* ok) {
     SrvMatrix& m = S->mats[id];
     *ok = true;
     if (m.h) return LILAC_OK;
-    const int64_t need = estimate_matrix_bytes(m);
-    while (used_bytes(S) + need > S->o.hbm_budget_bytes) {
-        // evict the least recently used resident matrix nobody uses
-        int victim = -1;
-        for (int i = 0; i < (int)S->mats.size(); ++i) {
-            const SrvMatrix& c = S->mats[i];
-            if (c.h && c.users == 0 && (victim < 0 || c.last_use < S->mats[victim].last_use)) victim = i;
-        }
-        if (victim < 0) {
-            *ok = false;
-            return LILAC_OK;
-        }
-        lilac_csr_destroy(S->mats[victim].h);
-        S->mats[victim].h = nullptr;
-        S->stats.evictions++;
+    if (!evict_for(S, estimate_matrix_bytes(m), id)) {
+        *ok = false;
+        return LILAC_OK;
     }
     LILAC_TRY(lilac_csr_create(m.rows, m.ncols, m.nnz, m.row_ptr, m.col_ind, m.vals, LILAC_F64,
-                               LILAC_MEM_HOST, LILAC_CREATE_NO_TUNE, S->stream, &m.h));
+                               LILAC_MEM_HOST, S->o.tune ? 0u : LILAC_CREATE_NO_TUNE, S->stream, &m.h));
     lilac_csr_info_t info;
     lilac_csr_info(m.h, &info);
     m.bytes = info.device_bytes;
@@ -180,18 +216,39 @@ static int req_prec(const SrvRequest* q) {
     return q->r.kind == LILAC_REQ_CG && q->r.precision == 2 ? BP_F32_RU : BP_F64;
 }
 
+static bool req_multi(const SrvRequest* q) {
+    return q->r.kind == LILAC_REQ_SPMV && q->r.nvec >= kServerMultiMin && q->r.nvec <= kServerMultiMax;
+}
+
+static bool req_large(const lilac_server_s* S, const SrvRequest* q) {
+    const SrvMatrix& m = S->mats[q->r.matrix];
+    return m.nnz >= kServerLargeNnz && !req_multi(q) &&
+           (q->r.kind == LILAC_REQ_CG || q->r.nvec == 1);
+}
+
 // Workspace of a request: per-vector problem workspaces + device in/out vectors.
 static size_t request_bytes(const lilac_server_s* S, const SrvRequest* q) {
     const SrvMatrix& m = S->mats[q->r.matrix];
     auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+    const size_t xb1 = al(sizeof(double) * (size_t)std::max(1, m.ncols));
+    const size_t yb1 = al(sizeof(double) * (size_t)std::max(1, m.rows));
+    if (req_large(S, q))
+        return q->r.kind == LILAC_REQ_SPMV
+                   ? xb1 + yb1
+                   : al(solo_cg_bytes(m.h, q->r.precision == 2 ? 2 : 0)) + 2 * yb1;
     if (q->r.kind == LILAC_REQ_SPMV) {
         const size_t k = (size_t)q->r.nvec;
+        if (req_multi(q))
+            return 2 * (al(sizeof(double) * k * (size_t)std::max(1, m.ncols)) +
+                        al(sizeof(double) * k * (size_t)std::max(1, m.rows)));
         return k * (al(batch_workspace_bytes(m.h, BK_SPMV, BP_F64)) +
                     al(sizeof(double) * (size_t)std::max(1, m.ncols)) +
                     al(sizeof(double) * (size_t)std::max(1, m.rows)));
     }
     return al(batch_workspace_bytes(m.h, BK_CG, req_prec(q))) + 2 * al(sizeof(double) * (size_t)m.rows);
 }
+
+static void retire(lilac_server_s* S, SrvRequest* q, int status, int iters, double rel_res);
 
 static lilac_status admit(lilac_server_s* S) {
     while (!S->queue.empty() && (int)S->active.size() < S->o.max_active) {
@@ -200,10 +257,16 @@ static lilac_status admit(lilac_server_s* S) {
         bool ok = false;
         LILAC_TRY(make_resident(S, q->r.matrix, &ok));
         if (!ok) break;  // wait for memory to be released
+        q->multi = req_multi(q);
+        q->large = req_large(S, q);
         {
-            // the copy the batched kernels run on (once per matrix)
-            const int kind = q->r.kind == LILAC_REQ_SPMV ? BK_SPMV : BK_CG;
-            LILAC_TRY(batch_prepare_layout(m.h, kind, req_prec(q), S->stream));
+            // what the request's kernels need of the matrix (once per matrix):
+            // the batched copy, or the scratch of the matrix's own CG kernels
+            if (q->large && q->r.kind == LILAC_REQ_CG && q->r.precision == 0)
+                LILAC_TRY(solo_cg_prepare(m.h, 0, S->stream));
+            else if (!q->large && !q->multi)
+                LILAC_TRY(batch_prepare_layout(m.h, q->r.kind == LILAC_REQ_SPMV ? BK_SPMV : BK_CG,
+                                               req_prec(q), S->stream));
             lilac_csr_info_t info;
             lilac_csr_info(m.h, &info);
             m.bytes = info.device_bytes;
@@ -212,12 +275,24 @@ static lilac_status admit(lilac_server_s* S) {
         // a mixed-precision solve derives the matrix's FP32 values on first use
         const bool needs_val32 = req_prec(q) == BP_F32_RU && !m.h->val32_valid;
         const int64_t extra = needs_val32 ? (int64_t)m.nnz * 4 + 256 : 0;
-        if (used_bytes(S) + (int64_t)DevicePool::cls(need) + extra > S->o.hbm_budget_bytes) {
+        if (!evict_for(S, (int64_t)DevicePool::cls(need) + extra, q->r.matrix)) {
+            if (S->active.empty()) {
+                // nothing will release memory: the request can never fit
+                S->queue.pop_front();
+                set_last_error("request larger than the server's device-memory budget");
+                q->admitted = now_s();
+                m.users++;  // (retire releases one use)
+                retire(S, q, LILAC_ERR_BUDGET, 0, 0.0);
+                continue;
+            }
             S->stats.budget_waits++;
             break;
         }
-        if (needs_val32) {
-            LILAC_TRY(make_val32(m.h, S->stream));
+        if (needs_val32 || (q->large && req_prec(q) == BP_F32_RU)) {
+            if (q->large)
+                LILAC_TRY(solo_cg_prepare(m.h, 2, S->stream));
+            else
+                LILAC_TRY(make_val32(m.h, S->stream));
             lilac_csr_info_t info;
             lilac_csr_info(m.h, &info);
             m.bytes = info.device_bytes;
@@ -228,7 +303,36 @@ static lilac_status admit(lilac_server_s* S) {
         auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
         unsigned char* w = static_cast<unsigned char*>(q->ws);
         q->probs.clear();
-        if (q->r.kind == LILAC_REQ_SPMV) {
+        q->admitted = now_s();
+        if (q->large) {
+            // SpMV: x | y; CG: the solve's vectors and state | b | x
+            const size_t xb = al(sizeof(double) * (size_t)std::max(1, m.ncols));
+            const size_t yb = al(sizeof(double) * (size_t)std::max(1, m.rows));
+            if (q->r.kind == LILAC_REQ_SPMV) {
+                q->sb = reinterpret_cast<const double*>(w);
+                q->sx = reinterpret_cast<double*>(w + xb);
+                LILAC_CUDA_TRY(cudaMemcpyAsync(w, q->r.in, sizeof(double) * (size_t)m.ncols,
+                                               cudaMemcpyHostToDevice, S->stream));
+            } else {
+                const int prec = q->r.precision == 2 ? 2 : 0;
+                const size_t sb = al(solo_cg_bytes(m.h, prec));
+                solo_cg_bind(m.h, prec, w, q->solo);
+                q->sb = reinterpret_cast<const double*>(w + sb);
+                q->sx = reinterpret_cast<double*>(w + sb + yb);
+                LILAC_CUDA_TRY(cudaMemcpyAsync(w + sb, q->r.in, sizeof(double) * (size_t)m.rows,
+                                               cudaMemcpyHostToDevice, S->stream));
+            }
+        } else if (q->multi) {
+            // X in, then row-major X and Y, then Y out (request_bytes)
+            const size_t k = (size_t)q->r.nvec;
+            const size_t xb = al(sizeof(double) * k * (size_t)std::max(1, m.ncols));
+            const size_t yb = al(sizeof(double) * k * (size_t)std::max(1, m.rows));
+            q->xv = reinterpret_cast<double*>(w);
+            q->scratch = reinterpret_cast<double*>(w + xb);
+            q->yv = reinterpret_cast<double*>(w + 2 * xb + yb);
+            LILAC_CUDA_TRY(cudaMemcpyAsync(q->xv, q->r.in, sizeof(double) * k * (size_t)m.ncols,
+                                           cudaMemcpyHostToDevice, S->stream));
+        } else if (q->r.kind == LILAC_REQ_SPMV) {
             const size_t wsb = al(batch_workspace_bytes(m.h, BK_SPMV, BP_F64));
             const size_t xb = al(sizeof(double) * (size_t)std::max(1, m.ncols));
             const size_t yb = al(sizeof(double) * (size_t)std::max(1, m.rows));
@@ -269,6 +373,8 @@ static void retire(lilac_server_s* S, SrvRequest* q, int status, int iters, doub
     c.rel_res = rel_res;
     c.arrival = q->arrival;
     c.finish = now_s();
+    c.admitted = q->admitted;
+    c.rounds = q->rounds;
     S->done.push_back(c);
     S->pool.put(q->ws, q->ws_bytes);
     m.users--;
@@ -277,17 +383,62 @@ static void retire(lilac_server_s* S, SrvRequest* q, int status, int iters, doub
     delete q;
 }
 
+// The large-matrix lane of a round, on its own stream: multi-vector SpMVs,
+// single-vector SpMVs and R iterations of each CG solve on the matrices' own
+// kernels, then the solves' states to pinned host memory.
+static lilac_status run_lane2(lilac_server_s* S, const std::vector<SrvRequest*>& multi_reqs,
+                              const std::vector<SrvRequest*>& big_spmv,
+                              const std::vector<SrvRequest*>& big_cg) {
+    cudaStream_t s2 = S->lane2;
+    // after the admissions' uploads on the server's stream
+    LILAC_CUDA_TRY(cudaEventRecord(S->round_start, S->stream));
+    LILAC_CUDA_TRY(cudaStreamWaitEvent(s2, S->round_start, 0));
+    for (SrvRequest* q : multi_reqs)
+        LILAC_TRY(spmm_vectors_device(S->mats[q->r.matrix].h, q->r.nvec, q->xv, q->yv, q->scratch, s2));
+    for (SrvRequest* q : big_spmv)
+        LILAC_TRY(lilac_spmv(S->mats[q->r.matrix].h, q->sb, q->sx, LILAC_MEM_DEVICE, s2));
+    if ((int)big_cg.size() > S->solo_cap) {
+        if (S->solo_states) cudaFreeHost(S->solo_states);
+        S->solo_states = nullptr;
+        S->solo_cap = 0;
+        const int cap = std::max(16, 2 * (int)big_cg.size());
+        LILAC_CUDA_TRY(cudaMallocHost(reinterpret_cast<void**>(&S->solo_states), sizeof(CgState) * (size_t)cap));
+        S->solo_cap = cap;
+    }
+    for (size_t i = 0; i < big_cg.size(); ++i) {
+        SrvRequest* q = big_cg[i];
+        lilac_csr h = S->mats[q->r.matrix].h;
+        if (!q->started) {
+            LILAC_TRY(solo_cg_start(h, q->solo, q->sb, q->sx, q->r.rtol, q->r.max_iter, kServerRuDelta, s2));
+            q->started = true;
+        }
+        // always a whole round: iterations past the end of the solve return at once
+        LILAC_TRY(solo_cg_iters(h, q->solo, q->sb, q->sx, S->o.iters_per_round, s2));
+        q->launched += S->o.iters_per_round;
+        LILAC_CUDA_TRY(cudaMemcpyAsync(&S->solo_states[i], q->solo.W.state.p, sizeof(CgState),
+                                       cudaMemcpyDeviceToHost, s2));
+    }
+    return LILAC_OK;
+}
+
 static lilac_status run_round(lilac_server_s* S) {
     cudaStream_t s = S->stream;
-    std::vector<SrvRequest*> spmv_reqs, cg_reqs, new_cg;
+    std::vector<SrvRequest*> spmv_reqs, cg_reqs, new_cg, multi_reqs, big_spmv, big_cg;
     for (SrvRequest* q : S->active) {
-        if (q->r.kind == LILAC_REQ_SPMV)
+        q->rounds++;
+        if (q->multi)
+            multi_reqs.push_back(q);
+        else if (q->large)
+            (q->r.kind == LILAC_REQ_SPMV ? big_spmv : big_cg).push_back(q);
+        else if (q->r.kind == LILAC_REQ_SPMV)
             spmv_reqs.push_back(q);
         else {
             cg_reqs.push_back(q);
             if (!q->started) new_cg.push_back(q);
         }
     }
+    const bool lane2 = !multi_reqs.empty() || !big_spmv.empty() || !big_cg.empty();
+    if (lane2) LILAC_TRY(run_lane2(S, multi_reqs, big_spmv, big_cg));
     // all SpMV requests in one batched launch
     if (!spmv_reqs.empty()) {
         std::vector<BatchProb> probs;
@@ -324,6 +475,7 @@ static lilac_status run_round(lilac_server_s* S) {
                                        cudaMemcpyDeviceToHost, s));
     }
     LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (lane2) LILAC_CUDA_TRY(cudaStreamSynchronize(S->lane2));
     S->stats.rounds++;
     // retire: every SpMV request, and the CG solves that are done
     for (SrvRequest* q : spmv_reqs) {
@@ -331,6 +483,28 @@ static lilac_status run_round(lilac_server_s* S) {
         for (int j = 0; j < q->r.nvec; ++j)
             LILAC_CUDA_TRY(cudaMemcpyAsync(q->r.out + (size_t)j * m.rows, q->probs[j].y_out,
                                            sizeof(double) * (size_t)m.rows, cudaMemcpyDeviceToHost, s));
+    }
+    for (SrvRequest* q : multi_reqs) {
+        const SrvMatrix& m = S->mats[q->r.matrix];
+        LILAC_CUDA_TRY(cudaMemcpyAsync(q->r.out, q->yv, sizeof(double) * (size_t)q->r.nvec * m.rows,
+                                       cudaMemcpyDeviceToHost, s));
+    }
+    for (SrvRequest* q : big_spmv) {
+        const SrvMatrix& m = S->mats[q->r.matrix];
+        LILAC_CUDA_TRY(cudaMemcpyAsync(q->r.out, q->sx, sizeof(double) * (size_t)m.rows,
+                                       cudaMemcpyDeviceToHost, s));
+    }
+    // a large solve ends when its state says so (or, as a guard, a round
+    // after its iteration limit)
+    std::vector<SrvRequest*> finished_big;
+    for (size_t i = 0; i < big_cg.size(); ++i) {
+        SrvRequest* q = big_cg[i];
+        if (S->solo_states[i].done || q->launched > q->r.max_iter) {
+            const SrvMatrix& m = S->mats[q->r.matrix];
+            LILAC_CUDA_TRY(cudaMemcpyAsync(q->r.out, q->sx, sizeof(double) * (size_t)m.rows,
+                                           cudaMemcpyDeviceToHost, s));
+            finished_big.push_back(q);
+        }
     }
     std::vector<SrvRequest*> finished_cg;
     for (size_t i = 0; i < cg_reqs.size(); ++i)
@@ -340,11 +514,26 @@ static lilac_status run_round(lilac_server_s* S) {
                                            sizeof(double) * (size_t)m.rows, cudaMemcpyDeviceToHost, s));
             finished_cg.push_back(cg_reqs[i]);
         }
-    if (!spmv_reqs.empty() || !finished_cg.empty()) LILAC_CUDA_TRY(cudaStreamSynchronize(s));
+    if (!spmv_reqs.empty() || !multi_reqs.empty() || !big_spmv.empty() || !finished_cg.empty() ||
+        !finished_big.empty())
+        LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<SrvRequest*> still;
     for (SrvRequest* q : S->active) {
         if (q->r.kind == LILAC_REQ_SPMV) {
             retire(S, q, LILAC_OK, 0, 0.0);
+            continue;
+        }
+        if (q->large) {
+            auto it = std::find(finished_big.begin(), finished_big.end(), q);
+            if (it == finished_big.end()) {
+                still.push_back(q);
+                continue;
+            }
+            const size_t i = (size_t)(std::find(big_cg.begin(), big_cg.end(), q) - big_cg.begin());
+            const CgState& st = S->solo_states[i];
+            const double rr = req_prec(q) == BP_F32_RU && st.true_rr >= 0.0 ? st.true_rr : st.rr;
+            retire(S, q, st.done ? st.status : LILAC_ERR_NOT_CONVERGED, st.iters,
+                   st.bb > 0.0 ? std::sqrt(rr / st.bb) : 0.0);
             continue;
         }
         auto it = std::find(finished_cg.begin(), finished_cg.end(), q);
@@ -372,7 +561,7 @@ void lilac_server_opts_default(lilac_server_opts* o) {
     o->hbm_budget_bytes = (int64_t)120 << 30;
     o->max_active = 256;
     o->iters_per_round = 16;
-    o->pad = 0;
+    o->tune = 0;
 }
 
 lilac_status lilac_server_create(const lilac_server_opts* opts, void* stream, lilac_server* out) try {
@@ -399,6 +588,13 @@ lilac_status lilac_server_create(const lilac_server_opts* opts, void* stream, li
         e->device = S->device;
         e->sm_count = S->sm_count;
     }
+    if (cudaStreamCreateWithFlags(&S->lane2, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&S->round_start, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        lilac_server_destroy(S);
+        set_last_error("lilac_server_create: stream or event creation failed");
+        return LILAC_ERR_CUDA;
+    }
     *out = S;
     return LILAC_OK;
 } catch (...) {
@@ -417,6 +613,9 @@ lilac_status lilac_server_destroy(lilac_server S) try {
     for (SrvMatrix& m : S->mats)
         if (m.h) lilac_csr_destroy(m.h);
     S->states_d.release();
+    if (S->solo_states) cudaFreeHost(S->solo_states);
+    if (S->round_start) cudaEventDestroy(S->round_start);
+    if (S->lane2) cudaStreamDestroy(S->lane2);
     delete S;
     return LILAC_OK;
 } catch (...) {

@@ -133,6 +133,22 @@ static lilac_status spmm_impl(lilac_csr A, const T* X, T* Y, int k, int layout, 
     return LILAC_OK;
 }
 
+// Y = A X for k (<= 32) FP64 vectors given and returned vector-major on the
+// device (X: k x ncols, Y: k x rows), through caller-held row-major scratch
+// (k x ncols then k x rows doubles): the server's multi-vector requests.
+lilac_status spmm_vectors_device(lilac_csr A, int k, const double* Xv, double* Yv, double* scratch,
+                                 cudaStream_t s) {
+    double* xr = scratch;
+    double* yr = scratch + (size_t)k * A->ncols;
+    const int tg = A->sm_count * 8;
+    spmm_transpose_kernel<double><<<tg, 256, 0, s>>>(A->ncols, k, Xv, xr, true);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    LILAC_TRY(spmm_launch<double>(A, k, xr, yr, s));
+    spmm_transpose_kernel<double><<<tg, 256, 0, s>>>(A->rows, k, yr, Yv, false);
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
+}
+
 }  // namespace lilac
 
 using namespace lilac;

@@ -92,7 +92,7 @@ class lilac_cg_info(ctypes.Structure):
 
 class lilac_server_opts(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_int64), ("max_active", ctypes.c_int32),
-                ("iters_per_round", ctypes.c_int32), ("pad", ctypes.c_int32)]
+                ("iters_per_round", ctypes.c_int32), ("tune", ctypes.c_int32)]
 
 
 class lilac_request(ctypes.Structure):
@@ -105,7 +105,8 @@ class lilac_request(ctypes.Structure):
 class lilac_completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_int64), ("status", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("rel_res", ctypes.c_double), ("arrival", ctypes.c_double),
-                ("finish", ctypes.c_double)]
+                ("finish", ctypes.c_double), ("admitted", ctypes.c_double),
+                ("rounds", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class lilac_server_stats_t(ctypes.Structure):
@@ -427,7 +428,8 @@ class Batch:
 class Server:
     """Owns a lilac_server (continuous batching of SpMV / CG requests)."""
 
-    def __init__(self, hbm_budget_bytes=None, max_active=None, iters_per_round=None, stream=None):
+    def __init__(self, hbm_budget_bytes=None, max_active=None, iters_per_round=None, tune=None,
+                 stream=None):
         o = lilac_server_opts()
         _lib().lilac_server_opts_default(ctypes.byref(o))
         if hbm_budget_bytes is not None:
@@ -436,6 +438,8 @@ class Server:
             o.max_active = int(max_active)
         if iters_per_round is not None:
             o.iters_per_round = int(iters_per_round)
+        if tune is not None:
+            o.tune = int(tune)
         h = ctypes.c_void_p()
         _check(_lib().lilac_server_create(ctypes.byref(o), stream if stream is not None
                                           else current_stream(), ctypes.byref(h)),
@@ -473,7 +477,8 @@ class Server:
         for i in range(n.value):
             c = buf[i]
             out.append({"tag": c.tag, "status": c.status, "iters": c.iters, "rel_res": c.rel_res,
-                        "arrival": c.arrival, "finish": c.finish})
+                        "arrival": c.arrival, "finish": c.finish, "admitted": c.admitted,
+                        "rounds": c.rounds})
             self._keep.pop(("r", c.tag), None)
         return out
 

@@ -1,8 +1,10 @@
 """The request server: every request of a mixed SpMV / CG stream (CG in FP64
-or in FP32 with FP64 reliable updates) completes with the oracle's result
-(SpMV tolerance; CG true residual <= 1e-10), a
-request's result is bitwise the same alone and in the mix, and a small
-device-memory budget forces evictions and waiting without changing results."""
+or in FP32 with FP64 reliable updates; SpMV of one vector batched, of 2..32
+through the multi-vector kernel) completes with the oracle's result (SpMV
+tolerance; CG true residual <= 1e-10), with arrival <= admission <= finish,
+a request's result is bitwise the same alone and in the mix, the matrices
+may be tuned at upload, and a small device-memory budget forces
+evictions and waiting without changing results."""
 import numpy as np
 import pytest
 
@@ -38,13 +40,15 @@ def _requests(pool, n, seed):
     return out
 
 
-def _serve(pool, reqs, budget=None, burst=7):
+def _serve(pool, reqs, budget=None, burst=7, tune=0):
     torch_cuda()
-    S = L.Server(hbm_budget_bytes=budget, iters_per_round=8)
+    S = L.Server(hbm_budget_bytes=budget, iters_per_round=8, tune=tune)
     ids = [S.add_matrix(A) for A in pool]
     outs, results = {}, {}
-    i = 0
+    i, steps = 0, 0
     while i < len(reqs) or len(results) < len(reqs):
+        steps += 1
+        assert steps < 20000, ("no progress", S.stats())
         for kind, mi, inp, k, tag, prec in reqs[i:i + burst]:
             A = pool[mi]
             if kind == "spmv":
@@ -68,7 +72,7 @@ def _check(pool, reqs, outs, results):
     for kind, mi, inp, k, tag, prec in reqs:
         A, out, c = pool[mi], outs[tag], results[tag]
         assert c["status"] == L.LILAC_OK, (tag, c)
-        assert c["finish"] >= c["arrival"]
+        assert c["arrival"] <= c["admitted"] <= c["finish"] and c["rounds"] >= 1
         if kind == "spmv":
             for j in range(k):
                 x = inp[j * A.ncols:(j + 1) * A.ncols]
@@ -81,24 +85,27 @@ def _check(pool, reqs, outs, results):
                 assert c["rel_res"] <= 1e-10
 
 
-def test_mixed_stream_matches_oracle():
+@pytest.mark.parametrize("tune", [0, 1])
+def test_mixed_stream_matches_oracle(tune):
     pool = _pool()
     reqs = _requests(pool, 60, seed=0)
-    outs, results, stats = _serve(pool, reqs)
+    outs, results, stats = _serve(pool, reqs, tune=tune)
     assert stats["completed"] == 60 and stats["submitted"] == 60
     _check(pool, reqs, outs, results)
 
 
-def test_same_result_alone_and_in_the_mix():
+def test_same_result_alone_and_in_the_mix(tune=0):
+    """(Untuned: the timed tuner may pick another kernel in another run.)"""
     pool = _pool()
     reqs = _requests(pool, 40, seed=1)
-    outs_mix, _, _ = _serve(pool, reqs)
+    outs_mix, _, _ = _serve(pool, reqs, tune=tune)
     cgs = [r for r in reqs if r[0] == "cg"]
+    spmvs = [r for r in reqs if r[0] == "spmv"]
     probes = ([r for r in cgs if r[5] == 0][:2] + [r for r in cgs if r[5] == 2][:2] +
-              [r for r in reqs if r[0] == "spmv"][:3])
-    assert len(probes) == 7
+              [r for r in spmvs if r[3] == 1][:2] + [r for r in spmvs if r[3] > 1][:2])
+    assert len(probes) == 8
     for probe in probes:
-        outs_alone, _, _ = _serve(pool, [probe])
+        outs_alone, _, _ = _serve(pool, [probe], tune=tune)
         np.testing.assert_array_equal(outs_alone[probe[4]], outs_mix[probe[4]])
 
 
