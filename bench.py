@@ -790,9 +790,10 @@ WORKLOADS = {"cg75k": CG75k, "spmv2d": SpMV2D, "pagerank22": PageRank22, "ir192"
 def served_stream(n_req=2000, n_mats=32, n_lo=1e3, n_hi=2e5, kmax=8, seed=0):
     """Seeded request stream: a pool of 2D/3D Laplacians and banded SPD matrices
     (half-bandwidth 8..64) with n log-uniform in [n_lo, n_hi]; requests pick a
-    matrix with Zipf(1.1) popularity; half are SpMV batches of k in [1, kmax]
-    vectors, half CG solves to 1e-10 (b uniform in [-1, 1]), of which half ask
-    for FP32 values with FP64 refinement (precision 2)."""
+    matrix with Zipf(1.1) popularity; half are SpMV batches of k uniform in
+    [1, kmax] vectors, half CG solves to 1e-10, of which half ask for FP32
+    values with FP64 refinement (precision 2).  Requests are (kind, matrix, k,
+    precision); their vectors come from per-matrix blocks (served_inputs)."""
     from paper_2001_07938_gb300 import inputs
     rng = np.random.default_rng(seed)
     pool = []
@@ -810,158 +811,168 @@ def served_stream(n_req=2000, n_mats=32, n_lo=1e3, n_hi=2e5, kmax=8, seed=0):
     reqs = []
     for t in range(n_req):
         mi = int(rng.choice(n_mats, p=w))
-        A = pool[mi]
         if rng.random() < 0.5:
-            k = int(rng.integers(1, kmax + 1))
-            reqs.append(("spmv", mi, inputs.uniform(10_000 + t, k * A.ncols), k, 0))
+            reqs.append(("spmv", mi, int(rng.integers(1, kmax + 1)), 0))
         else:
-            prec = 2 if rng.random() < 0.5 else 0
-            reqs.append(("cg", mi, inputs.uniform(20_000 + t, A.n), 1, prec))
+            reqs.append(("cg", mi, 1, 2 if rng.random() < 0.5 else 0))
     return pool, reqs
 
 
-def run_marshal(args):
-    """The paper's marshaling experiment (Section 6.3) on the 2D Laplacian 64x64
-    (FP64): repeated y = A x through the host calling convention, naive (upload,
-    tune, multiply, free on every call) vs the library's resident copies with
-    change tracking by content hash or by version number, vs a device handle."""
+def _pinned(n):
+    """An FP64 host array in page-locked memory (a numpy view of a pinned
+    tensor, which the view keeps alive)."""
     import torch
-    from paper_2001_07938_gb300 import build as lbuild
+    return torch.empty(max(1, n), dtype=torch.float64, pin_memory=True).numpy()[:n]
+
+
+def served_inputs(pool, reqs, kmax, alloc=np.empty):
+    """Per used matrix: kmax SpMV input vectors (one block, a request of k
+    vectors takes the first k) and one right-hand side, uniform in [-1, 1]:
+    the requests' inputs without a copy per request."""
     from paper_2001_07938_gb300 import inputs
-    from paper_2001_07938_gb300 import lilac as L
-    torch.cuda.set_device(0)
-    lbuild.build()
-    L.load()
-    A = inputs.laplacian2d(64)
-    x = inputs.uniform(0, A.ncols)
-    y = np.zeros(A.n)
+    spmv_m = {r[1] for r in reqs if r[0] == "spmv"}
+    cg_m = {r[1] for r in reqs if r[0] == "cg"}
+    X, B = {}, {}
+    for mi in sorted(spmv_m):
+        X[mi] = alloc(kmax * pool[mi].ncols)
+        X[mi][:] = inputs.uniform(10_000 + mi, kmax * pool[mi].ncols)
+    for mi in sorted(cg_m):
+        B[mi] = alloc(pool[mi].n)
+        B[mi][:] = inputs.uniform(20_000 + mi, pool[mi].n)
+    return X, B
 
-    def timed(fn, calls):
-        for _ in range(3):
-            fn()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(calls):
-            fn()
-        torch.cuda.synchronize()
-        return (time.perf_counter() - t0) / calls
 
-    L.lilac_host_cache_clear()
-    modes = {}
-    modes["naive"] = timed(lambda: L.spmv_host(A, x, y, naive=True), 50)
-    modes["cached_hash"] = timed(lambda: L.spmv_host(A, x, y), 1000)
-    modes["cached_version"] = timed(lambda: L.spmv_host(A, x, y, version=1), 1000)
-    M = L.CsrMatrix.from_csr(A)
-    xd = torch.from_numpy(x).cuda()
-    yd = torch.empty(A.n, dtype=torch.float64, device="cuda")
-    modes["device_handle"] = timed(lambda: M.spmv(xd, yd), 1000)
-    M.close()
-    st = L.lilac_host_cache_stats()
-    L.lilac_host_cache_clear()
-    us = {k: v * 1e6 for k, v in modes.items()}
-    value = 1.0 / modes["cached_hash"]
-    line = {"metric": METRIC, "value": value, "unit": "calls/s", "n_gpus": 1, "steps": 1,
-            "warmup": 3, "ms_per_step": modes["cached_hash"] * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "marshal_laplacian2d_m64", "n": A.n, "nnz": A.nnz,
-                       "calls": {"naive": 50, "others": 1000},
-                       "note": "host x / y every call; device_handle keeps x, y on the device"},
-            "us_per_call": us,
-            "speedup_vs_naive": {k: modes["naive"] / v for k, v in modes.items()},
-            "cache_stats": st, "roofline": None, "cpu_baseline": None,
-            "e2e": {"value": value, "unit": "calls/s", "h2d_bytes_per_step": A.ncols * 8,
-                    "d2h_bytes_per_step": A.n * 8}}
-    print(json.dumps(line), flush=True)
-    return 0
+class _BufPool:
+    """Reusable host output buffers by length, page-locked like the inputs."""
+
+    def __init__(self, alloc=np.empty):
+        self.free = {}
+        self.alloc = alloc
+
+    def get(self, n):
+        lst = self.free.get(n)
+        return lst.pop() if lst else self.alloc(n)
+
+    def put(self, a):
+        self.free.setdefault(a.size, []).append(a)
 
 
 def run_served(args):
     """The served stream against the plain system (one request at a time,
-    lilac_spmv / FP64 lilac_cg, matrices resident), both with the same
-    tuning policy.  The server is created once; a first pass at saturation
-    uploads the pool (as the plain system's handles are created before it is
-    timed), then one saturated pass and one Poisson pass per load point are
-    timed.  Plain latencies under the same arrivals follow exactly from its
-    measured service times (FIFO, one server)."""
+    lilac_spmv per vector / FP64 lilac_cg, matrices resident), both with the
+    same tuning policy.  The server is created once; a first pass at
+    saturation uploads the pool (as the plain system's handles are created
+    before it is timed), then one saturated pass and one Poisson pass per load
+    point are timed.  Plain latencies under the same arrivals follow exactly
+    from its measured service times (FIFO, one server).  Every result is
+    compared with the plain system's at 16 sampled positions."""
     import torch
     from paper_2001_07938_gb300 import build as lbuild
     from paper_2001_07938_gb300 import lilac as L
     torch.cuda.set_device(0)
     lbuild.build()
     L.load()
+    t_begin = time.perf_counter()
+
+    def note(msg):
+        print(f"[served] {msg} at {time.perf_counter() - t_begin:.1f} s", file=sys.stderr, flush=True)
+
     pool, reqs = served_stream(n_req=args.served_requests, n_mats=args.served_mats,
                                n_hi=args.served_nmax, kmax=args.served_kmax)
+    X, B = served_inputs(pool, reqs, args.served_kmax, alloc=_pinned)
+    note(f"stream of {len(reqs)} requests over {len(pool)} matrices built")
     N = len(reqs)
     n_cg = sum(1 for r in reqs if r[0] == "cg")
-    n_mixed = sum(1 for r in reqs if r[0] == "cg" and r[4] == 2)
+    n_mixed = sum(1 for r in reqs if r[0] == "cg" and r[3] == 2)
     pool_bytes = sum(A.nnz * 12 + (A.n + 1) * 4 for A in pool)
+    req_bytes = sum(8 * r[2] * (pool[r[1]].ncols + pool[r[1]].n) for r in reqs)
+    bufs = _BufPool(alloc=_pinned)
+
+    def inp_of(r):
+        kind, mi, k, _ = r
+        return X[mi][:k * pool[mi].ncols] if kind == "spmv" else B[mi]
+
+    def out_len(r):
+        return r[2] * pool[r[1]].n
+
+    rs = np.random.default_rng(7)
+    samples = [rs.integers(0, out_len(r), 16) for r in reqs]
+    ref = [None] * N  # (values at the samples, max |plain result|)
+
     flags = 0 if args.served_tune else L.LILAC_CREATE_NO_TUNE
     Ms = [L.CsrMatrix.from_csr(A, flags=flags) for A in pool]
-    outs_plain = []
 
-    def plain_one(r):
-        kind, mi, inp, k, _ = r  # plain: every solve in FP64
-        A, M = pool[mi], Ms[mi]
+    def plain_one(r, out):
+        kind, mi, k, _ = r  # plain: every solve in FP64
+        A, M, inp = pool[mi], Ms[mi], inp_of(r)
         if kind == "spmv":
-            out = np.empty(k * A.n)
             for j in range(k):
                 M.spmv(inp[j * A.ncols:(j + 1) * A.ncols], out[j * A.n:(j + 1) * A.n])
         else:
-            out = np.zeros(A.n)
+            out[:] = 0.0
             M.cg(inp, out, max_iter=20000, rtol=1e-10, true_residual=False)
-        return out
 
     for r in reqs[:20]:  # warm-up (graph capture per matrix)
-        plain_one(r)
+        o = bufs.get(out_len(r))
+        plain_one(r, o)
+        bufs.put(o)
     service = []
     t_all = time.perf_counter()
-    for r in reqs:
+    for t, r in enumerate(reqs):
         t0 = time.perf_counter()
-        outs_plain.append(plain_one(r))
+        o = bufs.get(out_len(r))
+        plain_one(r, o)
         service.append(time.perf_counter() - t0)
+        ref[t] = (o[samples[t]].copy(), float(np.max(np.abs(o))))
+        bufs.put(o)
     plain_makespan = time.perf_counter() - t_all
     for M in Ms:
         M.close()
     cap = N / plain_makespan
+    note(f"plain done: {plain_makespan:.1f} s")
 
-    S = L.Server(hbm_budget_bytes=int(args.served_budget_gb * 2 ** 30),
-                 iters_per_round=args.served_round, tune=args.served_tune)
-    ids = [S.add_matrix(A) for A in pool]
-
-    def serve(timed_arrivals):
-        outs = [None] * N
+    def serve(S, ids, timed_arrivals, max_inflight=512, max_inflight_bytes=8 << 30):
+        """One pass of the stream; saturated (timed_arrivals None) keeps up to
+        max_inflight requests submitted and not yet completed."""
+        outs = {}
         lat, wait, svc, rounds = [0.0] * N, [0.0] * N, [0.0] * N, [0] * N
-        got = 0
+        worst = 0.0
+        got, i, inflight_bytes = 0, 0, 0
         t0 = L.Server.now()
         st0 = S.stats()
-        i = 0
         last_progress = L.Server.now()
         while got < N:
             now = L.Server.now() - t0
             if L.Server.now() - last_progress > 300.0:
                 raise RuntimeError(f"served stream stalled: {S.stats()}")
-            while i < N and (timed_arrivals is None or timed_arrivals[i] <= now):
-                kind, mi, inp, k, prec = reqs[i]
-                A = pool[mi]
-                out = np.empty(k * A.n) if kind == "spmv" else np.zeros(A.n)
+            while i < N and (timed_arrivals[i] <= now if timed_arrivals is not None else
+                             (i - got < max_inflight and inflight_bytes < max_inflight_bytes)):
+                kind, mi, k, prec = reqs[i]
+                out = bufs.get(out_len(reqs[i]))
                 outs[i] = out
+                inflight_bytes += out.nbytes
                 if kind == "spmv":
-                    S.submit(L.LILAC_REQ_SPMV, ids[mi], inp, out, i, nvec=k)
+                    S.submit(L.LILAC_REQ_SPMV, ids[mi], inp_of(reqs[i]), out, i, nvec=k)
                 else:
-                    S.submit(L.LILAC_REQ_CG, ids[mi], inp, out, i, max_iter=20000, rtol=1e-10,
-                             precision=prec)
+                    S.submit(L.LILAC_REQ_CG, ids[mi], inp_of(reqs[i]), out, i, max_iter=20000,
+                             rtol=1e-10, precision=prec)
                 i += 1
             pending = S.step()
             for c in S.poll():
                 # latency from the scheduled arrival when arrivals are timed
                 tag = c["tag"]
+                if c["status"] != L.LILAC_OK:
+                    raise RuntimeError(f"request {tag} failed: {c}")
                 a = c["arrival"] if timed_arrivals is None else t0 + timed_arrivals[tag]
                 lat[tag] = c["finish"] - a
                 wait[tag] = c["admitted"] - a
                 svc[tag] = c["finish"] - c["admitted"]
                 rounds[tag] = c["rounds"]
-                if c["status"] != L.LILAC_OK:
-                    raise RuntimeError(f"request {tag} failed: {c}")
+                out = outs.pop(tag)
+                vals, mx = ref[tag]
+                worst = max(worst, float(np.max(np.abs(out[samples[tag]] - vals))) / max(mx, 1e-300))
+                inflight_bytes -= out.nbytes
+                bufs.put(out)
                 got += 1
                 last_progress = L.Server.now()
             if pending == 0 and i < N and timed_arrivals is not None:
@@ -969,7 +980,7 @@ def run_served(args):
         makespan = L.Server.now() - t0
         st1 = S.stats()
         delta = {k: st1[k] - st0[k] for k in ("rounds", "uploads", "evictions", "budget_waits")}
-        return outs, lat, wait, svc, rounds, makespan, delta
+        return lat, wait, svc, rounds, makespan, delta, worst
 
     def pct(v, q):
         return 1000.0 * float(np.percentile(v, q))
@@ -990,48 +1001,78 @@ def run_served(args):
                                "n": float(np.mean([pool[reqs[t][1]].n for t in ts]))}
         return kinds
 
-    serve(None)  # warm-up: uploads, graph capture, pool blocks
-    outs_s, _, _, _, _, served_makespan, sat_delta = serve(None)
-    diff = max(float(np.max(np.abs(a - b)) / max(1e-300, float(np.max(np.abs(b)))))
-               for a, b in zip(outs_s, outs_plain))
-    value = N / served_makespan
-    loads = []
-    for load in [float(v) for v in args.served_loads.split(",")]:
+    def timed_pass(S, ids, load):
         lam = load * cap
-        rng = np.random.default_rng(1)
-        arrivals = np.cumsum(rng.exponential(1.0 / lam, N))
+        arrivals = np.cumsum(np.random.default_rng(1).exponential(1.0 / lam, N))
+        lat, wait, svc, rounds, mk, delta, worst = serve(S, ids, arrivals)
+        return {"load": load, "arrival_rate_per_s": lam,
+                "served": {"latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                           "queue_wait_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)},
+                           "p99_breakdown": breakdown(lat, wait, svc, rounds),
+                           "makespan_s": mk, "max_rel_diff_vs_plain": worst, **delta}}, arrivals
+
+    def plain_latency(arrivals):
         fin, lat_plain = 0.0, []
         for a, sv in zip(arrivals, service):  # FIFO single server, exact from service times
             fin = max(fin, a) + sv
             lat_plain.append(fin - a)
-        _, lat, wait, svc, rounds, mk, delta = serve(arrivals)
-        loads.append({"load": load, "arrival_rate_per_s": lam,
-                      "served": {"latency_ms": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
-                                 "queue_wait_ms": {"p50": pct(wait, 50), "p99": pct(wait, 99)},
-                                 "p99_breakdown": breakdown(lat, wait, svc, rounds),
-                                 "makespan_s": mk, **delta},
-                      "plain": {"latency_ms": {"p50": pct(lat_plain, 50),
-                                               "p99": pct(lat_plain, 99)}}})
+        return {"latency_ms": {"p50": pct(lat_plain, 50), "p99": pct(lat_plain, 99)}}
+
+    S = L.Server(hbm_budget_bytes=int(args.served_budget_gb * 2 ** 30),
+                 iters_per_round=args.served_round, tune=args.served_tune)
+    ids = [S.add_matrix(A) for A in pool]
+    serve(S, ids, None)  # warm-up: uploads, graph capture, pool blocks
+    note("warm-up pass done")
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    _, _, _, _, served_makespan, sat_delta, diff = serve(S, ids, None)
+    note("saturated pass done")
+    value = N / served_makespan
+    loads = []
+    for load in [float(v) for v in args.served_loads.split(",")]:
+        entry, arrivals = timed_pass(S, ids, load)
+        entry["plain"] = plain_latency(arrivals)
+        loads.append(entry)
+        note(f"load {load} done")
     st = S.stats()
     S.close()
+    bound = None
+    if args.served_bind_gb > 0:
+        # the same stream under a device-memory budget below the pool's
+        # footprint: uploads, evictions and waits inside the timed passes
+        S = L.Server(hbm_budget_bytes=int(args.served_bind_gb * 2 ** 30),
+                     iters_per_round=args.served_round, tune=args.served_tune)
+        ids = [S.add_matrix(A) for A in pool]
+        entry, arrivals = timed_pass(S, ids, 0.8)  # from cold: uploads inside the pass
+        entry["plain"] = plain_latency(arrivals)
+        bound = {"hbm_budget_gb": args.served_bind_gb, "load_0.8": entry}
+        S.close()
+        note("budget-bound passes done")
+    clk = clocks.stop()
     line = {"metric": METRIC, "value": value, "unit": "requests/s", "n_gpus": 1,
             "steps": 1, "warmup": 1, "ms_per_step": served_makespan * 1000,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": "served_stream", "requests": N, "cg_requests": n_cg,
                        "cg_mixed_precision_requests": n_mixed,
-                       "plain": "one request at a time, lilac_spmv / FP64 lilac_cg",
+                       "plain": "one request at a time, lilac_spmv per vector / FP64 lilac_cg",
                        "matrices": len(pool), "pool_matrix_bytes": pool_bytes,
+                       "request_vector_bytes": req_bytes,
                        "n_range": [1e3, args.served_nmax], "zipf": 1.1,
                        "spmv_vectors": f"1..{args.served_kmax}", "rtol": 1e-10,
                        "hbm_budget_gb": args.served_budget_gb, "tuned": bool(args.served_tune),
-                       "iters_per_round": args.served_round},
+                       "iters_per_round": args.served_round,
+                       "inputs": "per matrix one seeded block of SpMV vectors and one b, shared by "
+                                 "its requests; request vectors and results in page-locked host "
+                                 "memory (both arms); results checked against plain at 16 samples "
+                                 "each"},
             "served": {"requests_per_s": value, "cg_solves_per_s": n_cg / served_makespan,
                        "saturated": sat_delta, "resident_bytes_end": st["resident_bytes"]},
             "plain": {"requests_per_s": cap, "cg_solves_per_s": n_cg / plain_makespan},
             "served_vs_plain_throughput": value / cap,
             "max_rel_diff_served_vs_plain": diff,
             "loads": loads,
+            "budget_bound": bound, "clocks": clk,
             "roofline": None, "cpu_baseline": None,
             "e2e": {"value": value, "unit": "requests/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0, "note": "requests carry host buffers end to end"}}
@@ -1314,6 +1355,8 @@ def main():
     ap.add_argument("--served-loads", default="0.8",
                     help="arrival rates as fractions of the plain capacity (full: 0.5,0.8,0.95)")
     ap.add_argument("--served-budget-gb", type=float, default=120.0)
+    ap.add_argument("--served-bind-gb", type=float, default=0.0,
+                    help="also run the stream under this (binding) budget at load 0.8")
     ap.add_argument("--served-tune", type=int, default=0, help="1: timed tuning at upload")
     ap.add_argument("--served-round", type=int, default=16)
     ap.add_argument("--variant", default="",
