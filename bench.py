@@ -70,7 +70,8 @@ VARIANT_CODES = {"scalar": 1, "vector": 2, "staged": 3, "merge": 4, "slab": 5, "
 
 def _kernel_src_hash():
     h = hashlib.sha256()
-    for f in ("spmv_kernels.cuh", "ops.cuh", "lilac_device.cuh", "launch.cuh", "lilac_sell.cu"):
+    for f in ("spmv_kernels.cuh", "ops.cuh", "lilac_device.cuh", "launch.cuh", "lilac_sell.cu",
+              "lilac_hub.cu"):
         with open(os.path.join(ROOT, "paper_2001_07938_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -248,8 +249,13 @@ class CG75k(Workload):
 
     def roofline_sample(self, k):
         A = self.A
-        return self._profiled(k, _spmv_bytes(A.n, A.ncols, A.nnz, 8),
-                              " with the CG epilogue (q = A p, p.q fused)")
+        ms, n, nbytes, name = self._profiled(k, _spmv_bytes(A.n, A.ncols, A.nnz, 8),
+                                             " with the CG epilogue (q = A p, p.q fused)")
+        if self.M.info()["variant"] == VARIANT_CODES["slab"]:
+            # FP64 CG on a SLAB handle runs the SLAB CG form
+            name = ("spmv_slab_cg_kernel (sliced ELL over x slabs in shared memory; q left as slab "
+                    "partials and p.q as per-CTA sums for the fused CG step)")
+        return ms, n, nbytes, name
 
     def e2e_setup(self):
         torch = self.torch

@@ -137,3 +137,37 @@ def test_invalid_requests_are_rejected():
     assert e.value.status == L.LILAC_ERR_BUDGET
     S.close()
     big.close()
+
+
+def test_request_that_can_never_fit_completes_with_budget_error():
+    """A matrix that fits the budget with a request whose workspace never can
+    (a 32-vector SpMV: 4 MB of vectors against a 3 MB budget) completes with
+    LILAC_ERR_BUDGET instead of waiting forever; the server then serves a
+    single-vector request on the same matrix."""
+    torch_cuda()
+    A = inputs.laplacian2d(50)
+    S = L.Server(hbm_budget_bytes=3 << 20)
+    mid = S.add_matrix(A)
+    X = inputs.uniform(5, 32 * A.ncols)
+    Y = np.full(32 * A.n, np.nan)
+    S.submit(L.LILAC_REQ_SPMV, mid, X, Y, 7, nvec=32)
+    done = []
+    for _ in range(100):
+        S.step()
+        done += S.poll()
+        if done:
+            break
+    assert [c["tag"] for c in done] == [7] and done[0]["status"] == L.LILAC_ERR_BUDGET
+    x = inputs.uniform(6, A.ncols)
+    y = np.full(A.n, np.nan)
+    S.submit(L.LILAC_REQ_SPMV, mid, x, y, 8)
+    done = []
+    for _ in range(100):
+        S.step()
+        done += S.poll()
+        if done:
+            break
+    assert [c["tag"] for c in done] == [8] and done[0]["status"] == L.LILAC_OK
+    ref = oracle.spmv(A.row_ptr, A.col_ind, A.vals, x)
+    assert np.all(np.abs(y - ref) <= spmv_tolerance(A, x, False))
+    S.close()
