@@ -483,13 +483,19 @@ lilac_status lilac_batch_cg(lilac_batch B, int32_t count, const lilac_csr* A,
  * caller submits requests as they arrive and calls lilac_server_step in its
  * loop.  Each step admits queued requests in arrival order while the budget
  * and the active limit allow (uploading a matrix on first use and evicting
- * the least recently used idle matrix when memory is needed), runs every
- * admitted single-vector SpMV request in one batched launch and every SpMV
- * request of 2 to 32 vectors through the multi-vector kernel (each nonzero
- * streamed once for all its vectors), advances every active CG solve by
- * iters_per_round iterations in one captured graph, and retires finished
- * requests (result copied to the caller's host buffer).  A request's result
- * is bitwise the same whatever else is in flight.
+ * the least recently used idle matrix when memory is needed, for the matrix
+ * or for a request's workspace), runs one round and retires finished
+ * requests (result copied to the caller's host buffer).  A round has two
+ * lanes.  Requests on matrices of fewer than 2^19 nonzeros run batched:
+ * every single-vector SpMV in one launch, iters_per_round iterations of every
+ * CG solve in one captured graph.  On a second stream, concurrently, SpMV
+ * requests of 2 to 32 vectors run through the multi-vector kernel (each
+ * nonzero streamed once for all its vectors), and single-vector SpMVs and CG
+ * solves on larger matrices run the matrix's own tuned kernels (lilac_spmv's
+ * and lilac_cg's, iters_per_round iterations per round).  The lane depends
+ * on the request alone, so a request's result is bitwise the same whatever
+ * else is in flight.  A request that cannot fit the budget even with nothing
+ * else in flight completes with LILAC_ERR_BUDGET.
  */
 typedef struct lilac_server_s* lilac_server;
 
@@ -536,7 +542,9 @@ typedef struct {
 } lilac_server_stats_t;
 
 void lilac_server_opts_default(lilac_server_opts* o);
-/* Create on the current device; `stream` carries all of the server's work. */
+/* Create on the current device; `stream` carries the server's uploads and
+ * batched work (the large-matrix lane runs on a stream the server creates and
+ * orders after it).  Errors: INVALID_ARG (options), CUDA (stream creation). */
 lilac_status lilac_server_create(const lilac_server_opts* o, void* stream, lilac_server* out);
 /* Free everything (in-flight requests are dropped).  NULL is a no-op. */
 lilac_status lilac_server_destroy(lilac_server S);
