@@ -4,10 +4,11 @@
 // scalar kept on the device, plus the mixed-precision form: FP32 inner CG
 // and FP64 iterative refinement.
 //
-// One iteration is three launches:
+// One iteration is two launches:
 //   K1  q = A p, p.q  (SpMV epilogue) -> alpha = rr / p.q
-//   K2  x += alpha p, r -= alpha q, r.r (one pass) -> beta, convergence
-//   K3  p = r + beta p
+//   K2  x += alpha p, r -= alpha q, r.r -> a bounded grid barrier -> beta,
+//       convergence, p = r + beta p (cg_step_kernel; on SLAB handles the
+//       SpMV leaves q as slab partials and cg_step_slabs_kernel adds them)
 // A solve with a fixed iteration count is replayed as one CUDA graph; with a
 // tolerance, graphs of `check_every` iterations are replayed until the
 // device flags convergence (kernels after convergence return at once).
@@ -32,6 +33,7 @@ __global__ void cg_state_reset_kernel(CgState* st, int max_iter) {
     st->max_iter = max_iter;
     st->done = 0;
     st->status = LILAC_ERR_NOT_CONVERGED;
+    st->dir_iter = -1;
 }
 
 static lilac_status ensure_cg_work(lilac_csr A, CgWork& W, bool f32) {
@@ -69,11 +71,28 @@ static lilac_status collect_prof(lilac_csr A, int pairs, Prof& prof) {
     return collect_prof_events(A, pairs, &prof.ms, &prof.launches);
 }
 
-// Grid of the fused CG step: at most one CTA per SM (its grid barrier needs
-// every CTA resident), about two elements per thread.
+// Grid of the fused CG step after a SLAB SpMV: at most one CTA per SM (its
+// grid barrier needs every CTA resident), about two elements per thread.
 static int step_grid(lilac_csr A, int n) {
     const int64_t need = ((int64_t)n + 2 * kVecThreads - 1) / (2 * kVecThreads);
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
+}
+
+// Grid of cg_step_kernel: at most one CTA of kStepThreads per SM, at least
+// four elements per thread.
+static int wide_step_grid(lilac_csr A, int n) {
+    const int64_t need = ((int64_t)n + 4 * kStepThreads - 1) / (4 * kStepThreads);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
+}
+
+// The CG step kernels' barrier counters and per-CTA r.r partials.
+static lilac_status ensure_cg_step(lilac_csr A, cudaStream_t s) {
+    const size_t need = 4 * sizeof(unsigned) + sizeof(double) * (size_t)A->sm_count;
+    if (!A->cg_step.p || A->cg_step.bytes < need) {
+        LILAC_TRY(A->ws_alloc(A->cg_step, need));
+        LILAC_CUDA_TRY(cudaMemsetAsync(A->cg_step.p, 0, A->cg_step.bytes, s));
+    }
+    return LILAC_OK;
 }
 
 // Enqueue `nit` iterations of CG on the work set W (vectors of type T; the
@@ -82,7 +101,6 @@ template <class V, class T>
 static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, int nit,
                                   cudaStream_t s, bool profile) {
     const int n = A->rows;
-    const int vg = vec_grid(A, n);
     CgState* st = W.state.as<CgState>();
     bool slab_cg = false;
     if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
@@ -112,9 +130,11 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
         LILAC_TRY(launch_spmv(A, val, W.p.as<T>(), op, s));
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
-        cg_update_kernel<T><<<vg, kVecThreads, 0, s>>>(n, x, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(),
-                                                       FinCgUpdate<T>{st, nullptr}, A->scratch());
-        cg_direction_kernel<T><<<vg, kVecThreads, 0, s>>>(n, W.r.as<T>(), W.p.as<T>(), st);
+        // update, r.r and direction in one launch (a bounded grid barrier)
+        unsigned* bar = A->cg_step.as<unsigned>();
+        cg_step_kernel<T, false><<<wide_step_grid(A, n), kStepThreads, 0, s>>>(
+            n, x, nullptr, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(), st, reinterpret_cast<double*>(bar + 4),
+            bar, A->status.as<int>());
     }
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -125,7 +145,7 @@ template <class V, class T>
 static int iter_kernels(lilac_csr A, const V* val) {
     if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
         if (slab_cg_active(A, val)) return 2;
-    return 2 + spmv_launch_count<OpCgPq<V, T>>(A, val);
+    return 1 + spmv_launch_count<OpCgPq<V, T>>(A, val);
 }
 
 // What FP64 CG on the handle's values needs before its first (captured)
@@ -133,15 +153,8 @@ static int iter_kernels(lilac_csr A, const V* val) {
 // barrier counters and r.r partials.
 static lilac_status prepare_cg64(lilac_csr A, cudaStream_t s) {
     LILAC_TRY(prepare_spmv<OpCgPq<double, double>>(A));
-    if (slab_cg_active(A, A->val.as<double>())) {
-        LILAC_TRY(prepare_slab_cg(A));
-        const size_t need = 4 * sizeof(unsigned) + sizeof(double) * (size_t)A->sm_count;
-        if (!A->cg_step.p || A->cg_step.bytes < need) {
-            LILAC_TRY(A->ws_alloc(A->cg_step, need));
-            LILAC_CUDA_TRY(cudaMemsetAsync(A->cg_step.p, 0, A->cg_step.bytes, s));
-        }
-    }
-    return LILAC_OK;
+    if (slab_cg_active(A, A->val.as<double>())) LILAC_TRY(prepare_slab_cg(A));
+    return ensure_cg_step(A, s);
 }
 
 // Run CG iterations until the device says done: either one graph of
@@ -155,6 +168,7 @@ static lilac_status run_cg_loop(lilac_csr A, const V* val, T* x, CgWork& W, int 
     LILAC_TRY(prepare_spmv<OpCgPq<V, T>>(A));
     if constexpr (std::is_same<V, double>::value && std::is_same<T, double>::value)
         if (val == A->val.as<double>()) LILAC_TRY(prepare_cg64(A, s));
+    LILAC_TRY(ensure_cg_step(A, s));
     const uint64_t pflag = prof.on ? 1 : 0;
     if (!has_tol) {
         if (prof.on) LILAC_TRY(ensure_prof_events(A, max_iter));
@@ -341,11 +355,13 @@ static lilac_status enqueue_iters_ru(lilac_csr A, const float* val32, const V* v
         LILAC_TRY(launch_spmv(A, val32, p, OpCgPq<float, float>{q, p, st}, s));
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
-        cg_update_kernel<float><<<vg, kVecThreads, 0, s>>>(n, d, r, p, q, FinCgUpdateRU{st},
-                                                           A->scratch());
-        ru_apply_kernel<<<vg, kVecThreads, 0, s>>>(n, x, d, st);
+        // update, r.r and, unless a replacement is due, the direction (a
+        // replacement: x += d instead, and the direction after the residual)
+        unsigned* bar = A->cg_step.as<unsigned>();
+        cg_step_kernel<float, true><<<wide_step_grid(A, n), kStepThreads, 0, s>>>(
+            n, d, x, r, p, q, st, reinterpret_cast<double*>(bar + 4), bar, A->status.as<int>());
         LILAC_TRY(launch_spmv(A, val, x, OpResidualRU<V>{r, b, st}, s));
-        cg_direction_kernel<float><<<vg, kVecThreads, 0, s>>>(n, r, p, st);
+        cg_direction_after_ru_kernel<<<vg, kVecThreads, 0, s>>>(n, r, p, st);
     }
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -370,6 +386,7 @@ static lilac_status cg_mixed_ru_impl(lilac_csr A, const V* val, const double* b,
     LILAC_TRY(prepare_spmv<OpResidual<V, RES_OUTER>>(A));
     LILAC_TRY(prepare_spmv<OpResidualRU<V>>(A));
     LILAC_TRY(prepare_spmv<OpCgPq<float, float>>(A));
+    LILAC_TRY(ensure_cg_step(A, s));
     if (!o.use_x0) LILAC_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * (size_t)n, s));
     cg_state_reset_kernel<<<1, 1, 0, s>>>(st, o.max_iter);
     LILAC_CUDA_TRY(cudaGetLastError());
@@ -395,7 +412,7 @@ static lilac_status cg_mixed_ru_impl(lilac_csr A, const V* val, const double* b,
             return enqueue_iters_ru<V>(A, val32, val, b, x, d, W, nit, cs, prof.on);
         }));
         launched += nit;
-        prof.kernels += (3 + spmv_launch_count<OpCgPq<float, float>>(A, val32) +
+        prof.kernels += (2 + spmv_launch_count<OpCgPq<float, float>>(A, val32) +
                          spmv_launch_count<OpResidualRU<V>>(A, val)) * nit;
         LILAC_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -463,7 +480,7 @@ lilac_status solo_cg_prepare(lilac_csr A, int prec, cudaStream_t s) {
     LILAC_TRY(prepare_spmv<OpResidual<double, RES_OUTER>>(A));
     LILAC_TRY(prepare_spmv<OpResidualRU<double>>(A));
     LILAC_TRY(prepare_spmv<OpCgPq<float, float>>(A));
-    return LILAC_OK;
+    return ensure_cg_step(A, s);
 }
 
 lilac_status solo_cg_start(lilac_csr A, SoloCg& c, const double* b, double* x, double rtol,

@@ -49,6 +49,8 @@ struct CgState {
     double delta2;     // replace when r.r <= delta2 * rr_anchor
     int update;        // 1: this iteration replaces r by the FP64 residual
     int updates;       // replacements done
+    int dir_iter;      // iteration whose direction waits for the replaced residual (-1: none)
+    int pad_;
 };
 
 __device__ __forceinline__ bool cg_done(const CgState* st) {
@@ -179,28 +181,6 @@ static __global__ void __launch_bounds__(kVecThreads)
     grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
 }
 
-// x += alpha p;  r -= alpha q;  rr_new = r.r  ->  beta, convergence test.
-template <class T>
-struct FinCgUpdate {
-    CgState* st;
-    double* rr_hist;  // nullable, max_iter + 1 entries
-    __device__ void finish(const double* tot) const {
-        const double rr_new = tot[0];
-        const int it = st->iters + 1;
-        st->iters = it;
-        if (rr_hist) rr_hist[it] = rr_new;
-        st->beta = rr_new / st->rr;
-        st->rr = rr_new;
-        if (rr_new == 0.0 || (st->tol2 >= 0.0 && rr_new <= st->tol2)) {
-            st->done = 1;
-            st->status = LILAC_OK;
-        } else if (it >= st->max_iter) {
-            st->done = 1;
-            st->status = st->tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
-        }
-    }
-};
-
 // 16-byte vector of T: the CG vector kernels move four FP32 or two FP64
 // elements per access when every array is 16-byte aligned.
 template <class T>
@@ -230,43 +210,8 @@ __device__ __forceinline__ bool aligned16(const void* a, const void* b, const vo
              reinterpret_cast<uintptr_t>(c) | reinterpret_cast<uintptr_t>(d)) & 15u) == 0;
 }
 
-template <class T, class Fin>
-static __global__ void __launch_bounds__(kVecThreads)
-    cg_update_kernel(int n, T* __restrict__ x, T* __restrict__ r, const T* __restrict__ p,
-                     const T* __restrict__ q, Fin fin, Scratch s) {
-    if (cg_done(fin.st)) return;
-    using VT = Vec16<T>;
-    using V = typename VT::type;
-    constexpr int N = VT::N;
-    const T alpha = T(fin.st->alpha);
-    typename RedOf<T>::type rr{};  // FP32 vectors: compensated FP32 (see CompF32)
-    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
-    const int nv = aligned16(x, r, p, q) ? n / N : 0;
-    for (int i = g0; i < nv; i += gs) {
-        V xv = reinterpret_cast<const V*>(x)[i], rv = reinterpret_cast<const V*>(r)[i];
-        const V pv = reinterpret_cast<const V*>(p)[i], qv = reinterpret_cast<const V*>(q)[i];
-#pragma unroll
-        for (int e = 0; e < N; ++e) {
-            VT::set(xv, e, VT::get(xv, e) + alpha * VT::get(pv, e));
-            const T ri = VT::get(rv, e) - alpha * VT::get(qv, e);
-            VT::set(rv, e, ri);
-            red_add_prod(rr, ri, ri);
-        }
-        reinterpret_cast<V*>(x)[i] = xv;
-        reinterpret_cast<V*>(r)[i] = rv;
-    }
-    for (int i = nv * N + g0; i < n; i += gs) {
-        x[i] += alpha * p[i];
-        const T ri = r[i] - alpha * q[i];
-        r[i] = ri;
-        red_add_prod(rr, ri, ri);
-    }
-    double red[1] = {red_value(rr)};
-    grid_reduce_finish<1, kVecThreads>(fin, red, s, 0);
-}
-
 // SLAB, CG form: one FP64 CG step q = A p with p.q, leaving the ends of the
-// step to the update kernel that follows.  q is left as the S slab partials
+// step to cg_step_slabs_kernel, which follows.  q is left as the S slab partials
 // P[s][row]: the update adds them in slab order where it reads q (the same
 // sums as the row-group combine of spmv_slab_kernel).  p.q is taken from the
 // pieces instead of the rows: lane l of chunk c keeps t = p[row] * piece (0
@@ -333,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 // take the same beta = r.r / r.r_old and the same convergence decision) and
 // p = r + beta p on the elements the thread updated.  CTA 0 records the step
 // in the solver state (iterations, alpha, beta, r.r, done / status) with the
-// rules of FinCgUpdate, and a breakdown when p.q <= 0 or is not finite.  The
+// plain-CG rules of cg_step_kernel, and a breakdown when p.q <= 0 or is not finite.  The
 // grid must fit on the GPU at once (at
 // most one CTA per SM, see grid_barrier_bounded); a barrier that times out
 // leaves DEV_TIMEOUT in the handle's status word.
@@ -445,25 +390,162 @@ static __global__ void __launch_bounds__(kVecThreads)
     for (int i = nv2 * 2 + g0; i < n; i += gs) p[i] = r[i] + beta * p[i];
 }
 
-// p = r + beta p.
+// One whole CG step after the SpMV q = A p (which left alpha in the state),
+// in one launch of at most one CTA per SM (all resident), for handles whose
+// SpMV writes q:
+//   phase 1: u += alpha p, r -= alpha q, r.r per thread (FP64, or compensated
+//            FP32 for FP32 vectors), per-CTA sums to rr_parts; u is x, or for
+//            RU (FP32 CG with FP64 reliable updates) the FP32 correction d;
+//   a bounded grid barrier (grid_barrier_bounded);
+//   phase 2: r.r_new from the CTA sums (every CTA adds them in slot order,
+//            so all take the same decision), recorded by CTA 0:
+//            plain CG: iterations + 1, beta = r.r_new / r.r, r.r = r.r_new;
+//            done (OK) when r.r_new = 0 or <= tol2, done at max_iter (OK for
+//            a fixed count, else NOT_CONVERGED); RU: a replacement is due
+//            when r.r_new fell to delta2 times r.r at the last replacement,
+//            is 0 or <= tol2, or the iteration cap is reached (then r.r
+//            keeps its previous value for beta), else beta and r.r as above;
+//            then p = r + beta p on the thread's elements, walked backwards
+//            so that the r and p it read last -- still in L2, q and u having
+//            been streamed with evict-first loads -- come first; for RU,
+//            when a replacement is due: x += d (FP64), d = 0 instead, and
+//            the direction waits for the FP64 residual
+//            (cg_direction_after_ru_kernel).
+constexpr int kStepThreads = 1024;
+
 template <class T>
-static __global__ void __launch_bounds__(kVecThreads)
-    cg_direction_kernel(int n, const T* __restrict__ r, T* __restrict__ p, const CgState* st) {
+__device__ __forceinline__ typename Vec16<T>::type ld_stream16(const T* a, int i) {
+    return __ldcs(reinterpret_cast<const typename Vec16<T>::type*>(a) + i);
+}
+
+template <class T, bool RU>
+static __global__ void __launch_bounds__(kStepThreads, 1)
+    cg_step_kernel(int n, T* __restrict__ u, double* __restrict__ x64, T* __restrict__ r,
+                   T* __restrict__ p, const T* __restrict__ q, CgState* st,
+                   double* __restrict__ rr_parts, unsigned* bar, int* status) {
     if (cg_done(st)) return;
     using VT = Vec16<T>;
     using V = typename VT::type;
     constexpr int N = VT::N;
-    const T beta = T(st->beta);
-    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
-    const int nv = aligned16(r, p) ? n / N : 0;
+    // every state field this kernel reads, before CTA 0 may write it
+    const T alpha = T(st->alpha);
+    const double rr_old = st->rr;
+    const int it = st->iters + 1;
+    const int max_iter = st->max_iter;
+    const double tol2 = st->tol2;
+    const double ru_bound = RU ? st->delta2 * st->rr_anchor : 0.0;
+    typename RedOf<T>::type rr{};
+    const int g0 = blockIdx.x * kStepThreads + threadIdx.x, gs = gridDim.x * kStepThreads;
+    const bool vec = aligned16(u, r, p, q);
+    const int nv = vec ? n / N : 0;
     for (int i = g0; i < nv; i += gs) {
-        const V rv = reinterpret_cast<const V*>(r)[i];
-        V pv = reinterpret_cast<const V*>(p)[i];
+        V uv = ld_stream16(u, i), rv = reinterpret_cast<const V*>(r)[i];
+        const V pv = reinterpret_cast<const V*>(p)[i], qv = ld_stream16(q, i);
 #pragma unroll
-        for (int e = 0; e < N; ++e) VT::set(pv, e, VT::get(rv, e) + beta * VT::get(pv, e));
-        reinterpret_cast<V*>(p)[i] = pv;
+        for (int e = 0; e < N; ++e) {
+            VT::set(uv, e, VT::get(uv, e) + alpha * VT::get(pv, e));
+            const T ri = VT::get(rv, e) - alpha * VT::get(qv, e);
+            VT::set(rv, e, ri);
+            red_add_prod(rr, ri, ri);
+        }
+        __stcs(reinterpret_cast<V*>(u) + i, uv);
+        reinterpret_cast<V*>(r)[i] = rv;
     }
+    for (int i = nv * N + g0; i < n; i += gs) {
+        u[i] += alpha * p[i];
+        const T ri = r[i] - alpha * q[i];
+        r[i] = ri;
+        red_add_prod(rr, ri, ri);
+    }
+    {
+        double red[1] = {red_value(rr)}, tot[1];
+        __shared__ double sh[32];
+        block_sum<1, kStepThreads>(red, tot, sh);
+        if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot[0];
+    }
+    bool skip = false;
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        skip = atomicCAS(status + 1, DEV_INJECT_SKIP_BARRIER, DEV_INJECT_NONE) == DEV_INJECT_SKIP_BARRIER;
+    if (!grid_barrier_bounded(bar, status, skip)) return;
+    __shared__ double sh_v;
+    if (threadIdx.x < 32) {
+        double v = 0.0;
+        for (int i = (int)threadIdx.x; i < (int)gridDim.x; i += 32) v += __ldcg(rr_parts + i);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (threadIdx.x == 0) sh_v = v;
+    }
+    __syncthreads();
+    const double rr_new = sh_v;
+    const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+    bool direction = true;
+    if (RU) {
+        const bool due = rr_new <= ru_bound || rr_new == 0.0 || (tol2 >= 0.0 && rr_new <= tol2) ||
+                         it >= max_iter;
+        if (lead) {
+            st->iters = it;
+            if (due) {
+                st->update = 1;  // st->rr keeps the previous r.r for beta
+                st->dir_iter = it;
+            } else {
+                st->beta = rr_new / rr_old;
+                st->rr = rr_new;
+            }
+        }
+        if (due) {
+            // x += d in FP64, d = 0, on the elements this thread updated
+            for (int i = g0; i < nv; i += gs)
+#pragma unroll
+                for (int e = 0; e < N; ++e) {
+                    x64[(size_t)i * N + e] += double(u[(size_t)i * N + e]);
+                    u[(size_t)i * N + e] = T(0);
+                }
+            for (int i = nv * N + g0; i < n; i += gs) {
+                x64[i] += double(u[i]);
+                u[i] = T(0);
+            }
+            return;
+        }
+    } else {
+        const bool conv = rr_new == 0.0 || (tol2 >= 0.0 && rr_new <= tol2);
+        const bool cap = it >= max_iter;
+        if (lead) {
+            st->iters = it;
+            st->beta = rr_new / rr_old;
+            st->rr = rr_new;
+            if (conv) {
+                st->done = 1;
+                st->status = LILAC_OK;
+            } else if (cap) {
+                st->done = 1;
+                st->status = tol2 >= 0.0 ? LILAC_ERR_NOT_CONVERGED : LILAC_OK;
+            }
+        }
+        direction = !(conv || cap);
+    }
+    if (!direction) return;
+    const T beta = T(rr_new / rr_old);
     for (int i = nv * N + g0; i < n; i += gs) p[i] = r[i] + beta * p[i];
+    if (g0 < nv) {
+        for (int i = g0 + ((nv - 1 - g0) / gs) * gs; i >= g0; i -= gs) {
+            const V rv = reinterpret_cast<const V*>(r)[i];
+            V pv = reinterpret_cast<const V*>(p)[i];
+#pragma unroll
+            for (int e = 0; e < N; ++e) VT::set(pv, e, VT::get(rv, e) + beta * VT::get(pv, e));
+            reinterpret_cast<V*>(p)[i] = pv;
+        }
+    }
+}
+
+// p = r + beta p after a reliable update's FP64 residual (the step kernel
+// left the direction of that iteration to this launch); a no-op otherwise.
+static __global__ void __launch_bounds__(kVecThreads)
+    cg_direction_after_ru_kernel(int n, const float* __restrict__ r, float* __restrict__ p,
+                                 const CgState* st) {
+    if (cg_done(st) || st->dir_iter != st->iters) return;
+    const float beta = float(st->beta);
+    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
+        p[i] = r[i] + beta * p[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -476,34 +558,8 @@ static __global__ void __launch_bounds__(kVecThreads)
 // float(b - A x) computed in FP64, keeping the search direction.
 
 // K2 epilogue: flag a replacement instead of taking beta from the recursive r.
-struct FinCgUpdateRU {
-    CgState* st;
-    __device__ void finish(const double* tot) const {
-        const double rr_new = tot[0];
-        const int it = st->iters + 1;
-        st->iters = it;
-        if (rr_new <= st->delta2 * st->rr_anchor || rr_new == 0.0 ||
-            (st->tol2 >= 0.0 && rr_new <= st->tol2) || it >= st->max_iter) {
-            st->update = 1;  // st->rr keeps the previous r.r for beta
-        } else {
-            st->beta = rr_new / st->rr;
-            st->rr = rr_new;
-        }
-    }
-};
-
 __device__ __forceinline__ bool ru_due(const CgState* st) {
     return *reinterpret_cast<const volatile int*>(&st->update) != 0 && !cg_done(st);
-}
-
-// x += d (FP64), d = 0, when a replacement is due.
-static __global__ void __launch_bounds__(kVecThreads)
-    ru_apply_kernel(int n, double* __restrict__ x, float* __restrict__ d, const CgState* st) {
-    if (!ru_due(st)) return;
-    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads) {
-        x[i] += double(d[i]);
-        d[i] = 0.0f;
-    }
 }
 
 // r = float(b - A x) with b - A x in FP64 (values of any type promoted);

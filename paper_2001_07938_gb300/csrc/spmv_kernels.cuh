@@ -226,9 +226,11 @@ __global__ void __launch_bounds__(THREADS)
                      &bar[st], policy);
     };
 
-    // test hook: CTA 0 leaves its first copy unissued (the waits below time out)
+    // test hook: CTA 0 leaves its first copy unissued (the waits below time
+    // out); only this hook is consumed here, another one stays armed
     const bool skip_first = tid == 0 && blockIdx.x == 0 &&
-                            atomicExch(s.status + 1, DEV_INJECT_NONE) == DEV_INJECT_SKIP_COPY;
+                            atomicCAS(s.status + 1, DEV_INJECT_SKIP_COPY, DEV_INJECT_NONE) ==
+                                DEV_INJECT_SKIP_COPY;
     if (cnt > 0 && tid == 0 && !skip_first) issue(0, 0);
     bool failed = false;
     // epilogues with reductions: rows are stored in phase B and reduced one

@@ -57,28 +57,33 @@ def test_bounded_wait_timeout_is_reported_sticky_and_reset():
     M.close()
 
 
-def test_cg_step_barrier_timeout_is_reported_sticky_and_reset():
-    """FP64 CG on a SLAB handle runs each step's update and direction in one
-    launch with a bounded grid barrier.  With CTA 0 kept from arriving, the
-    other CTAs give up after ~2 s and the solve reports LILAC_ERR_TIMEOUT
-    (sticky); after the reset the same solve converges."""
+@pytest.mark.parametrize("variant,width,precision", [
+    (L.LILAC_VARIANT_SLAB, 4, 0),   # cg_step_slabs_kernel
+    (L.LILAC_VARIANT_SELL, 1, 0),   # cg_step_kernel, FP64
+    (L.LILAC_VARIANT_SELL, 1, 2),   # cg_step_kernel, FP32 with FP64 reliable updates
+])
+def test_cg_step_barrier_timeout_is_reported_sticky_and_reset(variant, width, precision):
+    """CG runs each step's update and direction in one launch with a bounded
+    grid barrier.  With CTA 0 kept from arriving, the other CTAs give up after
+    ~2 s and the solve reports LILAC_ERR_TIMEOUT (sticky); after the reset the
+    same solve converges."""
     torch = torch_cuda()
     A = inputs.spd_random(30000, 40, 20.0, 4)
     b = inputs.uniform(3, A.n)
     M = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
-    M.set_variant(L.LILAC_VARIANT_SLAB, 4)
-    assert M.info()["active_variant"] == L.LILAC_VARIANT_SLAB
+    M.set_variant(variant, width)
+    assert M.info()["active_variant"] == variant
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     L.lilac_debug_inject(M.handle, L.LILAC_INJECT_SKIP_BARRIER)
     with pytest.raises(L.LilacError) as e:
-        M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+        M.cg(dev(b), x, rtol=1e-10, max_iter=300, precision=precision)
     assert e.value.status == L.LILAC_ERR_TIMEOUT
     with pytest.raises(L.LilacError) as e:
-        M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+        M.cg(dev(b), x, rtol=1e-10, max_iter=300, precision=precision)
     assert e.value.status == L.LILAC_ERR_TIMEOUT
     L.lilac_csr_reset_error(M.handle)
     x.zero_()
-    st, info = M.cg(dev(b), x, rtol=1e-10, max_iter=300)
+    st, info = M.cg(dev(b), x, rtol=1e-10, max_iter=300, precision=precision)
     torch.cuda.synchronize()
     assert st == L.LILAC_OK
     assert true_rel_residual(A, b, host(x)) <= 1e-10
