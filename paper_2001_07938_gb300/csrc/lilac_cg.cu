@@ -71,18 +71,38 @@ static lilac_status collect_prof(lilac_csr A, int pairs, Prof& prof) {
     return collect_prof_events(A, pairs, &prof.ms, &prof.launches);
 }
 
-// Grid of the fused CG step after a SLAB SpMV: at most one CTA per SM (its
-// grid barrier needs every CTA resident), about two elements per thread.
+// Grid of the fused CG step after a SLAB SpMV: at most one CTA of
+// kSlabStepThreads per SM (its grid barrier needs every CTA resident), about
+// two elements per thread.  The step is a chain of dependent latencies, so
+// more SMs beat fewer barrier arrivals: at n = 75,000, 147 CTAs of 256
+// threads took 3.47 ms per 75-iteration solve, 37 of 1,024 threads 3.97 ms.
+constexpr int kSlabStepThreads = 256;
 static int step_grid(lilac_csr A, int n) {
-    const int64_t need = ((int64_t)n + 2 * kVecThreads - 1) / (2 * kVecThreads);
+    const int64_t need = ((int64_t)n + 2 * kSlabStepThreads - 1) / (2 * kSlabStepThreads);
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
 }
 
-// Grid of cg_step_kernel: at most one CTA of kStepThreads per SM, at least
-// four elements per thread.
-static int wide_step_grid(lilac_csr A, int n) {
-    const int64_t need = ((int64_t)n + 4 * kStepThreads - 1) / (4 * kStepThreads);
-    return (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
+// cg_step_kernel with at most one CTA per SM: CTAs of 1,024 threads when
+// every SM gets four elements per thread or more (enough loads in flight for
+// HBM), else CTAs of 256 threads with about two elements per thread (more
+// SMs for a latency-bound step).
+template <class T, bool RU>
+static lilac_status launch_cg_step(lilac_csr A, int n, T* u, double* x64, T* r, T* p, const T* q,
+                                   CgState* st, cudaStream_t s) {
+    unsigned* bar = A->cg_step.as<unsigned>();
+    double* rr_parts = reinterpret_cast<double*>(bar + 4);
+    const int64_t wide = (int64_t)A->sm_count * kStepThreads * 4;
+    if ((int64_t)n >= wide) {
+        cg_step_kernel<kStepThreads, T, RU><<<A->sm_count, kStepThreads, 0, s>>>(
+            n, u, x64, r, p, q, st, rr_parts, bar, A->status.as<int>());
+    } else {
+        const int64_t need = ((int64_t)n + 2 * 256 - 1) / (2 * 256);
+        const int g = (int)std::max<int64_t>(1, std::min<int64_t>(need, A->sm_count));
+        cg_step_kernel<256, T, RU><<<g, 256, 0, s>>>(n, u, x64, r, p, q, st, rr_parts, bar,
+                                                     A->status.as<int>());
+    }
+    LILAC_CUDA_TRY(cudaGetLastError());
+    return LILAC_OK;
 }
 
 // The CG step kernels' barrier counters and per-CTA r.r partials.
@@ -120,7 +140,7 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
                 // whose CTAs are all resident: at most one per SM
                 unsigned* bar = A->cg_step.as<unsigned>();
                 double* rr_parts = reinterpret_cast<double*>(bar + 4);
-                cg_step_slabs_kernel<<<step_grid(A, n), kVecThreads, 0, s>>>(
+                cg_step_slabs_kernel<kSlabStepThreads><<<step_grid(A, n), kSlabStepThreads, 0, s>>>(
                     n, x, W.r.as<double>(), W.p.as<double>(), A->slab_P.as<double>(), A->slab_S,
                     A->slab_pq.as<double>(), A->slab_grid, st, rr_parts, bar, A->status.as<int>());
                 continue;
@@ -131,10 +151,8 @@ static lilac_status enqueue_iters(lilac_csr A, const V* val, T* x, CgWork& W, in
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
         // update, r.r and direction in one launch (a bounded grid barrier)
-        unsigned* bar = A->cg_step.as<unsigned>();
-        cg_step_kernel<T, false><<<wide_step_grid(A, n), kStepThreads, 0, s>>>(
-            n, x, nullptr, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(), st, reinterpret_cast<double*>(bar + 4),
-            bar, A->status.as<int>());
+        LILAC_TRY((launch_cg_step<T, false>(A, n, x, nullptr, W.r.as<T>(), W.p.as<T>(), W.q.as<T>(),
+                                             st, s)));
     }
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -357,9 +375,7 @@ static lilac_status enqueue_iters_ru(lilac_csr A, const float* val32, const V* v
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
         // update, r.r and, unless a replacement is due, the direction (a
         // replacement: x += d instead, and the direction after the residual)
-        unsigned* bar = A->cg_step.as<unsigned>();
-        cg_step_kernel<float, true><<<wide_step_grid(A, n), kStepThreads, 0, s>>>(
-            n, d, x, r, p, q, st, reinterpret_cast<double*>(bar + 4), bar, A->status.as<int>());
+        LILAC_TRY((launch_cg_step<float, true>(A, n, d, x, r, p, q, st, s)));
         LILAC_TRY(launch_spmv(A, val, x, OpResidualRU<V>{r, b, st}, s));
         cg_direction_after_ru_kernel<<<vg, kVecThreads, 0, s>>>(n, r, p, st);
     }

@@ -282,7 +282,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // grid must fit on the GPU at once (at
 // most one CTA per SM, see grid_barrier_bounded); a barrier that times out
 // leaves DEV_TIMEOUT in the handle's status word.
-static __global__ void __launch_bounds__(kVecThreads)
+template <int THREADS>
+static __global__ void __launch_bounds__(THREADS, 1)
     cg_step_slabs_kernel(int n, double* __restrict__ x, double* __restrict__ r,
                          double* __restrict__ p, const double* __restrict__ P, int S,
                          const double* __restrict__ pq_parts, int nparts, CgState* st,
@@ -305,7 +306,7 @@ static __global__ void __launch_bounds__(kVecThreads)
     const bool ok = pq > 0.0 && isfinite(pq);
     const double alpha = ok ? rr / pq : 0.0;
     double red[1] = {0.0};
-    const int g0 = blockIdx.x * kVecThreads + threadIdx.x, gs = gridDim.x * kVecThreads;
+    const int g0 = blockIdx.x * THREADS + threadIdx.x, gs = gridDim.x * THREADS;
     const bool vec = aligned16(x, r, p, P) && (n & 1) == 0;
     const int nv = (ok && vec) ? n / 2 : 0;
     for (int i = g0; i < nv; i += gs) {
@@ -337,7 +338,7 @@ static __global__ void __launch_bounds__(kVecThreads)
     {
         __shared__ double sh[32];
         double tot[1];
-        block_sum<1, kVecThreads>(red, tot, sh);
+        block_sum<1, THREADS>(red, tot, sh);
         if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot[0];
     }
     bool skip = false;
@@ -418,8 +419,8 @@ __device__ __forceinline__ typename Vec16<T>::type ld_stream16(const T* a, int i
     return __ldcs(reinterpret_cast<const typename Vec16<T>::type*>(a) + i);
 }
 
-template <class T, bool RU>
-static __global__ void __launch_bounds__(kStepThreads, 1)
+template <int THREADS, class T, bool RU>
+static __global__ void __launch_bounds__(THREADS, 1)
     cg_step_kernel(int n, T* __restrict__ u, double* __restrict__ x64, T* __restrict__ r,
                    T* __restrict__ p, const T* __restrict__ q, CgState* st,
                    double* __restrict__ rr_parts, unsigned* bar, int* status) {
@@ -435,7 +436,7 @@ static __global__ void __launch_bounds__(kStepThreads, 1)
     const double tol2 = st->tol2;
     const double ru_bound = RU ? st->delta2 * st->rr_anchor : 0.0;
     typename RedOf<T>::type rr{};
-    const int g0 = blockIdx.x * kStepThreads + threadIdx.x, gs = gridDim.x * kStepThreads;
+    const int g0 = blockIdx.x * THREADS + threadIdx.x, gs = gridDim.x * THREADS;
     const bool vec = aligned16(u, r, p, q);
     const int nv = vec ? n / N : 0;
     for (int i = g0; i < nv; i += gs) {
@@ -460,7 +461,7 @@ static __global__ void __launch_bounds__(kStepThreads, 1)
     {
         double red[1] = {red_value(rr)}, tot[1];
         __shared__ double sh[32];
-        block_sum<1, kStepThreads>(red, tot, sh);
+        block_sum<1, THREADS>(red, tot, sh);
         if (threadIdx.x == 0) rr_parts[blockIdx.x] = tot[0];
     }
     bool skip = false;
