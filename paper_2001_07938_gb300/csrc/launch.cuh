@@ -178,11 +178,20 @@ lilac_status launch_staged_any(lilac_csr_s* A, const typename Op::ValT* val,
 }
 
 // Elements in flight per lane in the sliced ELL kernels (SELL, SLAB).
-constexpr int kSellUnroll = 8;
+#ifndef LILAC_SELL_UNROLL
+#define LILAC_SELL_UNROLL 8
+#endif
+constexpr int kSellUnroll = LILAC_SELL_UNROLL;
 #ifndef LILAC_SLAB_UNROLL
 #define LILAC_SLAB_UNROLL 4
 #endif
 constexpr int kSlabUnroll = LILAC_SLAB_UNROLL;
+// Elements in flight per lane in the HUB pieces kernel (FP32 values and
+// 16-bit columns: more of them fit in a lane's registers than SLAB's).
+#ifndef LILAC_HUB_UNROLL
+#define LILAC_HUB_UNROLL 16
+#endif
+constexpr int kHubUnroll = LILAC_HUB_UNROLL;
 
 // SLAB: one CTA per SM holding a slab of x in shared memory (lilac_sell.cu
 // builds the sliced ELL copy of every slab and row group).  The copy holds the
@@ -330,7 +339,7 @@ template <int V, class Op>
 lilac_status prepare_hub(lilac_csr_s* A) {
     int& bps = bps_slot<V + 512, Op, true>(A->device);
     if (bps == 0) {
-        auto kern = hub_pieces_kernel<kSlabThreads, kSlabUnroll, Op>;
+        auto kern = hub_pieces_kernel<kSlabThreads, kHubUnroll, Op>;
         LILAC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             kSlabMaxBytes + 64));
         bps = 1;
@@ -361,7 +370,7 @@ lilac_status launch_hub(lilac_csr_s* A, const typename Op::ValT* val, const type
     const size_t smem = (sizeof(VecT) * ((size_t)A->hub_W + 1) + 15) & ~size_t(15);
     const HubSplits hs{A->hub_splits.as<int4>(), A->hub_sub_split.as<int>(), A->hub_part.as<double>(),
                        A->hub_cnt.as<unsigned>()};
-    hub_pieces_kernel<kSlabThreads, kSlabUnroll, Op><<<(unsigned)A->hub_grid, kSlabThreads, smem, stream>>>(
+    hub_pieces_kernel<kSlabThreads, kHubUnroll, Op><<<(unsigned)A->hub_grid, kSlabThreads, smem, stream>>>(
         hv, A->hub_ranges.as<int4>(), A->hub_val.as<typename Op::ValT>(), xhot, H,
         A->hub_P.as<AccT>(), hs, op);
     LILAC_CUDA_TRY(cudaGetLastError());
