@@ -17,6 +17,7 @@
 #include <cstring>
 #include <type_traits>
 
+#include "cg_step.cuh"
 #include "launch.cuh"
 
 namespace lilac {
