@@ -344,6 +344,19 @@ lilac_status prepare_hub(lilac_csr_s* A) {
                                             kSlabMaxBytes + 64));
         bps = 1;
     }
+    // the cold part's SELL kernel (adding the slab sums): its own occupancy
+    int& cps = bps_slot<V + 768, Op, false>(A->device);
+    if (cps == 0) {
+        auto k1 = spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op, true>;
+        LILAC_CUDA_TRY(cudaFuncSetAttribute(k1, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+        int b = occupancy_per_sm(k1, kSellThreads, 0);
+        if constexpr (Op::kTwoPhase && Op::NR > 0) {
+            auto k2 = spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op, true>;
+            LILAC_CUDA_TRY(cudaFuncSetAttribute(k2, cudaFuncAttributePreferredSharedMemoryCarveout, 0));
+            b = std::min(b, occupancy_per_sm(k2, kSellThreads, 0));
+        }
+        cps = b;
+    }
     LILAC_TRY(prepare_sell<V, Op>(A));
     return prepare_staged_any<Op>(A);
 }
@@ -374,7 +387,7 @@ lilac_status launch_hub(lilac_csr_s* A, const typename Op::ValT* val, const type
         hv, A->hub_ranges.as<int4>(), A->hub_val.as<typename Op::ValT>(), xhot, H,
         A->hub_P.as<AccT>(), hs, op);
     LILAC_CUDA_TRY(cudaGetLastError());
-    const int bps = bps_slot<V + 256, Op, false>(A->device);
+    const int bps = bps_slot<V + 768, Op, false>(A->device);
     constexpr int kWarps = kSellThreads / 32;
     int64_t grid = (int64_t)A->sm_count * bps;
     const int64_t need = ((int64_t)A->hubc_nchunks + kWarps - 1) / kWarps;
@@ -389,8 +402,8 @@ lilac_status launch_hub(lilac_csr_s* A, const typename Op::ValT* val, const type
     sc.long_cnt = A->hubc_cnt.as<unsigned>();
     if constexpr (Op::kTwoPhase && Op::NR > 0) {
         if (hub_split_epilogue<Op>(A)) {
-            spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op><<<(unsigned)grid, kSellThreads, 0, stream>>>(
-                cv, A->hubc_val.as<typename Op::ValT>(), x, op, sc);
+            spmv_sell_kernel<kSellThreads, kSellUnroll, true, Op, true>
+                <<<(unsigned)grid, kSellThreads, 0, stream>>>(cv, A->hubc_val.as<typename Op::ValT>(), x, op, sc);
             LILAC_CUDA_TRY(cudaGetLastError());
             rows_reduce_kernel<kVecThreads, Op><<<vec_grid(A, A->rows), kVecThreads, 0, stream>>>(
                 A->rows, op, A->scratch());
@@ -398,7 +411,7 @@ lilac_status launch_hub(lilac_csr_s* A, const typename Op::ValT* val, const type
             return LILAC_OK;
         }
     }
-    spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op><<<(unsigned)grid, kSellThreads, 0, stream>>>(
+    spmv_sell_kernel<kSellThreads, kSellUnroll, false, Op, true><<<(unsigned)grid, kSellThreads, 0, stream>>>(
         cv, A->hubc_val.as<typename Op::ValT>(), x, op, sc);
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;

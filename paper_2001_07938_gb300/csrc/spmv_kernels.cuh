@@ -417,10 +417,19 @@ struct SellView {
     int add_split_base;
 };
 
+// Slab sums added by a cold lane: those of the first kSellPreSlabs slabs are
+// loaded at the start of its chunk, the rest (slab q0 on) here.
+#ifndef LILAC_SELL_PRE_SLABS
+#define LILAC_SELL_PRE_SLABS 4
+#endif
+constexpr int kSellPreSlabs = LILAC_SELL_PRE_SLABS;
+
 template <class AccT>
-__device__ __forceinline__ AccT sell_add_slabs(const SellView& S, int idx, unsigned mask, AccT acc) {
+__device__ __forceinline__ AccT sell_add_slabs(const SellView& S, int idx, unsigned mask, AccT acc,
+                                               int q0 = 0) {
     const AccT* __restrict__ P = static_cast<const AccT*>(S.addP);
-    for (int q = 0; mask != 0u; ++q, mask >>= 1)
+    mask >>= q0;
+    for (int q = q0; mask != 0u; ++q, mask >>= 1)
         if (mask & 1u) acc += __ldg(P + (size_t)q * S.add_stride + idx);
     return acc;
 }
@@ -455,7 +464,9 @@ __device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& o
 // kStoreOnly (two-phase epilogues): rows are only stored; the reductions run
 // in row order in rows_reduce_kernel, which keeps their loads coalesced when
 // the rows are sorted by length.
-template <int THREADS, int UNR, bool kStoreOnly, class Op>
+// kAdd (the cold part of a HUB copy): every lane adds its row's slab sums
+// (S.addP), loaded at the start of its chunk.
+template <int THREADS, int UNR, bool kStoreOnly, class Op, bool kAdd = false>
 __global__ void __launch_bounds__(THREADS)
     spmv_sell_kernel(SellView S, const typename Op::ValT* __restrict__ val,
                      const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
@@ -472,19 +483,33 @@ __global__ void __launch_bounds__(THREADS)
     // short chunks (many on power-law matrices) then cost no extra round trip
     int ch = (int)((blockIdx.x * THREADS + threadIdx.x) >> 5);
     int nbase = 0, nend = 0, nwho = -1;
+    unsigned nmask = 0u;  // slab sums to add (HUB cold part), also loaded ahead
     if (ch < S.nchunks) {
         nbase = __ldg(S.cptr + ch);
         nend = __ldg(S.cptr + ch + 1);
         nwho = __ldg(S.crow + (size_t)ch * 32 + lane);
+        if constexpr (kAdd) nmask = __ldg(S.add_mask + (size_t)ch * 32 + lane);
     }
     for (; ch < S.nchunks; ch += nwarps) {
         const int base = nbase;
         const int width = (nend - base) >> 5;
         const int who = nwho;
+        const unsigned mask = who >= 0 ? nmask : 0u;
         if (ch + nwarps < S.nchunks) {
             nbase = __ldg(S.cptr + ch + nwarps);
             nend = __ldg(S.cptr + ch + nwarps + 1);
             nwho = __ldg(S.crow + (size_t)(ch + nwarps) * 32 + lane);
+            if constexpr (kAdd) nmask = __ldg(S.add_mask + (size_t)(ch + nwarps) * 32 + lane);
+        }
+        // the row's slab sums of the first kSellPreSlabs slabs, issued before
+        // the element loop (added after it, in slab order)
+        AccT pre[kAdd && kSellPreSlabs > 0 ? kSellPreSlabs : 1];
+        if constexpr (kAdd) {
+#pragma unroll
+            for (int q = 0; q < kSellPreSlabs; ++q)
+                pre[q] = (mask >> q) & 1u ? __ldg(static_cast<const AccT*>(S.addP) +
+                                                   (size_t)q * S.add_stride + (size_t)ch * 32 + lane)
+                                          : AccT(0);
         }
         const ValT* __restrict__ vp = val + base + lane;
         const int* __restrict__ cp = S.col + base + lane;
@@ -523,8 +548,15 @@ __global__ void __launch_bounds__(THREADS)
                 if (k + u < width) acc += AccT(vv[u]) * AccT(xx[u]);
         }
         if (who >= 0) {
-            if (S.addP)
-                acc = sell_add_slabs(S, ch * 32 + lane, __ldg(S.add_mask + (size_t)ch * 32 + lane), acc);
+            if constexpr (kAdd) {
+                if (mask != 0u) {
+#pragma unroll
+                    for (int q = 0; q < kSellPreSlabs; ++q)
+                        if ((mask >> q) & 1u) acc += pre[q];
+                    if (mask >> kSellPreSlabs)
+                        acc = sell_add_slabs(S, ch * 32 + lane, mask, acc, kSellPreSlabs);
+                }
+            }
             if constexpr (kStoreOnly)
                 op.store(who, acc);
             else
