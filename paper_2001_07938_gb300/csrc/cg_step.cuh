@@ -31,6 +31,32 @@ static __global__ void __launch_bounds__(THREADS, 1)
     const int it = st->iters + 1;
     const int max_iter = st->max_iter;
     const double tol2 = st->tol2;
+    const int g0 = blockIdx.x * THREADS + threadIdx.x, gs = gridDim.x * THREADS;
+    const bool vec = aligned16(x, r, p, P) && (n & 1) == 0;
+    const double2* __restrict__ P2 = reinterpret_cast<const double2*>(P);
+    // Held form (every thread has at most kHeld 16-byte vectors, at most
+    // kHeldSlabs slabs): the thread's x, r, p and slab partials are loaded
+    // before the p.q sum and kept in registers across the grid barrier, so
+    // the update and the direction read nothing more: two dependent L2 round
+    // trips fewer in a latency-bound step.  Same arithmetic in the same order.
+    constexpr int kHeld = 2, kHeldSlabs = 4;
+    const int nh = n / 2;
+    const bool held = vec && nh <= kHeld * gs && S <= kHeldSlabs;
+    double2 xh[kHeld], rh[kHeld], ph[kHeld], qh[kHeld][kHeldSlabs];
+    if (held) {
+#pragma unroll
+        for (int k = 0; k < kHeld; ++k) {
+            const int i = g0 + k * gs;
+            if (i < nh) {
+                xh[k] = reinterpret_cast<const double2*>(x)[i];
+                rh[k] = reinterpret_cast<const double2*>(r)[i];
+                ph[k] = reinterpret_cast<const double2*>(p)[i];
+#pragma unroll
+                for (int q = 0; q < kHeldSlabs; ++q)
+                    if (q < S) qh[k][q] = P2[(size_t)q * nh + i];
+            }
+        }
+    }
     __shared__ double sh_v;
     if (threadIdx.x < 32) {
         double v = 0.0;
@@ -44,15 +70,36 @@ static __global__ void __launch_bounds__(THREADS, 1)
     const bool ok = pq > 0.0 && isfinite(pq);
     const double alpha = ok ? rr / pq : 0.0;
     double red[1] = {0.0};
-    const int g0 = blockIdx.x * THREADS + threadIdx.x, gs = gridDim.x * THREADS;
-    const bool vec = aligned16(x, r, p, P) && (n & 1) == 0;
-    const int nv = (ok && vec) ? n / 2 : 0;
+    if (held) {
+#pragma unroll
+        for (int k = 0; k < kHeld; ++k) {
+            const int i = g0 + k * gs;
+            if (ok && i < nh) {
+                double2 qv = qh[k][0];
+#pragma unroll
+                for (int q = 1; q < kHeldSlabs; ++q)
+                    if (q < S) {
+                        qv.x += qh[k][q].x;
+                        qv.y += qh[k][q].y;
+                    }
+                xh[k].x += alpha * ph[k].x;
+                xh[k].y += alpha * ph[k].y;
+                rh[k].x -= alpha * qv.x;
+                rh[k].y -= alpha * qv.y;
+                red[0] += rh[k].x * rh[k].x;
+                red[0] += rh[k].y * rh[k].y;
+                reinterpret_cast<double2*>(x)[i] = xh[k];
+                reinterpret_cast<double2*>(r)[i] = rh[k];
+            }
+        }
+    }
+    const int nv = (ok && vec && !held) ? nh : 0;
     for (int i = g0; i < nv; i += gs) {
         double2 xv = reinterpret_cast<const double2*>(x)[i], rv = reinterpret_cast<const double2*>(r)[i];
         const double2 pv = reinterpret_cast<const double2*>(p)[i];
-        double2 qv = reinterpret_cast<const double2*>(P)[i];
+        double2 qv = P2[i];
         for (int q = 1; q < S; ++q) {
-            const double2 t = reinterpret_cast<const double2*>(P + (size_t)q * n)[i];
+            const double2 t = P2[(size_t)q * nh + i];
             qv.x += t.x;
             qv.y += t.y;
         }
@@ -65,7 +112,8 @@ static __global__ void __launch_bounds__(THREADS, 1)
         reinterpret_cast<double2*>(x)[i] = xv;
         reinterpret_cast<double2*>(r)[i] = rv;
     }
-    for (int i = nv * 2 + g0; ok && i < n; i += gs) {
+    // elements left to the scalar loop: all of them when not vectorised
+    for (int i = (vec ? 2 * nh : 0) + g0; ok && i < n; i += gs) {
         double qi = P[i];
         for (int q = 1; q < S; ++q) qi += P[(size_t)q * n + i];
         x[i] += alpha * p[i];
@@ -118,7 +166,20 @@ static __global__ void __launch_bounds__(THREADS, 1)
         }
     }
     if (done) return;
-    const int nv2 = vec ? n / 2 : 0;
+    if (held) {
+#pragma unroll
+        for (int k = 0; k < kHeld; ++k) {
+            const int i = g0 + k * gs;
+            if (i < nh) {
+                double2 pv = ph[k];
+                pv.x = rh[k].x + beta * pv.x;
+                pv.y = rh[k].y + beta * pv.y;
+                reinterpret_cast<double2*>(p)[i] = pv;
+            }
+        }
+        return;
+    }
+    const int nv2 = vec ? nh : 0;
     for (int i = g0; i < nv2; i += gs) {
         const double2 rv = reinterpret_cast<const double2*>(r)[i];
         double2 pv = reinterpret_cast<const double2*>(p)[i];

@@ -4,8 +4,8 @@
 //
 //   hub columns  the H most frequent columns (ties: the lower column first),
 //                in column order: slot h holds column hub_cols[h]; slab h / W
-//                of at most W = 192 KB of x, S <= 4 slabs (a slab is added
-//                while it covers at least 5% more of the nonzeros)
+//                of at most W = 192 KB of x, S <= 5 slabs (a slab is added
+//                while it covers at least 3% more of the nonzeros)
 //   hot part     per slab, the piece of every row that has one (its nonzeros
 //                in the slab's hub columns, in CSR order) as one lane, or as
 //                sub-pieces of at most kHubPieceCap, one lane each; lanes
@@ -33,9 +33,17 @@ namespace lilac {
 
 namespace {
 
-constexpr int kHubMaxSlabs = 4;
+// At most 8 slabs (the cold copy's per-lane slab mask is one byte).
+#ifndef LILAC_HUB_MAX_SLABS
+#define LILAC_HUB_MAX_SLABS 5
+#endif
+#ifndef LILAC_HUB_SLAB_GAIN
+#define LILAC_HUB_SLAB_GAIN 0.03
+#endif
+constexpr int kHubMaxSlabs = LILAC_HUB_MAX_SLABS;
+static_assert(kHubMaxSlabs >= 1 && kHubMaxSlabs <= 8, "the slab mask is one byte");
 constexpr double kHubMinShare = 0.4;
-constexpr double kHubSlabGain = 0.05;
+constexpr double kHubSlabGain = LILAC_HUB_SLAB_GAIN;
 constexpr int64_t kHubMinXBytes = int64_t(1) << 20;
 constexpr int64_t kHubChunkCost = 256;
 constexpr int kHubPieceCap = 1024;  // hot elements per lane at most
@@ -101,7 +109,7 @@ static lilac_status build_hub(lilac_csr A, cudaStream_t s) {
     LILAC_CUDA_TRY(cudaStreamSynchronize(s));
     std::vector<int64_t> cnt((size_t)ncols, 0);
     for (int64_t k = 0; k < nnz; ++k) cnt[(size_t)col[(size_t)k]]++;
-    // the most frequent columns and the share the first 1 .. 4 slabs of them hold
+    // the most frequent columns and the share the first 1 .. S slabs of them hold
     const int64_t hmax = std::min<int64_t>(ncols, (int64_t)kHubMaxSlabs * W);
     std::vector<int32_t> idx((size_t)ncols);
     std::iota(idx.begin(), idx.end(), 0);

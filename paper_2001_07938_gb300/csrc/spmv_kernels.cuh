@@ -394,9 +394,9 @@ __device__ __forceinline__ void slab_load_x(VecT* xs, const VecT* __restrict__ x
 
 // Global-x form.  crow[c * 32 + l] is the lane's row (>= 0), -1 (padding lane)
 // or -(2 + p) for piece p of a row longer than the piece cap: its sum goes to
-// part[p], and the last of the row's pieces to arrive (counter) adds them in
-// piece order and runs the epilogue.  Padding elements have column -1 (no
-// load; they add 0 * 0).
+// part[p], and the warp of the last of the row's pieces to arrive (counter)
+// adds them in a fixed order (sell_finish_pieces) and runs the epilogue.
+// Padding elements have column -1 (no load; they add 0 * 0).
 struct SellView {
     const int* __restrict__ cptr;         // [nchunks + 1]
     const int* __restrict__ crow;         // [nchunks * 32]
@@ -434,30 +434,54 @@ __device__ __forceinline__ AccT sell_add_slabs(const SellView& S, int idx, unsig
     return acc;
 }
 
+// Pieces of split rows, for the whole warp (warp-uniform call): every lane
+// holding a piece stores its sum to part[p] and takes a ticket on its row's
+// counter; for each lane whose piece came last, the warp adds the row's
+// pieces -- lane l the pieces l, l + 32, ... in order, then a butterfly of
+// shuffles, the same fixed order for a given piece count -- and that lane
+// runs the epilogue.  A row of hundreds of pieces (a hub row of a power-law
+// graph) then costs a few L2 round trips instead of one per piece.
 template <bool kStoreOnly, class AccT, class Op>
-__device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& op, const Scratch& s,
-                                                  int p, AccT acc) {
+__device__ __forceinline__ void sell_finish_pieces(const SellView& S, const Op& op, const Scratch& s,
+                                                   int who, AccT acc, int lane) {
     constexpr int NR = kStoreOnly ? 0 : Op::NR;
-    s.long_part[p] = (double)acc;
-    __threadfence();
-    const int lid = S.piece_split[p];
-    const int4 sp = S.splits[lid];
-    const unsigned c = atomicAdd(&s.long_cnt[lid], 1u);
-    if (c == (unsigned)sp.z - 1u) {
+    bool last = false;
+    int4 sp = make_int4(0, 0, 0, 0);
+    int lid = 0;
+    if (who < -1) {
+        const int p = -who - 2;
+        s.long_part[p] = (double)acc;
         __threadfence();
-        AccT rs = AccT(0);
-        for (int j = 0; j < sp.z; ++j) rs += AccT(__ldcg(&s.long_part[sp.y + j]));
-        if (S.addP) rs = sell_add_slabs(S, S.add_split_base + lid, (unsigned)sp.w, rs);
-        if constexpr (kStoreOnly) {
-            op.store(sp.x, rs);
-        } else {
-            typename Op::RedT lred[NR > 0 ? NR : 1] = {};
-            op.row(sp.x, rs, lred);
+        lid = S.piece_split[p];
+        sp = S.splits[lid];
+        last = atomicAdd(&s.long_cnt[lid], 1u) == (unsigned)sp.z - 1u;
+    }
+    unsigned m = __ballot_sync(0xffffffffu, last);
+    if (m == 0u) return;
+    __threadfence();
+    while (m != 0u) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1u;
+        const int first = __shfl_sync(0xffffffffu, sp.y, src);
+        const int np = __shfl_sync(0xffffffffu, sp.z, src);
+        AccT v = AccT(0);
+        for (int j = lane; j < np; j += 32) v += AccT(__ldcg(&s.long_part[first + j]));
 #pragma unroll
-            for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = red_value(lred[q]);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == src) {
+            AccT rs = v;
+            if (S.addP) rs = sell_add_slabs(S, S.add_split_base + lid, (unsigned)sp.w, rs);
+            if constexpr (kStoreOnly) {
+                op.store(sp.x, rs);
+            } else {
+                typename Op::RedT lred[NR > 0 ? NR : 1] = {};
+                op.row(sp.x, rs, lred);
+#pragma unroll
+                for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = red_value(lred[q]);
+            }
+            s.long_cnt[lid] = 0u;
+            __threadfence();  // the epilogue sums before this CTA's grid-reduction ticket
         }
-        s.long_cnt[lid] = 0u;
-        __threadfence();  // the epilogue sums before this CTA's grid-reduction ticket
     }
 }
 
@@ -466,8 +490,19 @@ __device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& o
 // the rows are sorted by length.
 // kAdd (the cold part of a HUB copy): every lane adds its row's slab sums
 // (S.addP), loaded at the start of its chunk.
+// The HUB cold part's lanes are short (a few elements each): with FP32
+// vectors the kernel is bound by load latency, so it is held to 48 registers
+// for five CTAs per SM (80 registers gave two: 1.13x slower on an R-MAT
+// scale-22 PageRank); FP64 forms would spill there and keep their registers.
+#ifndef LILAC_HUB_COLD_MIN_BLOCKS
+#define LILAC_HUB_COLD_MIN_BLOCKS 5
+#endif
+template <class Op, bool kAdd>
+constexpr int sell_min_blocks() {
+    return kAdd && sizeof(typename Op::VecT) == 4 ? LILAC_HUB_COLD_MIN_BLOCKS : 1;
+}
 template <int THREADS, int UNR, bool kStoreOnly, class Op, bool kAdd = false>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, sell_min_blocks<Op, kAdd>())
     spmv_sell_kernel(SellView S, const typename Op::ValT* __restrict__ val,
                      const typename Op::VecT* __restrict__ x, Op op, Scratch s) {
     if (op.skip()) return;
@@ -561,9 +596,9 @@ __global__ void __launch_bounds__(THREADS)
                 op.store(who, acc);
             else
                 op.row(who, acc, red);
-        } else if (who < -1) {
-            sell_finish_piece<kStoreOnly, AccT>(S, op, s, -who - 2, acc);
         }
+        if (__any_sync(0xffffffffu, who < -1))
+            sell_finish_pieces<kStoreOnly, AccT>(S, op, s, who, acc, lane);
     }
     if constexpr (NR > 0) {
         double r2[NR];
