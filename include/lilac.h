@@ -122,7 +122,9 @@ typedef enum {
  * tile) and other short rows: STAGED with min(w, 8) lanes per row, w the
  * smallest power of two >= m / 2; long regular rows: VECTOR with the smallest
  * power of two >= m / 16 lanes per row (2 .. 32).  The timed trial starts
- * from this choice and keeps it unless another candidate is faster. */
+ * from this choice and keeps it unless another candidate is faster; a
+ * sliced ELL candidate (SELL, SLAB, HUB) within 3% of the fastest counts as
+ * a tie and is kept (its solver forms are the cheaper ones). */
 
 /*
  * Upload a CSR matrix once and return a handle (construct + update of the

@@ -394,8 +394,9 @@ __device__ __forceinline__ void slab_load_x(VecT* xs, const VecT* __restrict__ x
 
 // Global-x form.  crow[c * 32 + l] is the lane's row (>= 0), -1 (padding lane)
 // or -(2 + p) for piece p of a row longer than the piece cap: its sum goes to
-// part[p], and the warp of the last of the row's pieces to arrive (counter)
-// adds them in a fixed order (sell_finish_pieces) and runs the epilogue.
+// part[p], and the last of the row's pieces to arrive (counter) adds them in
+// piece order (the HUB cold part: its warp adds them in a fixed order) and
+// runs the epilogue.
 // Padding elements have column -1 (no load; they add 0 * 0).
 struct SellView {
     const int* __restrict__ cptr;         // [nchunks + 1]
@@ -434,13 +435,43 @@ __device__ __forceinline__ AccT sell_add_slabs(const SellView& S, int idx, unsig
     return acc;
 }
 
-// Pieces of split rows, for the whole warp (warp-uniform call): every lane
-// holding a piece stores its sum to part[p] and takes a ticket on its row's
-// counter; for each lane whose piece came last, the warp adds the row's
-// pieces -- lane l the pieces l, l + 32, ... in order, then a butterfly of
-// shuffles, the same fixed order for a given piece count -- and that lane
-// runs the epilogue.  A row of hundreds of pieces (a hub row of a power-law
-// graph) then costs a few L2 round trips instead of one per piece.
+// Piece p of a split row: its sum goes to part[p], and the last of the row's
+// pieces to arrive (counter) adds them in piece order and runs the epilogue.
+template <bool kStoreOnly, class AccT, class Op>
+__device__ __forceinline__ void sell_finish_piece(const SellView& S, const Op& op, const Scratch& s,
+                                                  int p, AccT acc) {
+    constexpr int NR = kStoreOnly ? 0 : Op::NR;
+    s.long_part[p] = (double)acc;
+    __threadfence();
+    const int lid = S.piece_split[p];
+    const int4 sp = S.splits[lid];
+    const unsigned c = atomicAdd(&s.long_cnt[lid], 1u);
+    if (c == (unsigned)sp.z - 1u) {
+        __threadfence();
+        AccT rs = AccT(0);
+        for (int j = 0; j < sp.z; ++j) rs += AccT(__ldcg(&s.long_part[sp.y + j]));
+        if (S.addP) rs = sell_add_slabs(S, S.add_split_base + lid, (unsigned)sp.w, rs);
+        if constexpr (kStoreOnly) {
+            op.store(sp.x, rs);
+        } else {
+            typename Op::RedT lred[NR > 0 ? NR : 1] = {};
+            op.row(sp.x, rs, lred);
+#pragma unroll
+            for (int q = 0; q < NR; ++q) s.long_red[lid * kMaxRed + q] = red_value(lred[q]);
+        }
+        s.long_cnt[lid] = 0u;
+        __threadfence();  // the epilogue sums before this CTA's grid-reduction ticket
+    }
+}
+
+// The same for the whole warp (warp-uniform call; the FP32 HUB cold part,
+// whose hub rows split into hundreds of pieces): every lane holding a piece stores
+// its sum to part[p] and takes a ticket on its row's counter; for each lane
+// whose piece came last, the warp adds the row's pieces -- lane l the pieces
+// l, l + 32, ... in order, then a butterfly of shuffles, the same fixed order
+// for a given piece count -- and that lane runs the epilogue: a few L2 round
+// trips instead of one per few pieces.  (It costs registers: the other SELL
+// forms, whose split rows have few pieces, keep the one-lane finish.)
 template <bool kStoreOnly, class AccT, class Op>
 __device__ __forceinline__ void sell_finish_pieces(const SellView& S, const Op& op, const Scratch& s,
                                                    int who, AccT acc, int lane) {
@@ -494,12 +525,14 @@ __device__ __forceinline__ void sell_finish_pieces(const SellView& S, const Op& 
 // vectors the kernel is bound by load latency, so it is held to 48 registers
 // for five CTAs per SM (80 registers gave two: 1.13x slower on an R-MAT
 // scale-22 PageRank); FP64 forms would spill there and keep their registers.
+// The other forms keep the compiler's own choice (0: no minimum; a minimum
+// of 1 let it take up to 96 registers and cost the FP32 Poisson CG SpMV 14%).
 #ifndef LILAC_HUB_COLD_MIN_BLOCKS
 #define LILAC_HUB_COLD_MIN_BLOCKS 5
 #endif
 template <class Op, bool kAdd>
 constexpr int sell_min_blocks() {
-    return kAdd && sizeof(typename Op::VecT) == 4 ? LILAC_HUB_COLD_MIN_BLOCKS : 1;
+    return kAdd && sizeof(typename Op::VecT) == 4 ? LILAC_HUB_COLD_MIN_BLOCKS : 0;
 }
 template <int THREADS, int UNR, bool kStoreOnly, class Op, bool kAdd = false>
 __global__ void __launch_bounds__(THREADS, sell_min_blocks<Op, kAdd>())
@@ -597,8 +630,12 @@ __global__ void __launch_bounds__(THREADS, sell_min_blocks<Op, kAdd>())
             else
                 op.row(who, acc, red);
         }
-        if (__any_sync(0xffffffffu, who < -1))
-            sell_finish_pieces<kStoreOnly, AccT>(S, op, s, who, acc, lane);
+        if constexpr (kAdd && sizeof(VecT) == 4) {
+            if (__any_sync(0xffffffffu, who < -1))
+                sell_finish_pieces<kStoreOnly, AccT>(S, op, s, who, acc, lane);
+        } else if (who < -1) {
+            sell_finish_piece<kStoreOnly, AccT>(S, op, s, -who - 2, acc);
+        }
     }
     if constexpr (NR > 0) {
         double r2[NR];

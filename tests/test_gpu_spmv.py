@@ -394,8 +394,9 @@ def _time_calls(M, x, calls=20):
 def test_tuned_choice_is_within_a_factor_of_the_fastest_candidate(kind):
     """The timed autotuner (the per-matrix tuning phase; no single kernel wins
     everywhere) records its trial; the kernel it keeps is the trial's fastest
-    entry, and re-timed after create on a separate untuned handle it is
-    within 1.3x of the fastest candidate re-timed the same way."""
+    entry or a sliced ELL entry (SELL, SLAB, HUB) within 3% of it (a tie),
+    and re-timed after create on a separate untuned handle it is within 1.3x
+    of the fastest candidate re-timed the same way."""
     if kind == "random_columns":
         A = inputs.spd_random(40000, 40, 20.0, 11)
     else:
@@ -407,7 +408,12 @@ def test_tuned_choice_is_within_a_factor_of_the_fastest_candidate(kind):
     M.close()
     assert len(table) >= 5 and all(t["ms"] > 0 for t in table)
     best = min(table, key=lambda t: t["ms"])
-    assert (best["variant"], best["width"]) == (info["variant"], info["vector_width"])
+    kept = [t for t in table if (t["variant"], t["width"]) == (info["variant"], info["vector_width"])]
+    assert kept, (info, table)
+    sliced = (L.LILAC_VARIANT_SELL, L.LILAC_VARIANT_SLAB, L.LILAC_VARIANT_HUB)
+    if (best["variant"], best["width"]) != (info["variant"], info["vector_width"]):
+        ties = [t for t in table if t["variant"] in sliced and t["ms"] <= 1.03 * best["ms"] * (1 + 1e-6)]
+        assert ties and kept[0]["ms"] == min(t["ms"] for t in ties), (info, table)
     R = L.CsrMatrix.from_csr(A, flags=L.LILAC_CREATE_NO_TUNE)
     assert R.tune_table() == []
     retimed = {}
