@@ -452,6 +452,30 @@ struct OpPageRank {
         red_add_absdiff(red[0], yi, x[r]);
         if (is_dangling(has_out, r)) red_add(red[1], yi);
     }
+    __device__ bool reduce4_ok() const { return aligned16(y, x); }
+    // Rows r0 .. r0 + 3 (r0 a multiple of 4, y and x 16-byte aligned), in
+    // row order, with 16-byte loads and one bitmap word.
+    __device__ void reduce4(int r0, RedT* red) const {
+        using VT = Vec16<T>;
+        constexpr int N = VT::N;
+        T yv[4], xv[4];
+#pragma unroll
+        for (int k = 0; k < 4; k += N) {
+            const typename VT::type a = __ldcg(reinterpret_cast<const typename VT::type*>(y + r0 + k));
+            const typename VT::type b = __ldg(reinterpret_cast<const typename VT::type*>(x + r0 + k));
+#pragma unroll
+            for (int e = 0; e < N; ++e) {
+                yv[k + e] = VT::get(a, e);
+                xv[k + e] = VT::get(b, e);
+            }
+        }
+        const unsigned w = __ldg(has_out + (r0 >> 5)) >> (r0 & 31);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            red_add_absdiff(red[0], yv[k], xv[k]);
+            if (((w >> k) & 1u) == 0u) red_add(red[1], yv[k]);
+        }
+    }
     __device__ void finish(const double* tot) const {
         const int t = st->iter;
         l1[t] = tot[0];
