@@ -203,14 +203,13 @@ static __global__ void __launch_bounds__(THREADS, 1)
 //            done (OK) when r.r_new = 0 or <= tol2, done at max_iter (OK for
 //            a fixed count, else NOT_CONVERGED); RU: a replacement is due
 //            when r.r_new fell to delta2 times r.r at the last replacement,
-//            is 0 or <= tol2, or the iteration cap is reached (then r.r
-//            keeps its previous value for beta), else beta and r.r as above;
+//            is 0 or <= tol2, or the iteration cap is reached; beta and r.r
+//            as above either way;
 //            then p = r + beta p on the thread's elements, walked backwards
 //            so that the r and p it read last -- still in L2, q and u having
 //            been streamed with evict-first loads -- come first; for RU,
-//            when a replacement is due: x += d (FP64), d = 0 instead, and
-//            the direction waits for the FP64 residual
-//            (cg_direction_after_ru_kernel).
+//            when a replacement is due, also x += d (FP64), d = 0 (the
+//            replacement that follows changes r, not the direction).
 constexpr int kStepThreads = 1024;
 #ifndef LILAC_STEP_UNROLL
 #define LILAC_STEP_UNROLL 2
@@ -319,16 +318,14 @@ static __global__ void __launch_bounds__(THREADS, 1)
                          it >= max_iter;
         if (lead) {
             st->iters = it;
-            if (due) {
-                st->update = 1;  // st->rr keeps the previous r.r for beta
-                st->dir_iter = it;
-            } else {
-                st->beta = rr_new / rr_old;
-                st->rr = rr_new;
-            }
+            st->beta = rr_new / rr_old;
+            st->rr = rr_new;  // replaced by the new residual's r.r when one is due
+            if (due) st->update = 1;
         }
         if (due) {
-            // x += d in FP64, d = 0, on the elements this thread updated
+            // x += d in FP64, d = 0, on the elements this thread updated; the
+            // direction below is taken from this iteration's recursive r, and
+            // the replacement changes r only (the direction is kept)
             for (int i = g0; i < nv; i += gs)
 #pragma unroll
                 for (int e = 0; e < N; ++e) {
@@ -339,7 +336,6 @@ static __global__ void __launch_bounds__(THREADS, 1)
                 x64[i] += double(u[i]);
                 u[i] = T(0);
             }
-            return;
         }
     } else {
         const bool conv = rr_new == 0.0 || (tol2 >= 0.0 && rr_new <= tol2);
@@ -372,14 +368,4 @@ static __global__ void __launch_bounds__(THREADS, 1)
     }
 }
 
-// p = r + beta p after a reliable update's FP64 residual (the step kernel
-// left the direction of that iteration to this launch); a no-op otherwise.
-static __global__ void __launch_bounds__(kVecThreads)
-    cg_direction_after_ru_kernel(int n, const float* __restrict__ r, float* __restrict__ p,
-                                 const CgState* st) {
-    if (cg_done(st) || st->dir_iter != st->iters) return;
-    const float beta = float(st->beta);
-    for (int i = blockIdx.x * kVecThreads + threadIdx.x; i < n; i += gridDim.x * kVecThreads)
-        p[i] = r[i] + beta * p[i];
-}
 }  // namespace lilac

@@ -351,19 +351,18 @@ static lilac_status cg_mixed(lilac_csr A, const double* b, double* x, const lila
 // Mixed precision with reliable updates: one FP32 CG (FP32 values and
 // vectors, FP64 scalars) whose residual is replaced by the FP64 residual
 // b - A x whenever it has fallen by ru_delta, with x accumulated in FP64.
-// One iteration is five launches; K3 and K4 return at once unless a
-// replacement is due:
+// One iteration is three launches; K3 returns at once unless a replacement
+// is due:
 //   K1  q = A p, p.q -> alpha            (FP32 values)
-//   K2  d += alpha p, r -= alpha q, r.r  -> beta, or flag a replacement
-//   K3  x += d, d = 0                    (FP64 x)
-//   K4  r = float(b - A x), ||b - A x||  (handle values, FP64) -> beta, convergence
-//   K5  p = r + beta p
+//   K2  d += alpha p, r -= alpha q, r.r -> beta, p = r + beta p; when a
+//       replacement is due also x += d, d = 0 (FP64 x) and flag it
+//   K3  r = float(b - A x), ||b - A x||  (handle values, FP64) -> r.r, convergence
+// The replacement changes r and keeps the direction (van der Vorst & Ye).
 template <class V>
 static lilac_status enqueue_iters_ru(lilac_csr A, const float* val32, const V* val, const double* b,
                                      double* x, float* d, CgWork& W, int nit, cudaStream_t s,
                                      bool profile) {
     const int n = A->rows;
-    const int vg = vec_grid(A, n);
     CgState* st = W.state.as<CgState>();
     float* r = W.r.as<float>();
     float* p = W.p.as<float>();
@@ -374,11 +373,9 @@ static lilac_status enqueue_iters_ru(lilac_csr A, const float* val32, const V* v
         LILAC_TRY(launch_spmv(A, val32, p, OpCgPq<float, float>{q, p, st}, s));
         if (profile)
             LILAC_CUDA_TRY(cudaEventRecordWithFlags(A->prof_events[2 * it + 1], s, cudaEventRecordExternal));
-        // update, r.r and, unless a replacement is due, the direction (a
-        // replacement: x += d instead, and the direction after the residual)
+        // update, r.r and the direction (and x += d when a replacement is due)
         LILAC_TRY((launch_cg_step<float, true>(A, n, d, x, r, p, q, st, s)));
         LILAC_TRY(launch_spmv(A, val, x, OpResidualRU<V>{r, b, st}, s));
-        cg_direction_after_ru_kernel<<<vg, kVecThreads, 0, s>>>(n, r, p, st);
     }
     LILAC_CUDA_TRY(cudaGetLastError());
     return LILAC_OK;
@@ -429,7 +426,7 @@ static lilac_status cg_mixed_ru_impl(lilac_csr A, const V* val, const double* b,
             return enqueue_iters_ru<V>(A, val32, val, b, x, d, W, nit, cs, prof.on);
         }));
         launched += nit;
-        prof.kernels += (2 + spmv_launch_count<OpCgPq<float, float>>(A, val32) +
+        prof.kernels += (1 + spmv_launch_count<OpCgPq<float, float>>(A, val32) +
                          spmv_launch_count<OpResidualRU<V>>(A, val)) * nit;
         LILAC_CUDA_TRY(cudaMemcpyAsync(hs, st, sizeof(CgState), cudaMemcpyDeviceToHost, s));
         LILAC_CUDA_TRY(cudaStreamSynchronize(s));

@@ -49,7 +49,7 @@ struct CgState {
     double delta2;     // replace when r.r <= delta2 * rr_anchor
     int update;        // 1: this iteration replaces r by the FP64 residual
     int updates;       // replacements done
-    int dir_iter;      // iteration whose direction waits for the replaced residual (-1: none)
+    int dir_iter;      // -1: no direction waits for a replaced residual (kept for the layout)
     int pad_;
 };
 
@@ -278,15 +278,17 @@ __global__ void __launch_bounds__(THREADS, 1)
 // FP32 CG whose correction d accumulates in FP32; when its recursive residual
 // has fallen by delta since the last replacement (or reaches the tolerance,
 // or the iteration cap), x += d in FP64, d = 0, and r is replaced by
-// float(b - A x) computed in FP64, keeping the search direction.
+// float(b - A x) computed in FP64, keeping the search direction (the CG step
+// took beta from the recursive r and formed p before the replacement).
 
-// K2 epilogue: flag a replacement instead of taking beta from the recursive r.
+// A replacement flagged by the CG step, in a solve that is not finished.
 __device__ __forceinline__ bool ru_due(const CgState* st) {
     return *reinterpret_cast<const volatile int*>(&st->update) != 0 && !cg_done(st);
 }
 
 // r = float(b - A x) with b - A x in FP64 (values of any type promoted);
-// ||b - A x||^2 decides convergence, float(r).float(r) gives beta.
+// ||b - A x||^2 decides convergence, float(r).float(r) is the new r.r (beta
+// is recorded too but no longer read: the direction was formed already).
 template <class V>
 struct OpResidualRU {
     using ValT = V;
